@@ -1,0 +1,99 @@
+"""Seeded workload generators for the 2D type-II inverse NUDFT (points, coefficients, noise).
+
+Point sets follow the jittered-grid recipe: an m_x-by-m_y lattice whose nodes are shifted
+independently per coordinate by theta ~ U[lo, hi] lattice cells and wrapped into [0, 1)
+(paper Sec. 1: sample points lie anywhere in [0, 1)^2; M >= N = n_x n_y).  Coefficients are
+complex with independent N(0, 1) real and imaginary parts.  Nothing here evaluates the
+NUDFT; right-hand sides f = A c are formed by whichever side (oracle or device) the caller
+is testing.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def jittered_grid(mx: int, my: int, lo: float, hi: float, seed: int):
+    """Points x=((i+theta)/mx) mod 1, y=((j+theta')/my) mod 1, i-major order, theta iid U[lo,hi]."""
+    rng = _rng(seed)
+    i, j = np.meshgrid(np.arange(mx, dtype=np.float64), np.arange(my, dtype=np.float64), indexing="ij")
+    tx = rng.uniform(lo, hi, size=i.size)
+    ty = rng.uniform(lo, hi, size=j.size)
+    x = np.mod((i.ravel() + tx) / mx, 1.0)
+    y = np.mod((j.ravel() + ty) / my, 1.0)
+    # a value that rounds to exactly 1.0 after the wrap belongs to 0 (half-open [0, 1))
+    x[x >= 1.0] = 0.0
+    y[y >= 1.0] = 0.0
+    return x, y
+
+
+def uniform_grid(mx: int, my: int):
+    """Unperturbed lattice x=i/mx, y=j/my (i-major), the closed-form special case."""
+    i, j = np.meshgrid(np.arange(mx, dtype=np.float64), np.arange(my, dtype=np.float64), indexing="ij")
+    return (i.ravel() / mx), (j.ravel() / my)
+
+
+def complex_normal(shape, seed: int) -> np.ndarray:
+    """complex128 with iid N(0,1) real and imaginary parts."""
+    rng = _rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def noise_like(f0: np.ndarray, rel: float, seed: int) -> np.ndarray:
+    """Noise e = rel * ||f0|| * w / ||w|| per column, w iid complex normal."""
+    w = complex_normal(f0.shape, seed)
+    if f0.ndim == 1:
+        return rel * np.linalg.norm(f0) * w / np.linalg.norm(w)
+    return rel * np.linalg.norm(f0, axis=0) * w / np.linalg.norm(w, axis=0)
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One synthetic problem: sizes, grid recipe, solver options."""
+    name: str
+    nx: int
+    ny: int
+    mx: int
+    my: int
+    theta: tuple
+    nrhs: int
+    levels: int          # equal depth of both 1D trees; product leaf = (nx>>L) x (ny>>L)
+    eps: float
+    noise: float = 0.0
+    mixed: bool = False
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def M(self) -> int:
+        return self.mx * self.my
+
+
+WORKLOADS = {
+    # plain FP64 solve, N=256, M=512 on a 32x16 jittered grid, product leaf 4x4
+    "fp64_n16": Workload("fp64_n16", 16, 16, 32, 16, (-0.25, 0.25), 1, 2, 1e-10, seed=1),
+    # plain FP64 solve at scale, N=16384, M=32768, leaf 8x8, 1e-12 relative noise, 4 RHS
+    "fp64_n128": Workload("fp64_n128", 128, 128, 256, 128, (-0.3, 0.3), 4, 4, 1e-10, noise=1e-12, seed=2),
+    # mixed precision, N=65536, M=131072, leaf 8x8, 16 RHS, FP64 refinement
+    "mixed_n256": Workload("mixed_n256", 256, 256, 512, 256, (-0.3, 0.3), 16, 5, 1e-10, mixed=True, seed=3),
+    # differentiation workload, N=16384, M=32768, 16 RHS
+    "grad_n128": Workload("grad_n128", 128, 128, 256, 128, (-0.3, 0.3), 16, 4, 1e-10, seed=5),
+    # mid-size case the dense oracle finishes in seconds: several tiles, ragged leaves
+    "fp64_n32": Workload("fp64_n32", 32, 32, 64, 32, (-0.3, 0.3), 3, 3, 1e-10, seed=11),
+}
+
+
+def make_workload(w: Workload):
+    """Return (x, y, c_true) for a workload; c_true is (N, nrhs) in lexicographic ky + kx*ny order."""
+    x, y = jittered_grid(w.mx, w.my, w.theta[0], w.theta[1], w.seed)
+    c = complex_normal((w.N, w.nrhs), w.seed + 1000)
+    return x, y, c

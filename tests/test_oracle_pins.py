@@ -1,0 +1,263 @@
+"""Pins for the CPU oracle: each check ties an oracle function to something other than itself.
+
+* unperturbed grids reduce A to the 2D DFT (checked against numpy's FFT) and A^*A to N I
+  (Sec. 1, uniform Cartesian grid remark);
+* tiny least-squares problems are solved again by brute force (normal equations, extended
+  precision Gaussian elimination);
+* the transformed 1D matrix satisfies the Sylvester displacement identity and the
+  Cauchy-like closed form of Sec. 2.4, has unit row norms (Sec. 3.3, equal row norms), and
+  is the identity on the unperturbed square grid (Psi = 1 at coincidence, Sec. 2.4);
+* the face-splitting identity A F^{-1} = (A^x F_x^{-1}) . (A^y F_y^{-1}) (Sec. 3.1).
+
+The mutation tests at the end plant plausible mistakes in copies of oracle routines (sign of
+the exponent, transposed column order, dropped reflector factor) and assert a pin catches each.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from synthetic import WORKLOADS, complex_normal, jittered_grid, make_workload, noise_like, uniform_grid
+
+
+# ---------------------------------------------------------------- pin helpers (return errors)
+def fft_pin_error(forward_fn, nx, ny, seed=7):
+    """max |forward(c) - fft2(c)| / max|fft2(c)| on the unperturbed M = N grid."""
+    x, y = uniform_grid(nx, ny)
+    c = complex_normal(nx * ny, seed)
+    f = forward_fn(x, y, c, nx, ny)
+    ref = np.fft.fft2(c.reshape(nx, ny)).ravel()     # point (i, j) -> index i*ny + j
+    return np.max(np.abs(f - ref)) / np.max(np.abs(ref))
+
+
+def qr_pin_error(qr_fn, A, compare_lapack=True):
+    """max of ||Q R - A||, ||Q^*Q - I|| and the |R_ii| mismatch against LAPACK's QR.
+
+    |R_ii| is unique only for full column rank, so rank-deficient inputs skip that part.
+    """
+    R, vs, taus = qr_fn(A)
+    m, n = A.shape
+    Q = orc.apply_q(vs, taus, np.eye(m, dtype=complex))
+    e1 = np.max(np.abs(Q @ R - A)) / np.max(np.abs(A))
+    e2 = np.max(np.abs(Q.conj().T @ Q - np.eye(m)))
+    Rl = np.linalg.qr(A, mode="r")
+    p = min(m, n)
+    e3 = np.max(np.abs(np.abs(np.diag(R[:p, :p])) - np.abs(np.diag(Rl[:p, :p])))) / np.max(np.abs(A))
+    e3 = e3 if compare_lapack else 0.0
+    e4 = np.max(np.abs(np.tril(R[:p, :p], -1))) if p > 1 else 0.0
+    return max(e1, e2, e3, e4)
+
+
+# ---------------------------------------------------------------- forward / adjoint
+@pytest.mark.parametrize("nx,ny", [(8, 6), (5, 7), (16, 16)])
+def test_forward_is_fft2_on_unperturbed_grid(nx, ny):
+    assert fft_pin_error(orc.forward, nx, ny) < 1e-13
+
+
+def test_dense_matrix_matches_direct_sum():
+    x, y = jittered_grid(12, 10, -0.3, 0.3, 3)
+    nx, ny = 6, 5
+    c = complex_normal((nx * ny, 2), 4)
+    A = orc.nudft_matrix(x, y, nx, ny)
+    assert np.max(np.abs(A @ c - orc.forward(x, y, c, nx, ny))) < 1e-12
+    # an entry written out by hand: j=7, (kx, ky)=(3, 2) -> column 2 + 3*ny
+    j, kx, ky = 7, 3, 2
+    assert abs(A[j, ky + kx * ny] - np.exp(-2j * np.pi * (kx * x[j] + ky * y[j]))) < 1e-13
+
+
+def test_adjoint_is_conjugate_transpose():
+    x, y = jittered_grid(10, 9, -0.3, 0.3, 5)
+    nx, ny = 5, 4
+    A = orc.nudft_matrix(x, y, nx, ny)
+    f = complex_normal((x.size, 3), 6)
+    assert np.max(np.abs(orc.adjoint(x, y, f, nx, ny) - A.conj().T @ f)) < 1e-12
+    c = complex_normal(nx * ny, 8)
+    lhs = np.vdot(orc.forward(x, y, c, nx, ny), f[:, 0])
+    rhs = np.vdot(c, orc.adjoint(x, y, f[:, 0], nx, ny))
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+@pytest.mark.parametrize("nx,ny", [(6, 4), (8, 8)])
+def test_unperturbed_normal_matrix_is_N_identity(nx, ny):
+    x, y = uniform_grid(nx, ny)
+    A = orc.nudft_matrix(x, y, nx, ny)
+    assert np.max(np.abs(A.conj().T @ A - nx * ny * np.eye(nx * ny))) < 1e-11
+
+
+def test_oversampled_grid_lstsq_is_scaled_adjoint():
+    nx, ny = 6, 5
+    x, y = uniform_grid(2 * nx, 2 * ny)                # M = 4N, columns of a larger DFT
+    M = x.size
+    A = orc.nudft_matrix(x, y, nx, ny)
+    assert np.max(np.abs(A.conj().T @ A - M * np.eye(nx * ny))) < 1e-10
+    f = complex_normal(M, 9)
+    c, _, _ = orc.lstsq(A, f)
+    assert np.max(np.abs(c - orc.adjoint(x, y, f, nx, ny) / M)) < 1e-13
+
+
+# ---------------------------------------------------------------- least squares
+def _normal_eq_bruteforce(A, f):
+    """Normal equations A^*A c = A^*f by Gaussian elimination with partial pivoting in long double."""
+    A = A.astype(np.clongdouble)
+    G = A.conj().T @ A
+    b = A.conj().T @ f.astype(np.clongdouble)
+    n = G.shape[0]
+    M = np.concatenate([G, b[:, None]], axis=1)
+    for k in range(n):
+        piv = k + int(np.argmax(np.abs(M[k:, k])))
+        M[[k, piv]] = M[[piv, k]]
+        for i in range(k + 1, n):
+            M[i] -= (M[i, k] / M[k, k]) * M[k]
+    c = np.zeros(n, dtype=np.clongdouble)
+    for i in range(n - 1, -1, -1):
+        c[i] = (M[i, n] - np.sum(M[i, i + 1:n] * c[i + 1:])) / M[i, i]
+    return c.astype(np.complex128)
+
+
+def test_lstsq_matches_bruteforce_tiny():
+    x, y = jittered_grid(4, 2, -0.3, 0.3, 12)          # M = 8
+    nx, ny = 2, 2                                      # N = 4
+    A = orc.nudft_matrix(x, y, nx, ny)
+    f = complex_normal(8, 13)
+    c, res, rmin = orc.lstsq(A, f)
+    cb = _normal_eq_bruteforce(A, f)
+    assert np.max(np.abs(c - cb)) < 1e-12
+    assert rmin > 0
+    assert abs(res[0] - np.linalg.norm(A @ c - f)) < 1e-12
+
+
+def test_lstsq_recovers_consistent_data():
+    w = WORKLOADS["fp64_n16"]
+    x, y, ct = make_workload(w)
+    A = orc.nudft_matrix(x, y, w.nx, w.ny)
+    f = orc.forward(x, y, ct, w.nx, w.ny)
+    c, res, rmin = orc.lstsq(A, f)
+    assert np.max(orc.relerr(c, ct)) < 1e-12
+    assert rmin > 1.0          # full column rank with margin (smallest |R_ii| reported)
+
+
+def test_lstsq_residual_orthogonal_to_range():
+    w = WORKLOADS["fp64_n16"]
+    x, y, ct = make_workload(w)
+    A = orc.nudft_matrix(x, y, w.nx, w.ny)
+    f = orc.forward(x, y, ct, w.nx, w.ny) + noise_like(orc.forward(x, y, ct, w.nx, w.ny), 1e-3, 17)
+    c, res, _ = orc.lstsq(A, f)
+    r = f - A @ c
+    assert np.linalg.norm(A.conj().T @ r) < 1e-12 * np.linalg.norm(A) * np.linalg.norm(f)
+    assert abs(res[0] - np.linalg.norm(r)) < 1e-10 * np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("m,n", [(9, 5), (5, 9), (7, 7), (1, 3)])
+def test_householder_qr(m, n):
+    A = complex_normal((m, n), 21 + m * n)
+    assert qr_pin_error(orc.householder_qr, A) < 1e-13
+
+
+def test_householder_qr_zero_column():
+    A = complex_normal((6, 4), 3)
+    A[:, 1] = 0.0
+    assert qr_pin_error(orc.householder_qr, A, compare_lapack=False) < 1e-13
+    R, _, _ = orc.householder_qr(A)
+    assert R[1, 1] == 0.0
+
+
+def test_cgls_matches_dense_lstsq():
+    x, y = jittered_grid(16, 8, -0.3, 0.3, 31)
+    nx, ny = 8, 8
+    A = orc.nudft_matrix(x, y, nx, ny)
+    f = complex_normal((x.size, 2), 32)
+    c1, _, _ = orc.lstsq(A, f)
+    c2, it = orc.cgls(x, y, f, nx, ny, tol=1e-14)
+    assert np.max(orc.relerr(c2, c1)) < 1e-11
+
+
+# ---------------------------------------------------------------- transformed kernel matrix
+def test_tilde_sylvester_identity():
+    n = 12
+    x, _ = jittered_grid(30, 1, -0.4, 0.4, 41)
+    G = orc.tilde_1d(x, n)
+    gam = np.exp(-2j * np.pi * x)
+    xi = np.exp(-2j * np.pi * np.arange(n) / n)
+    u = gam ** n - 1.0
+    v = xi / n
+    lhs = gam[:, None] * G - G * xi[None, :]
+    assert np.max(np.abs(lhs - np.outer(u, v))) < 1e-13
+
+
+def test_tilde_cauchy_closed_form_and_unit_rows():
+    n = 10
+    x, _ = jittered_grid(25, 1, -0.4, 0.4, 43)
+    G = orc.tilde_1d(x, n)
+    gam = np.exp(-2j * np.pi * x)
+    xi = np.exp(-2j * np.pi * np.arange(n) / n)
+    closed = ((gam ** n - 1.0)[:, None] * (xi / n)[None, :]) / (gam[:, None] - xi[None, :])
+    assert np.max(np.abs(G - closed)) < 1e-12
+    assert np.max(np.abs(np.linalg.norm(G, axis=1) - 1.0)) < 1e-13
+
+
+def test_tilde_unperturbed_square_grid_is_identity():
+    n = 16
+    x = np.arange(n) / n
+    assert np.max(np.abs(orc.tilde_1d(x, n) - np.eye(n))) < 1e-13
+
+
+def test_tilde_2d_is_face_splitting_product():
+    x, y = jittered_grid(10, 8, -0.3, 0.3, 51)
+    nx, ny = 5, 4
+    Gx = orc.tilde_1d(x, nx)
+    Gy = orc.tilde_1d(y, ny)
+    fs = (Gx[:, :, None] * Gy[:, None, :]).reshape(x.size, nx * ny)
+    assert np.max(np.abs(orc.tilde_2d(x, y, nx, ny) - fs)) < 1e-12
+
+
+def test_idft2_matches_numpy_ifft2():
+    nx, ny = 8, 6
+    Y = complex_normal((nx * ny, 2), 61)
+    ref = np.stack([np.fft.ifft2(Y[:, q].reshape(nx, ny)).ravel() for q in range(2)], axis=1)
+    assert np.max(np.abs(orc.idft2(Y, nx, ny) - ref)) < 1e-14
+
+
+def test_solution_through_transformed_basis():
+    """c = F^{-1} argmin ||G~ y - f|| equals argmin ||A c - f|| (Sec. 4.1 change of basis)."""
+    w = WORKLOADS["fp64_n16"]
+    x, y, ct = make_workload(w)
+    f = orc.forward(x, y, ct, w.nx, w.ny)
+    Gt = orc.tilde_2d(x, y, w.nx, w.ny)
+    yv, _, _ = orc.lstsq(Gt, f)
+    assert np.max(orc.relerr(orc.idft2(yv, w.nx, w.ny), ct)) < 1e-12
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_pin_catches_wrong_exponent_sign():
+    def bad_forward(x, y, c, nx, ny):
+        return _forward_sign(x, y, c, nx, ny, +1)        # exp(+2 pi i ...) instead of exp(-...)
+    assert fft_pin_error(bad_forward, 8, 6) > 1e-3
+
+
+def _forward_sign(x, y, c, nx, ny, sgn):
+    kx = np.repeat(np.arange(nx), ny)
+    ky = np.tile(np.arange(ny), nx)
+    A = np.exp(sgn * 2j * np.pi * (np.outer(x, kx) + np.outer(y, ky)))
+    return A @ c
+
+
+def test_pin_catches_transposed_column_order():
+    def bad_forward(x, y, c, nx, ny):
+        kx = np.tile(np.arange(nx), ny)          # kx + ky*nx ordering instead of ky + kx*ny
+        ky = np.repeat(np.arange(ny), nx)
+        return np.exp(-2j * np.pi * (np.outer(x, kx) + np.outer(y, ky))) @ c
+    assert fft_pin_error(bad_forward, 8, 6) > 1e-3
+
+
+def test_pin_catches_dropped_reflector_factor():
+    def bad_qr(A):
+        R, vs, taus = orc.householder_qr(A)
+        return R, vs, [t / 2 for t in taus]      # plausible slip: tau = 1/||v||^2
+    A = complex_normal((7, 4), 5)
+    assert qr_pin_error(bad_qr, A) > 1e-3
+
+
+def test_pin_catches_wrong_dft_normalisation():
+    n = 12
+    x, _ = jittered_grid(30, 1, -0.4, 0.4, 41)
+    G = orc.nudft_1d(x, n) @ orc.dft_matrix(n).conj()      # forgot the 1/n of F^{-1}
+    assert np.max(np.abs(np.linalg.norm(G, axis=1) - 1.0)) > 1.0
