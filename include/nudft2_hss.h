@@ -1,0 +1,126 @@
+/*
+ * nudft2_hss -- direct solver for the 2D type-II inverse NUDFT on one GPU (sm_103a).
+ *
+ * Problem (Li & Liu, Sec. 1, Eq. 1-2): given M sample points (x_j, y_j) in [0,1)^2 and values
+ * f_j, find the coefficients c on the nx-by-ny frequency grid minimising ||A c - f||_2 with
+ *     A(j, (kx, ky)) = exp(-2 pi i (kx x_j + ky y_j)),  M >= N = nx * ny,
+ * columns ordered lexicographically: index ky + kx * ny, frequencies 0..n-1.
+ *
+ * Method (Sec. 4.1, Algorithm 1): c = F^{-1} G~_hss^+ f where G~ = A F^{-1} (F = F^x (x) F^y the
+ * 2D DFT) is approximated by an HSS matrix built from two 1D HSS approximations through the
+ * face-splitting product (Thm. 3.5), recompressed (Sec. 2.2) and factorised by URV (Sec. 2.3).
+ *
+ * Conventions for every entry point
+ *   - Arrays marked d_ are DEVICE pointers (cudaMalloc / torch CUDA tensors) owned by the
+ *     caller.  Complex data is interleaved (re, im) complex128 (double2) unless stated.
+ *     Matrices of right-hand sides are column major with the given leading dimension.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All work is
+ *     enqueued on it; build and factor synchronise it internally (ranks are read back).
+ *   - Return value: NUDFT2_OK or an error code; no exception crosses this interface.  The
+ *     message of the last error on the calling thread is returned by nudft2_last_error().
+ *   - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef NUDFT2_HSS_H
+#define NUDFT2_HSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nudft2_hss_s* nudft2_hss_t;
+
+typedef enum {
+  NUDFT2_OK = 0,
+  NUDFT2_EINVAL = 1,   /* invalid argument: M < N, bad sizes, points outside [0,1), eps not in (0,1) */
+  NUDFT2_ENOMEM = 2,   /* device allocation failed */
+  NUDFT2_ECUDA = 3,    /* CUDA runtime error (message in nudft2_last_error) */
+  NUDFT2_ERANK = 4,    /* a URV block is rank deficient (fewer rows than eliminated columns) */
+  NUDFT2_ETIMEOUT = 5, /* reserved: a bounded device wait expired */
+  NUDFT2_ESTATE = 6,   /* call out of order (factor before build, solve before factor) */
+  NUDFT2_ENOTIMPL = 7  /* operation not available in this build */
+} nudft2_status;
+
+typedef enum {
+  NUDFT2_FP64 = 0,     /* all HSS work in complex128 */
+  NUDFT2_MIXED = 1     /* HSS work in complex64, FP64 iterative refinement with the exact apply */
+} nudft2_prec;
+
+typedef enum {
+  NUDFT2_FAST_FWD = 0,  /* out (M x nrhs) = G~_hss F in: the HSS forward map (Sec. 4.1, A_fast)   */
+  NUDFT2_FAST_ADJ = 1,  /* reserved */
+  NUDFT2_EXACT_FWD = 2, /* out (M x nrhs) = A in, direct O(MN) sum of Eq. 1 in FP64              */
+  NUDFT2_EXACT_ADJ = 3, /* out (N x nrhs) = A^* in, direct O(MN) sum in FP64                     */
+  NUDFT2_PINV = 4,      /* out (N x nrhs) = F^{-1} G~_hss^+ in (same as nudft2_hss_solve)         */
+  NUDFT2_PINV_ADJ = 5   /* reserved */
+} nudft2_op;
+
+typedef struct {
+  double eps;          /* HSS tolerance of the recompression (Alg. 1 step 3); 1D factors use eps/10 */
+  int levels;          /* depth L of both 1D trees; 0 = derive from leaf                           */
+  int leaf;            /* max columns of a product leaf when levels == 0 (e.g. 64 -> 8 x 8)         */
+  int prec;            /* nudft2_prec                                                             */
+  double refine_tol;   /* MIXED: stop when max relative residual ||f - A c||/||f|| <= refine_tol    */
+  int refine_max;      /* MIXED: maximum refinement steps                                          */
+  unsigned flags;      /* reserved, 0                                                              */
+} nudft2_opts;
+
+typedef struct {
+  int64_t M;
+  int nx, ny, levels, prec;
+  int max_rank;              /* HSS rank after recompression (r_h of Sec. 5)            */
+  int level_rank[16];        /* max basis size per level, level 0 = root               */
+  double t_build_ms;         /* t_c: 1D construction + face splitting + recompression  */
+  double t_factor_ms;        /* t_f: URV factorization                                 */
+  double t_solve_ms;         /* t_s of the last solve (incl. refinement in MIXED)       */
+  int refine_iters;          /* refinement steps of the last MIXED solve               */
+  double refine_relres;      /* max relative residual after the last MIXED solve       */
+  size_t device_bytes;       /* device memory reserved by the handle                   */
+  int launches;              /* kernel launches issued by the handle so far            */
+} nudft2_info;
+
+/* Build the HSS approximation of G~ = A F^{-1} (Alg. 1 steps 1-3, Sec. 3 and Sec. 2.2).
+ * d_x, d_y: M sample coordinates in [0,1) (copied).  nx, ny: frequency grid, M >= nx*ny.
+ * o: options (NULL = defaults: eps 1e-10, leaf 64, FP64).  *out receives the handle.
+ * Errors: EINVAL (sizes, eps, points outside [0,1)), ENOMEM, ECUDA. */
+nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, int nx, int ny,
+                               const nudft2_opts* o, void* stream, nudft2_hss_t* out);
+
+/* URV factorization of the HSS matrix (Alg. 1 step 4, Sec. 2.3).
+ * Errors: ESTATE (no build), ERANK (a node has fewer rows than eliminated columns). */
+nudft2_status nudft2_hss_factor(nudft2_hss_t h, void* stream);
+
+/* c = F^{-1} G~_hss^+ f (Alg. 1 step 5): URV sweeps then the 2D inverse DFT.
+ * d_f: M x nrhs complex128 (ld ldf >= M), point order as given to build.
+ * d_c: N x nrhs complex128 (ld ldc >= N), lexicographic ky + kx*ny.
+ * MIXED handles refine with the exact FP64 residual (opts.refine_tol / refine_max).
+ * Errors: ESTATE (not factorised), EINVAL (ld too small, nrhs < 0). */
+nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
+                               void* stream);
+
+/* Apply one operator of nudft2_op to nrhs columns: EXACT_FWD/EXACT_ADJ need only build;
+ * FAST_FWD needs build; PINV needs factor.  Shapes as documented on nudft2_op.
+ * Errors: EINVAL (op unknown, ld too small), ESTATE, ENOTIMPL (reserved ops). */
+nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t ldi, int nrhs, void* d_out,
+                               int64_t ldo, void* stream);
+
+/* Statistics of the handle (ranks, stage times, memory).  Errors: EINVAL (NULL). */
+nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);
+
+/* Release every device allocation of the handle.  NULL is ignored. */
+void nudft2_hss_free(nudft2_hss_t h);
+
+/* Entries of the transformed 1D matrix A^x (F^x)^{-1} (Sec. 2.4, the Cauchy-like kernel
+ * Psi(gamma_j, xi_k) = (1/n)((gamma_j/xi_k)^n - 1)/((gamma_j/xi_k) - 1), Psi = 1 at gamma = xi).
+ * d_x: M points (device), d_out: M x n complex128 column major (ld M).  Errors: EINVAL. */
+nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* nudft2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUDFT2_HSS_H */

@@ -1,0 +1,9 @@
+"""B300-native direct solver for the 2D type-II inverse NUDFT (HSS face-splitting + URV).
+
+Public API: NudftHSS (build / factor / solve / apply / info), psi_eval, and the operator
+constants of include/nudft2_hss.h.  All arithmetic runs in the CUDA library libnudft2_hss.so.
+"""
+from .binding import (  # noqa: F401
+    EXACT_ADJ, EXACT_FWD, FAST_ADJ, FAST_FWD, FP64, MIXED, PINV, PINV_ADJ, LIB_PATH, NudftError, NudftHSS, lib,
+    psi_eval,
+)

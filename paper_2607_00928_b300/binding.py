@@ -1,0 +1,155 @@
+"""Thin ctypes binding of the C-ABI in include/nudft2_hss.h.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.  Tensors are
+torch CUDA tensors; complex right-hand sides are complex128 and are passed column major
+(a (M, s) tensor is handed over as its (s, M) contiguous transpose with leading dimension M).
+If the shared library is missing this module raises at first use; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnudft2_hss.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ERANK, ETIMEOUT, ESTATE, ENOTIMPL = range(8)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ETIMEOUT", 6: "ESTATE", 7: "ENOTIMPL"}
+FP64, MIXED = 0, 1
+FAST_FWD, FAST_ADJ, EXACT_FWD, EXACT_ADJ, PINV, PINV_ADJ = range(6)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("levels", ctypes.c_int), ("leaf", ctypes.c_int), ("prec", ctypes.c_int),
+                ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("levels", ctypes.c_int),
+                ("prec", ctypes.c_int), ("max_rank", ctypes.c_int), ("level_rank", ctypes.c_int * 16),
+                ("t_build_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("refine_iters", ctypes.c_int), ("refine_relres", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int)]
+
+
+class NudftError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnudft2_hss.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with `python -m paper_2607_00928_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.nudft2_hss_build.argtypes = [vp, vp, i64, ci, ci, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    L.nudft2_hss_factor.argtypes = [vp, vp]
+    L.nudft2_hss_solve.argtypes = [vp, vp, i64, ci, vp, i64, vp]
+    L.nudft2_hss_apply.argtypes = [vp, ci, vp, i64, ci, vp, i64, vp]
+    L.nudft2_hss_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.nudft2_hss_free.argtypes = [vp]
+    L.nudft2_hss_free.restype = None
+    L.nudft2_psi_eval.argtypes = [vp, i64, ci, vp, vp]
+    L.nudft2_last_error.restype = ctypes.c_char_p
+    for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
+              "nudft2_psi_eval"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != OK:
+        raise NudftError(code, lib().nudft2_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor(a: torch.Tensor, rows: int) -> torch.Tensor:
+    """(rows,) or (rows, s) complex128 CUDA tensor -> contiguous (s, rows) (= column major)."""
+    if a.dim() == 1:
+        a = a[:, None]
+    assert a.shape[0] == rows, (a.shape, rows)
+    return a.to(device="cuda", dtype=torch.complex128).t().contiguous()
+
+
+def psi_eval(x: torch.Tensor, n: int) -> torch.Tensor:
+    """Entries Psi(gamma_j, xi_k) of the transformed 1D matrix (M x n complex128)."""
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    out = torch.empty((n, x.numel()), dtype=torch.complex128, device="cuda")
+    _check(lib().nudft2_psi_eval(ctypes.c_void_p(x.data_ptr()), x.numel(), n, ctypes.c_void_p(out.data_ptr()),
+                                 _stream()))
+    return out.t()
+
+
+class NudftHSS:
+    """Handle of one point set: build (Alg. 1 steps 1-3), factor (step 4), solve (step 5)."""
+
+    def __init__(self, x, y, nx: int, ny: int, eps: float = 1e-10, levels: int = 0, leaf: int = 64,
+                 prec: str = "fp64", refine_tol: float = 1e-8, refine_max: int = 8, stream=None):
+        self._h = ctypes.c_void_p()
+        self.x = torch.as_tensor(x).to(device="cuda", dtype=torch.float64).contiguous()
+        self.y = torch.as_tensor(y).to(device="cuda", dtype=torch.float64).contiguous()
+        self.M = self.x.numel()
+        self.nx, self.ny, self.N = nx, ny, nx * ny
+        self.stream = stream
+        o = Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max, 0)
+        _check(lib().nudft2_hss_build(ctypes.c_void_p(self.x.data_ptr()), ctypes.c_void_p(self.y.data_ptr()),
+                                      self.M, nx, ny, ctypes.byref(o), _stream(stream), ctypes.byref(self._h)))
+
+    def factor(self):
+        _check(lib().nudft2_hss_factor(self._h, _stream(self.stream)))
+        return self
+
+    def solve(self, f: torch.Tensor) -> torch.Tensor:
+        """c (N, s) = F^{-1} G~_hss^+ f for f (M,) or (M, s); lexicographic ky + kx*ny order."""
+        squeeze = f.dim() == 1
+        fc = _colmajor(f, self.M)
+        s = fc.shape[0]
+        c = torch.empty((s, self.N), dtype=torch.complex128, device="cuda")
+        _check(lib().nudft2_hss_solve(self._h, ctypes.c_void_p(fc.data_ptr()), self.M, s,
+                                      ctypes.c_void_p(c.data_ptr()), self.N, _stream(self.stream)))
+        return c[0] if squeeze else c.t()
+
+    def apply(self, op: int, v: torch.Tensor) -> torch.Tensor:
+        rows_in = self.N if op in (FAST_FWD, EXACT_FWD) else self.M
+        rows_out = self.M if op in (FAST_FWD, EXACT_FWD) else self.N
+        squeeze = v.dim() == 1
+        vc = _colmajor(v, rows_in)
+        s = vc.shape[0]
+        out = torch.empty((s, rows_out), dtype=torch.complex128, device="cuda")
+        _check(lib().nudft2_hss_apply(self._h, op, ctypes.c_void_p(vc.data_ptr()), rows_in, s,
+                                      ctypes.c_void_p(out.data_ptr()), rows_out, _stream(self.stream)))
+        return out[0] if squeeze else out.t()
+
+    def info(self) -> dict:
+        i = Info()
+        _check(lib().nudft2_hss_info(self._h, ctypes.byref(i)))
+        return {"M": i.M, "nx": i.nx, "ny": i.ny, "levels": i.levels, "prec": i.prec, "max_rank": i.max_rank,
+                "level_rank": list(i.level_rank)[: i.levels + 1], "t_build_ms": i.t_build_ms,
+                "t_factor_ms": i.t_factor_ms, "t_solve_ms": i.t_solve_ms, "refine_iters": i.refine_iters,
+                "refine_relres": i.refine_relres, "device_bytes": i.device_bytes, "launches": i.launches}
+
+    def close(self):
+        if self._h:
+            lib().nudft2_hss_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

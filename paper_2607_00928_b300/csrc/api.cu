@@ -1,0 +1,364 @@
+// C-ABI of the solver (include/nudft2_hss.h): argument checking, the exact FP64 apply,
+// the 2D inverse DFT, mixed-precision iterative refinement, and dispatch to Hss<R>.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nudft2_hss.h"
+#include "hss.cuh"
+
+using namespace nh;
+
+static thread_local std::string g_err;
+
+struct nudft2_hss_s {
+  nudft2_opts opt{};
+  int M = 0, nx = 0, ny = 0, L = 0, N = 0;
+  cudaStream_t st = 0;
+  Arena keep{(size_t)64 << 20};
+  Arena scr{(size_t)256 << 20};
+  Plan pl;
+  std::unique_ptr<Hss<double>> h64;
+  std::unique_ptr<Hss<float>> h32;
+  std::unique_ptr<Ops<double>> ops;
+  double2 *Ax = nullptr, *Ay = nullptr;              // exp(-2 pi i k x_j), caller order
+  double2 *Fxi = nullptr, *Fyi = nullptr;            // inverse DFT matrices (1/n included)
+  double2 *Fxf = nullptr, *Fyf = nullptr;            // forward DFT matrices
+  bool factored = false;
+  double t_build = 0, t_factor = 0, t_solve = 0, relres = 0;
+  int iters = 0;
+};
+
+template <typename F> static nudft2_status guard(F&& f) {
+  try {
+    f();
+    g_err.clear();
+    return NUDFT2_OK;
+  } catch (Error& e) {
+    g_err = e.what();
+    return (nudft2_status)e.code;
+  } catch (std::exception& e) {
+    g_err = e.what();
+    return NUDFT2_ECUDA;
+  }
+}
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static GemmD<double> g64(const double2* A, int lda, int opA, const double2* B, int ldb, int opB, double2* C, int ldc,
+                         int m, int n, int k, double alpha = 1.0, double beta = 0.0) {
+  return GemmD<double>{A, B, C, m, n, k, lda, ldb, ldc, opA, opB, alpha, beta};
+}
+
+// ----------------------------------------------------------------------------- exact apply (Eq. 1)
+// f_j = sum_kx Ax(j,kx) sum_ky Ay(j,ky) c(kx,ky): inner sum as a GEMM Ay * C (C viewed ny x nx).
+static void exact_fwd(nudft2_hss_s* h, const double2* c, int64_t ldc, int s, double2* f, int64_t ldf) {
+  const int M = h->M, nx = h->nx, ny = h->ny, N = h->N;
+  const int sc = std::max(1, std::min(s, (int)std::max<int64_t>(1, ((int64_t)1 << 31) / ((int64_t)M * nx * 16))));
+  auto mk = h->scr.mark();
+  double2* T = h->scr.arr<double2>((size_t)M * nx * sc);
+  double2* Cc = (ldc == N) ? nullptr : h->scr.arr<double2>((size_t)N * sc);
+  for (int q0 = 0; q0 < s; q0 += sc) {
+    const int qs = std::min(sc, s - q0);
+    const double2* C = c + (size_t)q0 * ldc;
+    if (Cc) {
+      NH_CK(cudaMemcpy2DAsync(Cc, N * sizeof(double2), C, ldc * sizeof(double2), N * sizeof(double2), qs,
+                              cudaMemcpyDeviceToDevice, h->st));
+      C = Cc;
+    }
+    h->ops->gemm({g64(h->Ay, M, OP_N, C, ny, OP_N, T, M, M, nx * qs, ny)});
+    rowdot(h->st, h->Ax, M, T, M, M, nx, qs, f + (size_t)q0 * ldf, (int)ldf);
+    h->ops->count();
+  }
+  h->scr.release(mk);
+}
+
+// (A^* f)(kx, ky) = sum_j conj(Ay(j,ky)) * (f_j conj(Ax(j,kx))): GEMM Ay^* Z, Z = f o conj(Ax).
+static void exact_adj(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* out, int64_t ldo) {
+  const int M = h->M, nx = h->nx, ny = h->ny, N = h->N;
+  const int sc = std::max(1, std::min(s, (int)std::max<int64_t>(1, ((int64_t)1 << 31) / ((int64_t)M * nx * 16))));
+  auto mk = h->scr.mark();
+  double2* Z = h->scr.arr<double2>((size_t)M * nx * sc);
+  double2* Oc = (ldo == N) ? nullptr : h->scr.arr<double2>((size_t)N * sc);
+  for (int q0 = 0; q0 < s; q0 += sc) {
+    const int qs = std::min(sc, s - q0);
+    nh::scale_rows_conj_multi(h->st, h->Ax, M, f + (size_t)q0 * ldf, (int)ldf, M, nx, qs, Z, M);
+    h->ops->count();
+    double2* O = Oc ? Oc : out + (size_t)q0 * ldo;
+    h->ops->gemm({g64(h->Ay, M, OP_C, Z, M, OP_N, O, ny, ny, nx * qs, M)});
+    if (Oc)
+      NH_CK(cudaMemcpy2DAsync(out + (size_t)q0 * ldo, ldo * sizeof(double2), Oc, N * sizeof(double2),
+                              N * sizeof(double2), qs, cudaMemcpyDeviceToDevice, h->st));
+  }
+  h->scr.release(mk);
+}
+
+// c = F^{-1} y per column: C = Fy^{-1} Y Fx^{-1} with Y viewed ny x nx (lexicographic order)
+static void dft2(nudft2_hss_s* h, const double2* y, int64_t ldy, int s, double2* c, int64_t ldc, bool inverse) {
+  const int nx = h->nx, ny = h->ny;
+  auto mk = h->scr.mark();
+  double2* T = h->scr.arr<double2>((size_t)h->N * s);
+  std::vector<GemmD<double>> g1, g2;
+  const double2* Fy = inverse ? h->Fyi : h->Fyf;
+  const double2* Fx = inverse ? h->Fxi : h->Fxf;
+  for (int q = 0; q < s; ++q) {
+    g1.push_back(g64(Fy, ny, OP_N, y + (size_t)q * ldy, ny, OP_N, T + (size_t)q * h->N, ny, ny, nx, ny));
+    g2.push_back(g64(T + (size_t)q * h->N, ny, OP_N, Fx, nx, OP_N, c + (size_t)q * ldc, ny, ny, nx, nx));
+  }
+  h->ops->gemm(g1);
+  h->ops->gemm(g2);
+  h->scr.release(mk);
+}
+
+template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, const double2* f, int64_t ldf, int s,
+                                                double2* ylex) {
+  const int M = h->M, N = h->N;
+  auto mk = h->scr.mark();
+  cplx<R>* f2 = h->scr.arr<cplx<R>>((size_t)M * s);
+  cplx<R>* yt = h->scr.arr<cplx<R>>((size_t)N * s);
+  convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, f2, M, 1.0);
+  H.solve(f2, M, s, yt, N);
+  convert_scatter<R, double>(h->st, yt, N, h->pl.colmap, N, s, ylex, N, 1.0);
+  h->scr.release(mk);
+}
+
+// ----------------------------------------------------------------------------- C-ABI
+extern "C" {
+
+const char* nudft2_last_error(void) { return g_err.c_str(); }
+
+nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(d_x && d_out && M > 0 && n > 0 && M < (1LL << 31), ST_EINVAL, "nudft2_psi_eval: bad arguments");
+    Arena scr;
+    scr.set_stream((cudaStream_t)stream);
+    Ops<double> ops((cudaStream_t)stream, &scr);
+    psi_eval<double>(ops, {PsiD<double>{d_x, (int)M, 0, n, n, (double2*)d_out, (int)M}});
+    NH_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, int nx, int ny,
+                               const nudft2_opts* o, void* stream, nudft2_hss_t* out) {
+  nudft2_hss_s* h = nullptr;
+  auto st = guard([&] {
+    NH_REQUIRE(out != nullptr, ST_EINVAL, "out is NULL");
+    *out = nullptr;
+    NH_REQUIRE(d_x && d_y, ST_EINVAL, "points are NULL");
+    NH_REQUIRE(nx >= 1 && ny >= 1 && (int64_t)nx * ny <= (1LL << 26), ST_EINVAL, "bad frequency grid");
+    NH_REQUIRE(M >= (int64_t)nx * ny, ST_EINVAL, "least squares needs M >= N = nx*ny");
+    NH_REQUIRE(M < (1LL << 31), ST_EINVAL, "M too large");
+    nudft2_opts opt{1e-10, 0, 64, NUDFT2_FP64, 1e-8, 8, 0};
+    if (o) opt = *o;
+    NH_REQUIRE(opt.eps > 0 && opt.eps < 1, ST_EINVAL, "eps must lie in (0,1)");
+    NH_REQUIRE(opt.prec == NUDFT2_FP64 || opt.prec == NUDFT2_MIXED, ST_EINVAL, "unknown precision");
+    int L = opt.levels;
+    if (L <= 0) {
+      // smallest depth whose product leaves have at most `leaf` columns
+      const int leaf = std::max(opt.leaf, 1);
+      L = 1;
+      while (L < 12 && (int64_t)(nx >> L) * (ny >> L) > leaf && (nx >> (L + 1)) >= 1 && (ny >> (L + 1)) >= 1) ++L;
+    }
+    NH_REQUIRE(L >= 1 && L <= 12 && (nx >> L) >= 1 && (ny >> L) >= 1, ST_EINVAL,
+               "levels must satisfy 1 <= L and 2^L <= min(nx, ny)");
+    // validate points on the host: finite and in [0, 1)
+    {
+      std::vector<double> hx(M), hy(M);
+      NH_CK(cudaMemcpy(hx.data(), d_x, M * sizeof(double), cudaMemcpyDeviceToHost));
+      NH_CK(cudaMemcpy(hy.data(), d_y, M * sizeof(double), cudaMemcpyDeviceToHost));
+      for (int64_t j = 0; j < M; ++j)
+        NH_REQUIRE(std::isfinite(hx[j]) && std::isfinite(hy[j]) && hx[j] >= 0 && hx[j] < 1 && hy[j] >= 0 && hy[j] < 1,
+                   ST_EINVAL, "points must be finite and lie in [0,1)^2");
+    }
+    h = new nudft2_hss_s();
+    h->opt = opt;
+    h->M = (int)M; h->nx = nx; h->ny = ny; h->L = L; h->N = nx * ny;
+    h->st = (cudaStream_t)stream;
+    h->keep.set_stream(h->st);
+    h->scr.set_stream(h->st);
+    h->ops.reset(new Ops<double>(h->st, &h->scr));
+    const double t0 = now_ms();
+    make_plan(h->st, h->keep, h->scr, d_x, d_y, (int)M, nx, ny, L, h->pl);
+    h->Ax = h->keep.arr<double2>((size_t)M * nx);
+    h->Ay = h->keep.arr<double2>((size_t)M * ny);
+    twiddle_table(h->st, h->pl.x, (int)M, nx, h->Ax);
+    twiddle_table(h->st, h->pl.y, (int)M, ny, h->Ay);
+    h->Fxi = h->keep.arr<double2>((size_t)nx * nx);
+    h->Fyi = h->keep.arr<double2>((size_t)ny * ny);
+    h->Fxf = h->keep.arr<double2>((size_t)nx * nx);
+    h->Fyf = h->keep.arr<double2>((size_t)ny * ny);
+    dft_matrix<double>(h->st, nx, +1, 1.0 / nx, h->Fxi);
+    dft_matrix<double>(h->st, ny, +1, 1.0 / ny, h->Fyi);
+    dft_matrix<double>(h->st, nx, -1, 1.0, h->Fxf);
+    dft_matrix<double>(h->st, ny, -1, 1.0, h->Fyf);
+    h->ops->count(8);
+    if (opt.prec == NUDFT2_FP64) {
+      h->h64.reset(new Hss<double>(h->st, &h->pl));
+      h->h64->build(opt.eps);
+    } else {
+      h->h32.reset(new Hss<float>(h->st, &h->pl));
+      h->h32->build(opt.eps);
+    }
+    NH_CK(cudaStreamSynchronize(h->st));
+    h->t_build = now_ms() - t0;
+    *out = h;
+  });
+  if (st != NUDFT2_OK && h) delete h;
+  return st;
+}
+
+nudft2_status nudft2_hss_factor(nudft2_hss_t h, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr, ST_ESTATE, "factor: no handle (build first)");
+    (void)stream;
+    const double t0 = now_ms();
+    if (h->h64) h->h64->factor();
+    else h->h32->factor();
+    NH_CK(cudaStreamSynchronize(h->st));
+    h->t_factor = now_ms() - t0;
+    h->factored = true;
+  });
+}
+
+static void do_solve(nudft2_hss_t h, const double2* f, int64_t ldf, int s, double2* c, int64_t ldc) {
+  const int M = h->M, N = h->N;
+  auto mk = h->scr.mark();
+  double2* ylex = h->scr.arr<double2>((size_t)N * s);
+  if (h->h64) {
+    hss_solve_lex<double>(h, *h->h64, f, ldf, s, ylex);
+    dft2(h, ylex, N, s, c, ldc, true);
+    h->iters = 0;
+    h->relres = -1;
+  } else {
+    // mixed precision: c <- c + F^{-1} G~32^+ (f - A c), residual in FP64 (exact apply)
+    double2* r = h->scr.arr<double2>((size_t)M * s);
+    double2* d = h->scr.arr<double2>((size_t)N * s);
+    double* fn = h->scr.arr<double>(s);
+    double* rn = h->scr.arr<double>(s);
+    NH_CK(cudaMemcpy2DAsync(r, M * sizeof(double2), f, ldf * sizeof(double2), M * sizeof(double2), s,
+                            cudaMemcpyDeviceToDevice, h->st));
+    NH_CK(cudaMemset2DAsync(c, ldc * sizeof(double2), 0, N * sizeof(double2), s, h->st));
+    colnorm2(h->st, M, s, r, M, fn);
+    std::vector<double> hf(s), hr(s);
+    NH_CK(cudaMemcpyAsync(hf.data(), fn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    int it = 0;
+    double worst = 1.0;
+    for (it = 1; it <= std::max(1, h->opt.refine_max); ++it) {
+      hss_solve_lex<float>(h, *h->h32, r, M, s, ylex);
+      dft2(h, ylex, N, s, d, N, true);
+      axpy2(h->st, N, s, 1.0, d, N, c, (int)ldc);
+      exact_fwd(h, c, ldc, s, r, M);                  // r = A c (FP64, Eq. 1)
+      axpy2(h->st, M, s, -1.0, f, (int)ldf, r, M);    // r = A c - f
+      colnorm2(h->st, M, s, r, M, rn);
+      NH_CK(cudaMemcpyAsync(hr.data(), rn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      NH_CK(cudaStreamSynchronize(h->st));
+      worst = 0;
+      for (int q = 0; q < s; ++q) worst = std::max(worst, std::sqrt(hr[q] / std::max(hf[q], 1e-300)));
+      if (worst <= h->opt.refine_tol) break;
+      axpy2(h->st, M, s, -2.0, r, M, r, M);            // r = f - A c
+    }
+    h->iters = std::min(it, std::max(1, h->opt.refine_max));
+    h->relres = worst;
+  }
+  h->scr.release(mk);
+}
+
+nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
+                               void* stream) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr, ST_ESTATE, "solve: no handle");
+    NH_REQUIRE(h->factored, ST_ESTATE, "solve before factor");
+    NH_REQUIRE(nrhs >= 0 && d_f && d_c && ldf >= h->M && ldc >= h->N, ST_EINVAL, "solve: bad arguments");
+    (void)stream;
+    if (nrhs == 0) return;
+    const double t0 = now_ms();
+    do_solve(h, (const double2*)d_f, ldf, nrhs, (double2*)d_c, ldc);
+    NH_CK(cudaStreamSynchronize(h->st));
+    h->t_solve = now_ms() - t0;
+  });
+}
+
+nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t ldi, int nrhs, void* d_out,
+                               int64_t ldo, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr, ST_ESTATE, "apply: no handle");
+    NH_REQUIRE(nrhs >= 0 && d_in && d_out, ST_EINVAL, "apply: bad arguments");
+    (void)stream;
+    if (nrhs == 0) return;
+    const int M = h->M, N = h->N;
+    switch (op) {
+      case NUDFT2_EXACT_FWD:
+        NH_REQUIRE(ldi >= N && ldo >= M, ST_EINVAL, "apply: leading dimension too small");
+        exact_fwd(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
+        break;
+      case NUDFT2_EXACT_ADJ:
+        NH_REQUIRE(ldi >= M && ldo >= N, ST_EINVAL, "apply: leading dimension too small");
+        exact_adj(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
+        break;
+      case NUDFT2_PINV:
+        NH_REQUIRE(h->factored, ST_ESTATE, "apply PINV before factor");
+        NH_REQUIRE(ldi >= M && ldo >= N, ST_EINVAL, "apply: leading dimension too small");
+        do_solve(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
+        break;
+      case NUDFT2_FAST_FWD: {
+        NH_REQUIRE(ldi >= N && ldo >= M, ST_EINVAL, "apply: leading dimension too small");
+        auto mk = h->scr.mark();
+        double2* y = h->scr.arr<double2>((size_t)N * nrhs);
+        dft2(h, (const double2*)d_in, ldi, nrhs, y, N, false);
+        if (h->h64) {
+          double2* yt = h->scr.arr<double2>((size_t)N * nrhs);
+          double2* o2 = h->scr.arr<double2>((size_t)M * nrhs);
+          convert_gather<double, double>(h->st, y, N, h->pl.colmap, N, nrhs, yt, N, 1.0);
+          h->h64->matvec(yt, N, nrhs, o2, M);
+          convert_scatter<double, double>(h->st, o2, M, h->pl.perm2, M, nrhs, (double2*)d_out, (int)ldo, 1.0);
+        } else {
+          float2* yt = h->scr.arr<float2>((size_t)N * nrhs);
+          float2* o2 = h->scr.arr<float2>((size_t)M * nrhs);
+          convert_gather<double, float>(h->st, y, N, h->pl.colmap, N, nrhs, yt, N, 1.0);
+          h->h32->matvec(yt, N, nrhs, o2, M);
+          convert_scatter<float, double>(h->st, o2, M, h->pl.perm2, M, nrhs, (double2*)d_out, (int)ldo, 1.0);
+        }
+        h->scr.release(mk);
+        break;
+      }
+      case NUDFT2_FAST_ADJ:
+      case NUDFT2_PINV_ADJ:
+        throw Error(ST_ENOTIMPL, "apply: operator not available in this build");
+      default:
+        throw Error(ST_EINVAL, "apply: unknown operator");
+    }
+    NH_CK(cudaStreamSynchronize(h->st));
+  });
+}
+
+nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info) {
+  return guard([&] {
+    NH_REQUIRE(h && info, ST_EINVAL, "info: NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->M = h->M; info->nx = h->nx; info->ny = h->ny; info->levels = h->L; info->prec = h->opt.prec;
+    std::vector<int> lr = h->h64 ? h->h64->level_ranks() : h->h32->level_ranks();
+    info->max_rank = h->h64 ? h->h64->max_rank() : h->h32->max_rank();
+    for (size_t i = 0; i < lr.size() && i < 16; ++i) info->level_rank[i] = lr[i];
+    info->t_build_ms = h->t_build;
+    info->t_factor_ms = h->t_factor;
+    info->t_solve_ms = h->t_solve;
+    info->refine_iters = h->iters;
+    info->refine_relres = h->relres;
+    info->device_bytes = h->keep.reserved() + h->scr.reserved() + (h->h64 ? h->h64->bytes() : h->h32->bytes());
+    info->launches = h->ops->launches() + (h->h64 ? h->h64->ops().launches() : h->h32->ops().launches());
+  });
+}
+
+void nudft2_hss_free(nudft2_hss_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+}  // extern "C"

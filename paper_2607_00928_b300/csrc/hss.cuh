@@ -1,0 +1,100 @@
+// HSS construction (1D compression, face-splitting assembly, recompression), URV
+// factorization and URV solve for the transformed 2D NUDFT matrix G~ = A F^{-1}.
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "la.cuh"
+#include "nudft.cuh"
+
+namespace nh {
+
+// ---------------------------------------------------------------- trees and point order
+// Equal-depth 1D binary trees T^x, T^y over the column index sets (bisection of the periodic
+// interval, Sec. 2.4) and their face-splitting product, the quadtree T = T^x . T^y
+// (Def. 3.3); nodes of level l are numbered in Morton order, child c = 2*bx + by of node p
+// is 4p + c (children order (1,1),(1,2),(2,1),(2,2) of the proof of Thm. 3.5).
+struct Tree1D {
+  int n = 0, L = 0;
+  std::vector<std::vector<int>> c0, c1;   // column range of node (l, i)
+  std::vector<std::vector<int>> r0, m;    // row range in this dimension's sorted point order
+  std::vector<int> leaf_of_col;           // column -> leaf index
+};
+
+struct Plan {
+  int M = 0, nx = 0, ny = 0, L = 0, N = 0;
+  Tree1D tx, ty;
+  // 2D: per level l, per node p: rows [r0, r0+m) in 2D order, columns [c0, c0+nc) in tree order
+  std::vector<std::vector<int>> r0, m, c0, nc;
+  std::vector<int> leaf_lx, leaf_ly;      // per leaf p: 1D leaf indices
+  // device arrays (owned by the handle's persistent arena)
+  double *x = nullptr, *y = nullptr;      // caller order
+  double *x2 = nullptr, *y2 = nullptr;    // 2D leaf order
+  double *xo = nullptr, *yo = nullptr;    // x-bin order / y-bin order
+  int *perm2 = nullptr;                   // 2D position -> caller index
+  int *posx = nullptr, *posy = nullptr;   // 2D position -> position in x-order / y-order
+  int *colmap = nullptr;                  // tree column -> lexicographic (kx*ny + ky)
+};
+
+// Build the plan: bins points on the device, sorts them (stable counting sort) into the
+// three orders and reads the per-bin counts back to size the trees.
+void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, const double* d_y, int M, int nx, int ny,
+               int L, Plan& pl);
+
+// ---------------------------------------------------------------- HSS generators and URV factors
+template <typename R> struct Gen1D {    // one node of a 1D HSS (Sec. 2.2, Def. 2.2)
+  int ru = 0, rv = 0;
+  Mat<R> U, V, P, R_, W, Bs, Rst, Wst;  // U leaf; V explicit; P = U^* G(J,:); R_,W transfer; Bs = B_{this,sibling}
+};
+
+template <typename R> struct Node2 {
+  int ku = 0, kv = 0;                   // basis sizes (ranks after recompression)
+  Mat<R> D, U, V;                       // leaf generators
+  Mat<R> R_, W;                         // transfer to the parent
+  Mat<R> B[4];                          // B_{this, sibling c'}; B[self] unused
+  // recompression temporaries
+  Mat<R> F, G;
+  int pu = 0, pv = 0;
+  std::vector<double> SU, SV;
+  // URV factor (Sec. 2.3)
+  bool omega = false;
+  QFac<R> Om, Qv, P;
+  int m = 0, n = 0, mc = 0, n1 = 0, rows2 = 0;
+  Mat<R> Wk;                            // [U D] working matrix after factorization
+  Mat<R> D11inv, V2;
+};
+
+template <typename R> class Hss {
+ public:
+  Hss(cudaStream_t st, const Plan* pl);
+  void build(double eps);
+  void factor();
+  // y (N x s, tree column order) = G~_hss^+ f (f: M x s in 2D row order); both device
+  void solve(const cplx<R>* f2, int ldf, int s, cplx<R>* ytree, int ldy);
+  // y = G~_hss x (x: N x s tree order, y: M x s 2D order): the HSS matrix-vector product
+  void matvec(const cplx<R>* x, int ldx, int s, cplx<R>* y, int ldy);
+  int max_rank() const;
+  std::vector<int> level_ranks() const;
+  size_t bytes() const { return keep_.reserved(); }
+  Ops<R>& ops() { return ops_; }
+  bool factored = false;
+
+ private:
+  void build_1d(const Tree1D& t, const double* xo, double eps, std::vector<std::vector<Gen1D<R>>>& g,
+                Mat<R>& G);
+  void assemble_2d();
+  void recompress(double eps);
+  cudaStream_t st_;
+  const Plan* pl_;
+  Arena keep_, scr_, tmp_;
+  Ops<R> ops_;
+  std::vector<std::vector<Gen1D<R>>> gx_, gy_;
+  Mat<R> Gx_, Gy_;
+  std::vector<std::vector<Node2<R>>> t_;
+  // root factor
+  QFac<R> Proot_;
+  Mat<R> Droot_, Rinv_;
+  int root_rows_ = 0, root_cols_ = 0;
+};
+
+}  // namespace nh

@@ -1,0 +1,933 @@
+// Batched complex dense linear algebra kernels (GEMM, Householder QR with compact-WY panel
+// factors, reflector application, triangular inverse, one-sided Jacobi SVD) and the small
+// data-movement kernels the HSS construction needs.  See la.cuh for the contracts.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "la.cuh"
+
+namespace nh {
+
+// =============================================================================== helpers
+template <typename R> __device__ __forceinline__ cplx<R> ld_op(const cplx<R>* p, int op) {
+  cplx<R> v = *p;
+  if (op == OP_C) v.y = -v.y;
+  return v;
+}
+
+// find problem by exclusive tile prefix (last i with pre[i] <= t)
+__device__ __forceinline__ int find_prob(const int* pre, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename R> template <typename D> D* Ops<R>::upload(const std::vector<D>& v) {
+  D* d = (D*)ar_->alloc(v.size() * sizeof(D));
+  NH_CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(D), cudaMemcpyHostToDevice, st_));
+  return d;
+}
+
+static int* upload_ints(Arena* ar, cudaStream_t st, const std::vector<int>& v) {
+  int* d = (int*)ar->alloc(v.size() * sizeof(int));
+  NH_CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+// =============================================================================== GEMM
+// C = alpha op(A) op(B) + beta C.  One CTA per BM x BN output tile of one problem; tiles of
+// all problems are numbered consecutively (exclusive prefix `pre`).
+template <typename R, int TM, int TN, int BK>
+__global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, const int* __restrict__ pre,
+                                              int np) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
+  __shared__ cplx<R> As[BK][BM + 1];
+  __shared__ cplx<R> Bs[BK][BN + 1];
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const GemmD<R> g = ds[pi];
+  const int lt = blockIdx.x - pre[pi];
+  const int tiles_m = (g.m + BM - 1) / BM;
+  const int row0 = (lt % tiles_m) * BM, col0 = (lt / tiles_m) * BN;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  cplx<R> acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = czero<R>();
+
+  for (int k0 = 0; k0 < g.k; k0 += BK) {
+    // A tile: op(A)(i, kk), i in [row0, row0+BM), kk in [k0, k0+BK)
+    for (int e = tid; e < BM * BK; e += 256) {
+      int ii, kk;
+      if (g.opA == OP_N) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
+      const int gi = row0 + ii, gk = k0 + kk;
+      cplx<R> v = czero<R>();
+      if (gi < g.m && gk < g.k) {
+        v = (g.opA == OP_N) ? g.A[(size_t)gi + (size_t)gk * g.lda]
+                            : ld_op<R>(g.A + (size_t)gk + (size_t)gi * g.lda, g.opA);
+      }
+      As[kk][ii] = v;
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      int jj, kk;
+      if (g.opB == OP_N) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
+      const int gj = col0 + jj, gk = k0 + kk;
+      cplx<R> v = czero<R>();
+      if (gj < g.n && gk < g.k) {
+        v = (g.opB == OP_N) ? g.B[(size_t)gk + (size_t)gj * g.ldb]
+                            : ld_op<R>(g.B + (size_t)gj + (size_t)gk * g.ldb, g.opB);
+      }
+      Bs[kk][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cplx<R> av[TM], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) cfma(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int i = row0 + ty + 16 * a;
+    if (i >= g.m) continue;
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int j = col0 + tx + 16 * b;
+      if (j >= g.n) continue;
+      cplx<R>* c = g.C + (size_t)i + (size_t)j * g.ldc;
+      cplx<R> v = g.alpha * acc[a][b];
+      if (g.beta != R(0)) v = v + g.beta * (*c);
+      *c = v;
+    }
+  }
+}
+
+template <typename R> struct GemmCfg;
+template <> struct GemmCfg<double> { static constexpr int TM = 2, TN = 2, BK = 16; };
+template <> struct GemmCfg<float> { static constexpr int TM = 4, TN = 4, BK = 16; };
+
+template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
+  constexpr int BM = 16 * GemmCfg<R>::TM, BN = 16 * GemmCfg<R>::TN;
+  std::vector<GemmD<R>> d;
+  d.reserve(d0.size());
+  std::vector<int> pre;
+  int tiles = 0;
+  for (const auto& g : d0) {
+    if (g.m <= 0 || g.n <= 0) continue;
+    if (g.k <= 0 && g.beta == R(1)) continue;
+    d.push_back(g);
+    pre.push_back(tiles);
+    tiles += ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
+  }
+  if (d.empty()) return;
+  GemmD<R>* dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+}
+
+// =============================================================================== copies
+template <typename R>
+__global__ void k_copy(const CopyD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const CopyD<R> c = ds[pi];
+  const int lt = blockIdx.x - pre[pi];
+  const int tm = (c.m + 31) / 32;
+  const int i0 = (lt % tm) * 32, j0 = (lt / tm) * 32;
+  __shared__ cplx<R> t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
+  if (c.op == OP_N) {
+    for (int jj = ty; jj < 32; jj += 8) {
+      const int i = i0 + tx, j = j0 + jj;
+      if (i < c.m && j < c.n) {
+        cplx<R> v = (c.rs ? c.alpha * c.rs[i] : c.alpha) * c.src[(size_t)i + (size_t)j * c.lds];
+        cplx<R>* o = c.dst + (size_t)i + (size_t)j * c.ldd;
+        if (c.beta != R(0)) v = v + c.beta * (*o);
+        *o = v;
+      }
+    }
+  } else {
+    // dst(i, j) = src(j, i) (conj): read src rows coalesced through shared memory
+    for (int ii = ty; ii < 32; ii += 8) {
+      const int j = j0 + tx, i = i0 + ii;     // src(j, i) at src[j + i*lds]
+      if (i < c.m && j < c.n) t[ii][tx] = ld_op<R>(c.src + (size_t)j + (size_t)i * c.lds, c.op);
+    }
+    __syncthreads();
+    for (int jj = ty; jj < 32; jj += 8) {
+      const int i = i0 + tx, j = j0 + jj;
+      if (i < c.m && j < c.n) {
+        cplx<R> v = (c.rs ? c.alpha * c.rs[i] : c.alpha) * t[tx][jj];
+        cplx<R>* o = c.dst + (size_t)i + (size_t)j * c.ldd;
+        if (c.beta != R(0)) v = v + c.beta * (*o);
+        *o = v;
+      }
+    }
+  }
+}
+
+template <typename R> void Ops<R>::copy(const std::vector<CopyD<R>>& d0) {
+  std::vector<CopyD<R>> d;
+  std::vector<int> pre;
+  int tiles = 0;
+  for (const auto& c : d0) {
+    if (c.m <= 0 || c.n <= 0) continue;
+    d.push_back(c);
+    pre.push_back(tiles);
+    tiles += ((c.m + 31) / 32) * ((c.n + 31) / 32);
+  }
+  if (d.empty()) return;
+  auto dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_copy<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+}
+
+// kron: grid over 32x32 tiles of the destination
+template <typename R>
+__global__ void k_kron(const KronD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const KronD<R> k = ds[pi];
+  const int lt = blockIdx.x - pre[pi];
+  const int M = k.ma * k.mb, N = k.na * k.nb;
+  const int tm = (M + 31) / 32;
+  const int i0 = (lt % tm) * 32, j0 = (lt / tm) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int r = i0 + tx, c = j0 + jj;
+    if (r >= M || c >= N) continue;
+    const int i = r / k.mb, kk = r % k.mb, j = c / k.nb, l = c % k.nb;
+    cplx<R> a = k.A ? k.A[(size_t)i + (size_t)j * k.lda] : mkc(R(i == j), R(0));
+    cplx<R> b = k.B ? k.B[(size_t)kk + (size_t)l * k.ldb] : mkc(R(kk == l), R(0));
+    k.dst[(size_t)r + (size_t)c * k.ldd] = k.alpha * (a * b);
+  }
+}
+
+template <typename R> void Ops<R>::kron(const std::vector<KronD<R>>& d0) {
+  std::vector<KronD<R>> d;
+  std::vector<int> pre;
+  int tiles = 0;
+  for (const auto& k : d0) {
+    const int M = k.ma * k.mb, N = k.na * k.nb;
+    if (M <= 0 || N <= 0) continue;
+    d.push_back(k);
+    pre.push_back(tiles);
+    tiles += ((M + 31) / 32) * ((N + 31) / 32);
+  }
+  if (d.empty()) return;
+  auto dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_kron<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+}
+
+template <typename R>
+__global__ void k_face(const FaceD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const FaceD<R> f = ds[pi];
+  const int lt = blockIdx.x - pre[pi];
+  const int N = f.na * f.nb;
+  const int tm = (f.m + 31) / 32;
+  const int i0 = (lt % tm) * 32, j0 = (lt / tm) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int r = i0 + tx, c = j0 + jj;
+    if (r >= f.m || c >= N) continue;
+    const int a = c / f.nb, s = c % f.nb;
+    f.dst[(size_t)r + (size_t)c * f.ldd] = f.A[(size_t)r + (size_t)a * f.lda] * f.B[(size_t)r + (size_t)s * f.ldb];
+  }
+}
+
+template <typename R> void Ops<R>::face(const std::vector<FaceD<R>>& d0) {
+  std::vector<FaceD<R>> d;
+  std::vector<int> pre;
+  int tiles = 0;
+  for (const auto& f : d0) {
+    const int N = f.na * f.nb;
+    if (f.m <= 0 || N <= 0) continue;
+    d.push_back(f);
+    pre.push_back(tiles);
+    tiles += ((f.m + 31) / 32) * ((N + 31) / 32);
+  }
+  if (d.empty()) return;
+  auto dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_face<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+}
+
+template <typename R>
+__global__ void k_gather(const GatherD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const GatherD<R> g = ds[pi];
+  const int lt = blockIdx.x - pre[pi];
+  const int tm = (g.m + 31) / 32;
+  const int i0 = (lt % tm) * 32, j0 = (lt / tm) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = i0 + tx;
+  if (i >= g.m) return;
+  const int si = g.idx[i] + g.base;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj;
+    if (j < g.n) g.dst[(size_t)i + (size_t)j * g.ldd] = g.src[(size_t)si + (size_t)j * g.lds];
+  }
+}
+
+template <typename R> void Ops<R>::gather(const std::vector<GatherD<R>>& d0) {
+  std::vector<GatherD<R>> d;
+  std::vector<int> pre;
+  int tiles = 0;
+  for (const auto& g : d0) {
+    if (g.m <= 0 || g.n <= 0) continue;
+    d.push_back(g);
+    pre.push_back(tiles);
+    tiles += ((g.m + 31) / 32) * ((g.n + 31) / 32);
+  }
+  if (d.empty()) return;
+  auto dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_gather<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+}
+
+template <typename R> __global__ void k_set_identity(const Mat<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const Mat<R> a = ds[pi];
+  const int lt = blockIdx.x - pre[pi];
+  const int tm = (a.m + 31) / 32;
+  const int i0 = (lt % tm) * 32, j0 = (lt / tm) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int i = i0 + tx, j = j0 + jj;
+    if (i < a.m && j < a.n) a.p[(size_t)i + (size_t)j * a.ld] = mkc(R(i == j), R(0));
+  }
+}
+
+template <typename R> void Ops<R>::set_identity(const std::vector<Mat<R>>& d0) {
+  std::vector<Mat<R>> d;
+  std::vector<int> pre;
+  int tiles = 0;
+  for (const auto& a : d0) {
+    if (a.m <= 0 || a.n <= 0) continue;
+    d.push_back(a);
+    pre.push_back(tiles);
+    tiles += ((a.m + 31) / 32) * ((a.n + 31) / 32);
+  }
+  if (d.empty()) return;
+  auto dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_set_identity<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+}
+
+// =============================================================================== Householder QR
+// Block reduction of a real value over 256 threads.
+template <typename R> __device__ R block_sum(R v, R* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  R t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : R(0);
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  R r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Factor panel columns [j0, j0+b) of every matrix; one CTA (256 threads) per matrix.
+// Reflector H = I - tau v v^*, v[0] = 1, tau = 2 / ||v||^2 real (Hermitian, unitary);
+// v = x + phase(x0) ||x|| e1 so H x = -phase(x0) ||x|| e1.  A zero column gets v = e1,
+// tau = 2.  The panel's compact-WY T (Q_p = I - V_p T V_p^*) is written to Tp.
+template <typename R>
+__global__ void __launch_bounds__(256) k_qr_panel(const QRD<R>* __restrict__ ds, int j0, int nb) {
+  const QRD<R> q = ds[blockIdx.x];
+  const int k = min(q.m, q.n);
+  if (j0 >= k) return;
+  const int b = min(nb, k - j0);
+  __shared__ R red[32];
+  __shared__ cplx<R> sv0;
+  __shared__ R stau;
+  __shared__ cplx<R> Ts[32][33];
+  __shared__ cplx<R> Ys[32][33];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int jj = 0; jj < b; ++jj) {
+    const int col = j0 + jj;
+    cplx<R>* x = q.A + (size_t)col * q.lda;
+    R s = 0;
+    for (int i = col + tid; i < q.m; i += 256) s += abs2(x[i]);
+    const R nrm2 = block_sum<R>(s, red);
+    if (tid == 0) {
+      const cplx<R> a0 = x[col];
+      const R nrm = sqrt(nrm2);
+      const R aa = sqrt(abs2(a0));
+      cplx<R> ph = aa > R(0) ? mkc(a0.x / aa, a0.y / aa) : mkc(R(1), R(0));
+      if (nrm == R(0)) {
+        sv0 = mkc(R(0), R(0));
+        stau = R(2);
+        x[col] = mkc(R(0), R(0));
+      } else {
+        const cplx<R> v0 = a0 + nrm * ph;           // = ph * (aa + nrm)
+        sv0 = v0;
+        const R v0a2 = abs2(v0);
+        const R vn2 = R(1) + (nrm2 - aa * aa) / v0a2;
+        stau = R(2) / vn2;
+        x[col] = mkc(-nrm * ph.x, -nrm * ph.y);
+      }
+      q.tau[col] = stau;
+      q.V[(size_t)col + (size_t)col * q.ldv] = mkc(R(1), R(0));
+    }
+    __syncthreads();
+    const cplx<R> v0 = sv0;
+    const R v0a2 = abs2(v0);
+    cplx<R>* vcol = q.V + (size_t)col * q.ldv;
+    for (int i = col + 1 + tid; i < q.m; i += 256) {
+      cplx<R> xv = x[i];
+      cplx<R> v = (v0a2 > R(0)) ? mkc((xv.x * v0.x + xv.y * v0.y) / v0a2, (xv.y * v0.x - xv.x * v0.y) / v0a2)
+                                : mkc(R(0), R(0));
+      vcol[i] = v;
+      x[i] = mkc(R(0), R(0));
+    }
+    __syncthreads();
+    const R tau = stau;
+    // apply H to the remaining panel columns: one warp per column
+    for (int c = col + 1 + warp; c < j0 + b; c += 8) {
+      cplx<R>* y = q.A + (size_t)c * q.lda;
+      cplx<R> w = czero<R>();
+      for (int i = col + lane; i < q.m; i += 32) cfmac(w, vcol[i], y[i]);
+      w.x = warp_sum(w.x);
+      w.y = warp_sum(w.y);
+      w = tau * w;
+      for (int i = col + lane; i < q.m; i += 32) {
+        cplx<R> v = vcol[i];
+        y[i] = y[i] - v * w;
+      }
+    }
+    __syncthreads();
+  }
+  // Y = V_p^* V_p (strict upper part) over rows [j0, m)
+  for (int p = warp; p < b * b; p += 8) {
+    const int i = p / b, j = p % b;
+    if (i >= j) continue;
+    const cplx<R>* vi = q.V + (size_t)(j0 + i) * q.ldv;
+    const cplx<R>* vj = q.V + (size_t)(j0 + j) * q.ldv;
+    cplx<R> w = czero<R>();
+    for (int r = j0 + j + lane; r < q.m; r += 32) cfmac(w, vi[r], vj[r]);   // v_j zero above j0+j
+    w.x = warp_sum(w.x);
+    w.y = warp_sum(w.y);
+    if (lane == 0) Ys[i][j] = w;
+  }
+  for (int e = tid; e < 32 * 33; e += 256) Ts[e / 33][e % 33] = czero<R>();
+  __syncthreads();
+  // T(j,j) = tau_j ; T(0:j, j) = -tau_j T(0:j,0:j) Y(0:j, j)
+  for (int j = 0; j < b; ++j) {
+    const R tj = q.tau[j0 + j];
+    if (tid < j) {
+      cplx<R> acc = czero<R>();
+      for (int l = tid; l < j; ++l) cfma(acc, Ts[tid][l], Ys[l][j]);
+      Ts[tid][j] = (-tj) * acc;
+    }
+    if (tid == 0) Ts[j][j] = mkc(tj, R(0));
+    __syncthreads();
+  }
+  cplx<R>* Tp = q.Tp + (size_t)(j0 / nb) * nb * nb;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    Tp[e] = (i < b && j < b) ? Ts[i][j] : czero<R>();
+  }
+}
+
+template <typename R>
+std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
+  std::vector<QFac<R>> out(A.size());
+  std::vector<QRD<R>> d(A.size());
+  int kmax = 0;
+  auto mk = ar_->mark();
+  for (size_t i = 0; i < A.size(); ++i) {
+    const Mat<R>& a = A[i];
+    const int k = std::min(a.m, a.n);
+    QFac<R>& f = out[i];
+    f.m = a.m; f.k = k;
+    f.ldv = std::max(a.m, 1);
+    if (k > 0) {
+      f.V = (cplx<R>*)keep.alloc((size_t)f.ldv * k * sizeof(cplx<R>));
+      NH_CK(cudaMemsetAsync(f.V, 0, (size_t)f.ldv * k * sizeof(cplx<R>), st_));
+      const int np = (k + NB - 1) / NB;
+      f.Tp = (cplx<R>*)keep.alloc((size_t)np * NB * NB * sizeof(cplx<R>));
+    }
+    QRD<R>& q = d[i];
+    q.A = a.p; q.lda = a.ld; q.m = a.m; q.n = a.n;
+    q.V = f.V; q.ldv = f.ldv;
+    q.tau = (R*)ar_->alloc(std::max(k, 1) * sizeof(R));
+    q.Tp = f.Tp;
+    q.W = (cplx<R>*)ar_->alloc((size_t)2 * NB * std::max(a.n, 1) * sizeof(cplx<R>));
+    kmax = std::max(kmax, k);
+  }
+  if (kmax == 0) { ar_->release(mk); return out; }
+  QRD<R>* dd = upload(d);
+  for (int j0 = 0; j0 < kmax; j0 += NB) {
+    k_qr_panel<R><<<(int)d.size(), 256, 0, st_>>>(dd, j0, NB);
+    NH_LAUNCH_CK();
+    count();
+    // trailing update A2 <- Q_p^* A2 = A2 - V_p T_p^* (V_p^* A2)
+    std::vector<GemmD<R>> g1, g2, g3;
+    for (size_t i = 0; i < d.size(); ++i) {
+      const QRD<R>& q = d[i];
+      const int k = std::min(q.m, q.n);
+      if (j0 >= k) continue;
+      const int b = std::min(NB, k - j0);
+      const int n2 = q.n - j0 - b;
+      if (n2 <= 0) continue;
+      const int mm = q.m - j0;
+      cplx<R>* Vp = q.V + (size_t)j0 + (size_t)j0 * q.ldv;
+      cplx<R>* A2 = q.A + (size_t)j0 + (size_t)(j0 + b) * q.lda;
+      cplx<R>* W1 = q.W;
+      cplx<R>* W2 = q.W + (size_t)NB * std::max(q.n, 1);
+      cplx<R>* Tp = q.Tp + (size_t)(j0 / NB) * NB * NB;
+      g1.push_back({Vp, A2, W1, b, n2, mm, q.ldv, q.lda, NB, OP_C, OP_N, R(1), R(0)});
+      g2.push_back({Tp, W1, W2, b, n2, b, NB, NB, NB, OP_C, OP_N, R(1), R(0)});
+      g3.push_back({Vp, W2, A2, mm, n2, b, q.ldv, NB, q.lda, OP_N, OP_N, R(-1), R(1)});
+    }
+    gemm(g1);
+    gemm(g2);
+    gemm(g3);
+  }
+  ar_->release(mk);
+  return out;
+}
+
+template <typename R>
+void Ops<R>::apply_q_left(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj) {
+  // Q = Q_0 Q_1 ... (panels); Q^* C applies panels in increasing order, Q C in decreasing order.
+  int pmax = 0;
+  for (auto& q : Q) pmax = std::max(pmax, (q.k + NB - 1) / NB);
+  if (pmax == 0) return;
+  auto mk = ar_->mark();
+  std::vector<cplx<R>*> W1(Q.size()), W2(Q.size());
+  for (size_t i = 0; i < Q.size(); ++i) {
+    W1[i] = (cplx<R>*)ar_->alloc((size_t)NB * std::max(C[i].n, 1) * sizeof(cplx<R>));
+    W2[i] = (cplx<R>*)ar_->alloc((size_t)NB * std::max(C[i].n, 1) * sizeof(cplx<R>));
+  }
+  for (int s = 0; s < pmax; ++s) {
+    std::vector<GemmD<R>> g1, g2, g3;
+    for (size_t i = 0; i < Q.size(); ++i) {
+      const QFac<R>& q = Q[i];
+      const int np = (q.k + NB - 1) / NB;
+      if (s >= np || C[i].n <= 0) continue;
+      const int p = conj ? s : (np - 1 - s);
+      const int j0 = p * NB, b = std::min(NB, q.k - j0), mm = q.m - j0;
+      const cplx<R>* Vp = q.V + (size_t)j0 + (size_t)j0 * q.ldv;
+      const cplx<R>* Tp = q.Tp + (size_t)p * NB * NB;
+      cplx<R>* Cp = C[i].p + j0;
+      g1.push_back({Vp, Cp, W1[i], b, C[i].n, mm, q.ldv, C[i].ld, NB, OP_C, OP_N, R(1), R(0)});
+      g2.push_back({Tp, W1[i], W2[i], b, C[i].n, b, NB, NB, NB, conj ? OP_C : OP_N, OP_N, R(1), R(0)});
+      g3.push_back({Vp, W2[i], Cp, mm, C[i].n, b, q.ldv, NB, C[i].ld, OP_N, OP_N, R(-1), R(1)});
+    }
+    gemm(g1);
+    gemm(g2);
+    gemm(g3);
+  }
+  ar_->release(mk);
+}
+
+template <typename R>
+void Ops<R>::apply_q_right(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj) {
+  // C Q = C - (C V) T V^* per panel, panels in increasing order; C Q^* in decreasing order.
+  int pmax = 0;
+  for (auto& q : Q) pmax = std::max(pmax, (q.k + NB - 1) / NB);
+  if (pmax == 0) return;
+  auto mk = ar_->mark();
+  std::vector<cplx<R>*> W1(Q.size()), W2(Q.size());
+  for (size_t i = 0; i < Q.size(); ++i) {
+    const int ld = std::max(C[i].m, 1);
+    W1[i] = (cplx<R>*)ar_->alloc((size_t)ld * NB * sizeof(cplx<R>));
+    W2[i] = (cplx<R>*)ar_->alloc((size_t)ld * NB * sizeof(cplx<R>));
+  }
+  for (int s = 0; s < pmax; ++s) {
+    std::vector<GemmD<R>> g1, g2, g3;
+    for (size_t i = 0; i < Q.size(); ++i) {
+      const QFac<R>& q = Q[i];
+      const int np = (q.k + NB - 1) / NB;
+      if (s >= np || C[i].m <= 0) continue;
+      const int p = conj ? (np - 1 - s) : s;
+      const int j0 = p * NB, b = std::min(NB, q.k - j0), nn = q.m - j0;
+      const int ld = std::max(C[i].m, 1);
+      const cplx<R>* Vp = q.V + (size_t)j0 + (size_t)j0 * q.ldv;
+      const cplx<R>* Tp = q.Tp + (size_t)p * NB * NB;
+      cplx<R>* Cp = C[i].p + (size_t)j0 * C[i].ld;   // columns j0.. of C
+      g1.push_back({Cp, Vp, W1[i], C[i].m, b, nn, C[i].ld, q.ldv, ld, OP_N, OP_N, R(1), R(0)});
+      g2.push_back({W1[i], Tp, W2[i], C[i].m, b, b, ld, NB, ld, OP_N, conj ? OP_C : OP_N, R(1), R(0)});
+      g3.push_back({W2[i], Vp, Cp, C[i].m, nn, b, ld, q.ldv, C[i].ld, OP_N, OP_C, R(-1), R(1)});
+    }
+    gemm(g1);
+    gemm(g2);
+    gemm(g3);
+  }
+  ar_->release(mk);
+}
+
+// =============================================================================== triangular inverse
+// Invert 32x32 diagonal blocks of upper-triangular matrices: one CTA (32 threads x 32) per block.
+template <typename R> struct TriD { const cplx<R>* A; cplx<R>* X; int n, lda, ldx; };
+
+template <typename R>
+__global__ void k_trinv_diag(const TriD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const TriD<R> t = ds[pi];
+  const int blk = blockIdx.x - pre[pi];
+  const int o = blk * 32, b = min(32, t.n - o);
+  __shared__ cplx<R> U[32][33];
+  __shared__ cplx<R> X[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    U[tx][j] = (tx < b && j < b && tx <= j) ? t.A[(size_t)(o + tx) + (size_t)(o + j) * t.lda] : czero<R>();
+    X[tx][j] = czero<R>();
+  }
+  __syncthreads();
+  // column j of X solves U x = e_j by back substitution; thread tx owns column tx
+  if (ty == 0 && tx < b) {
+    const int j = tx;
+    for (int i = j; i >= 0; --i) {
+      cplx<R> s = (i == j) ? mkc(R(1), R(0)) : czero<R>();
+      for (int l = i + 1; l <= j; ++l) s = s - U[i][l] * X[l][j];
+      const cplx<R> d = U[i][i];
+      const R dd = abs2(d);
+      X[i][j] = mkc((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+    }
+  }
+  __syncthreads();
+  for (int j = ty; j < b; j += 8)
+    if (tx < b) t.X[(size_t)(o + tx) + (size_t)(o + j) * t.ldx] = X[tx][j];
+}
+
+template <typename R>
+void Ops<R>::trinv(const std::vector<Mat<R>>& A, const std::vector<Mat<R>>& X) {
+  std::vector<TriD<R>> d;
+  std::vector<int> pre;
+  int blocks = 0, nmax = 0;
+  std::vector<Mat<R>> Xz;
+  for (size_t i = 0; i < A.size(); ++i) {
+    if (A[i].n <= 0) continue;
+    d.push_back({A[i].p, X[i].p, A[i].n, A[i].ld, X[i].ld});
+    pre.push_back(blocks);
+    blocks += (A[i].n + 31) / 32;
+    nmax = std::max(nmax, A[i].n);
+    NH_CK(cudaMemset2DAsync(X[i].p, (size_t)X[i].ld * sizeof(cplx<R>), 0, (size_t)A[i].n * sizeof(cplx<R>),
+                            A[i].n, st_));
+  }
+  if (d.empty()) return;
+  auto mk = ar_->mark();
+  auto dd = upload(d);
+  int* dp = upload_ints(ar_, st_, pre);
+  k_trinv_diag<R><<<blocks, 256, 0, st_>>>(dd, dp, (int)d.size());
+  NH_LAUNCH_CK();
+  count();
+  // doubling: blocks of size s are inverted; combine pairs into 2s:
+  //   X12 = -X11 A12 X22
+  for (int s = 32; s < nmax; s *= 2) {
+    std::vector<GemmD<R>> g1, g2;
+    std::vector<cplx<R>*> tmp;
+    for (auto& t : d) {
+      for (int o = 0; o + s < t.n; o += 2 * s) {
+        const int n1 = s, n2 = std::min(s, t.n - o - s);
+        cplx<R>* W = (cplx<R>*)ar_->alloc((size_t)n1 * n2 * sizeof(cplx<R>));
+        const cplx<R>* A12 = t.A + (size_t)o + (size_t)(o + s) * t.lda;
+        const cplx<R>* X22 = t.X + (size_t)(o + s) + (size_t)(o + s) * t.ldx;
+        const cplx<R>* X11 = t.X + (size_t)o + (size_t)o * t.ldx;
+        cplx<R>* X12 = t.X + (size_t)o + (size_t)(o + s) * t.ldx;
+        g1.push_back({A12, X22, W, n1, n2, n2, t.lda, t.ldx, n1, OP_N, OP_N, R(1), R(0)});
+        g2.push_back({X11, W, X12, n1, n2, n1, t.ldx, n1, t.ldx, OP_N, OP_N, R(-1), R(0)});
+      }
+    }
+    gemm(g1);
+    gemm(g2);
+  }
+  ar_->release(mk);
+}
+
+// =============================================================================== Jacobi SVD
+// One-sided (Hestenes) Jacobi on the columns of X (r x k), block-pair cyclic ordering:
+// columns are split into blocks of 16; each launch is one round of a round-robin
+// tournament over blocks; a CTA takes one block pair and sweeps all 32-choose-2 column
+// pairs of it (16 warps, one column pair per warp per inner round).
+template <typename R> struct JacD {
+  cplx<R>* X; int ld, r, k, nblk;   // nblk even
+  unsigned* off;                    // max |gamma|/sqrt(alpha beta) of this sweep (float bits)
+  const int* done;                  // converged flag from the previous sweep
+};
+
+__device__ __forceinline__ void rr_pair(int p, int r, int n, int& a, int& b) {
+  // circle method for n (even) players: player 0 fixed
+  if (p == 0) { a = 0; b = 1 + (r % (n - 1)); }
+  else { a = 1 + (r + p) % (n - 1); b = 1 + (r - p + n - 1) % (n - 1); }
+}
+
+template <typename R>
+__device__ void jac_rotate(cplx<R>* xa, cplx<R>* xb, int r, R tol, unsigned* off) {
+  const int lane = threadIdx.x & 31;
+  R al = 0, be = 0;
+  cplx<R> ga = czero<R>();
+  for (int i = lane; i < r; i += 32) {
+    const cplx<R> a = xa[i], b = xb[i];
+    al += abs2(a);
+    be += abs2(b);
+    cfmac(ga, a, b);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga.x = warp_sum(ga.x);
+  ga.y = warp_sum(ga.y);
+  const R g = sqrt(abs2(ga));
+  if (!(al > R(0)) || !(be > R(0)) || g == R(0)) return;
+  const R rel = g / sqrt(al * be);
+  if (lane == 0) atomicMax(off, __float_as_uint((float)rel));
+  if (rel <= tol) return;
+  const R zeta = (be - al) / (R(2) * g);
+  const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+  const R c = R(1) / sqrt(R(1) + t * t);
+  const R s = c * t;
+  const cplx<R> e = mkc(ga.x / g, ga.y / g);       // phase of gamma
+  const cplx<R> se = mkc(s * e.x, s * e.y);
+  const cplx<R> sec = mkc(s * e.x, -s * e.y);
+  for (int i = lane; i < r; i += 32) {
+    const cplx<R> a = xa[i], b = xb[i];
+    xa[i] = c * a - sec * b;
+    xb[i] = se * a + c * b;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_jacobi_round(const JacD<R>* __restrict__ ds, int round, R tol) {
+  const JacD<R> d = ds[blockIdx.y];
+  if (*d.done) return;
+  if (round >= d.nblk - 1 || (int)blockIdx.x >= d.nblk / 2) return;
+  int I, J;
+  rr_pair(blockIdx.x, round, d.nblk, I, J);
+  __shared__ int cidx[32];
+  __shared__ int nc;
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int q = 0; q < 2; ++q) {
+      const int B = q ? J : I;
+      for (int j = B * 16; j < min(B * 16 + 16, d.k); ++j) cidx[c++] = j;
+    }
+    nc = c;
+  }
+  __syncthreads();
+  const int n = nc;
+  if (n < 2) return;
+  const int warp = threadIdx.x >> 5;
+  // inner round-robin over 32 slots (empty slots skipped)
+  for (int ir = 0; ir < 31; ++ir) {
+    int a, b;
+    rr_pair(warp, ir, 32, a, b);
+    if (a < n && b < n) {
+      const int ca = min(cidx[a], cidx[b]), cb = max(cidx[a], cidx[b]);
+      jac_rotate<R>(d.X + (size_t)ca * d.ld, d.X + (size_t)cb * d.ld, d.r, tol, d.off);
+    }
+    __syncthreads();
+  }
+}
+
+// sigma_j = ||x_j||; rank positions by counting (descending, ties by index); count retained.
+template <typename R> struct SortD {
+  const cplx<R>* X; int ld, r, k;
+  R* sig;       // k: sorted descending
+  int* order;   // k: column index of the i-th largest
+  int* rank;    // out: number with sigma > eps * sigma_max
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_svd_sort(const SortD<R>* __restrict__ ds, R eps) {
+  const SortD<R> d = ds[blockIdx.x];
+  extern __shared__ unsigned char smraw[];
+  R* s = (R*)smraw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < d.k; j += 8) {
+    R acc = 0;
+    for (int i = lane; i < d.r; i += 32) acc += abs2(d.X[(size_t)i + (size_t)j * d.ld]);
+    acc = warp_sum(acc);
+    if (lane == 0) s[j] = sqrt(acc);
+  }
+  __syncthreads();
+  R smax = 0;
+  for (int j = 0; j < d.k; ++j) smax = fmax(smax, s[j]);
+  int cnt = 0;
+  for (int j = threadIdx.x; j < d.k; j += 256) {
+    const R v = s[j];
+    int pos = 0;
+    for (int l = 0; l < d.k; ++l) {
+      const R w = s[l];
+      pos += (w > v) || (w == v && l < j);
+    }
+    d.sig[pos] = v;
+    d.order[pos] = j;
+    cnt += (v > eps * smax && v > R(0));
+  }
+  __shared__ int tot;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  atomicAdd(&tot, cnt);
+  __syncthreads();
+  if (threadIdx.x == 0) *d.rank = tot;
+}
+
+// P(:, i) = X(:, order[i]) / sig[i], i < rank
+template <typename R> struct SelD { const cplx<R>* X; int ld, r; const R* sig; const int* order; cplx<R>* P; int ldp, rank; };
+
+template <typename R> __global__ void k_svd_select(const SelD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
+  const int pi = find_prob(pre, np, blockIdx.x);
+  const SelD<R> d = ds[pi];
+  const int i = blockIdx.x - pre[pi];   // one CTA per selected column
+  const int c = d.order[i];
+  const R inv = R(1) / d.sig[i];
+  for (int t = threadIdx.x; t < d.r; t += blockDim.x)
+    d.P[(size_t)t + (size_t)i * d.ldp] = inv * d.X[(size_t)t + (size_t)c * d.ld];
+}
+
+template <typename R>
+void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std::vector<Mat<R>>& P,
+                     std::vector<std::vector<double>>& S) {
+  const size_t nm = Ct.size();
+  P.assign(nm, Mat<R>());
+  S.assign(nm, {});
+  auto mk = ar_->mark();
+  // 1. QR of Ct (w x r) -> R factor (p x r), p = min(w, r)
+  Arena tmpk;
+  tmpk.set_stream(st_);
+  auto fac = qr(Ct, tmpk);
+  // 2. X = R^* (r x p), lower part of R ignored (k_qr zeroes it)
+  std::vector<Mat<R>> X(nm);
+  std::vector<CopyD<R>> cp;
+  for (size_t i = 0; i < nm; ++i) {
+    const int w = Ct[i].m, r = Ct[i].n, p = std::min(w, r);
+    X[i] = ar_->template mat<R>(r, p);
+    if (r > 0 && p > 0) cp.push_back({Ct[i].p, X[i].p, r, p, Ct[i].ld, X[i].ld, OP_C, R(1), R(0)});
+  }
+  copy(cp);
+  // 3. Jacobi sweeps
+  std::vector<JacD<R>> jd;
+  std::vector<int> jmap;
+  unsigned* offs = ar_->template arr<unsigned>(nm + 1);
+  int* done = ar_->template arr<int>(nm + 1, true);
+  int maxblk = 0;
+  for (size_t i = 0; i < nm; ++i) {
+    const int p = X[i].n;
+    if (p < 2 || X[i].m == 0) continue;
+    int nb = (p + 15) / 16;
+    if (nb < 2) nb = 2;
+    if (nb & 1) nb++;
+    jd.push_back({X[i].p, X[i].ld, X[i].m, p, nb, offs + i, done + i});
+    jmap.push_back((int)i);
+    maxblk = std::max(maxblk, nb);
+  }
+  const double u = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+  if (!jd.empty()) {
+    auto djd = upload(jd);
+    std::vector<unsigned> hoff(nm);
+    std::vector<int> hdone(nm, 0);
+    int rmax = 0;
+    for (auto& j : jd) rmax = std::max(rmax, j.r);
+    const R tol = (R)(4.0 * u * std::sqrt((double)std::max(rmax, 1)));
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      NH_CK(cudaMemsetAsync(offs, 0, nm * sizeof(unsigned), st_));
+      for (int rd = 0; rd < maxblk - 1; ++rd) {
+        dim3 grid(maxblk / 2, (unsigned)jd.size());
+        k_jacobi_round<R><<<grid, 512, 0, st_>>>(djd, rd, tol);
+        NH_LAUNCH_CK();
+        count();
+      }
+      NH_CK(cudaMemcpyAsync(hoff.data(), offs, nm * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
+      NH_CK(cudaStreamSynchronize(st_));
+      bool all = true;
+      for (size_t q = 0; q < jd.size(); ++q) {
+        const int i = jmap[q];
+        if (hdone[i]) continue;
+        float f;
+        std::memcpy(&f, &hoff[i], 4);
+        if ((double)f <= (double)tol) hdone[i] = 1; else all = false;
+      }
+      NH_CK(cudaMemcpyAsync(done, hdone.data(), nm * sizeof(int), cudaMemcpyHostToDevice, st_));
+      if (all) break;
+    }
+  }
+  // 4. sort + count
+  std::vector<SortD<R>> sd;
+  int* ranks = ar_->template arr<int>(nm + 1, true);
+  std::vector<R*> sig(nm, nullptr);
+  std::vector<int*> order(nm, nullptr);
+  int kmax = 1;
+  for (size_t i = 0; i < nm; ++i) {
+    const int p = X[i].n;
+    sig[i] = ar_->template arr<R>(std::max(p, 1));
+    order[i] = ar_->template arr<int>(std::max(p, 1));
+    if (p > 0 && X[i].m > 0) {
+      sd.push_back({X[i].p, X[i].ld, X[i].m, p, sig[i], order[i], ranks + i});
+      kmax = std::max(kmax, p);
+    }
+  }
+  if (!sd.empty()) {
+    auto dsd = upload(sd);
+    const size_t smem = (size_t)kmax * sizeof(R);
+    if (smem > 48 * 1024)
+      NH_CK(cudaFuncSetAttribute(k_svd_sort<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_svd_sort<R><<<(int)sd.size(), 256, smem, st_>>>(dsd, (R)eps);
+    NH_LAUNCH_CK();
+    count();
+  }
+  std::vector<int> hr(nm, 0);
+  NH_CK(cudaMemcpyAsync(hr.data(), ranks, nm * sizeof(int), cudaMemcpyDeviceToHost, st_));
+  NH_CK(cudaStreamSynchronize(st_));
+  // 5. select
+  std::vector<SelD<R>> sel;
+  std::vector<int> pre;
+  int tot = 0;
+  std::vector<std::vector<R>> hs(nm);
+  for (size_t i = 0; i < nm; ++i) {
+    const int r = X[i].m;
+    const int rk = (X[i].n > 0 && r > 0) ? hr[i] : 0;
+    P[i] = keep.template mat<R>(r, rk);
+    if (rk > 0) {
+      sel.push_back({X[i].p, X[i].ld, r, sig[i], order[i], P[i].p, P[i].ld, rk});
+      pre.push_back(tot);
+      tot += rk;
+      hs[i].resize(rk);
+      NH_CK(cudaMemcpyAsync(hs[i].data(), sig[i], rk * sizeof(R), cudaMemcpyDeviceToHost, st_));
+    }
+  }
+  if (!sel.empty()) {
+    auto dsel = upload(sel);
+    int* dp = upload_ints(ar_, st_, pre);
+    k_svd_select<R><<<tot, 256, 0, st_>>>(dsel, dp, (int)sel.size());
+    NH_LAUNCH_CK();
+    count();
+  }
+  NH_CK(cudaStreamSynchronize(st_));
+  for (size_t i = 0; i < nm; ++i) S[i].assign(hs[i].begin(), hs[i].end());
+  tmpk.free_all();
+  ar_->release(mk);
+}
+
+template class Ops<double>;
+template class Ops<float>;
+
+}  // namespace nh

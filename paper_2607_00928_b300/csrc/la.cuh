@@ -1,0 +1,106 @@
+// Batched complex dense linear algebra on variable-size problems.
+//
+// Every routine takes a host vector of descriptors (one per independent problem), uploads
+// it, and covers the whole batch with ONE launch per algorithmic step, so each tree level
+// of the HSS algorithms costs a fixed number of launches regardless of how many nodes it
+// has.  Matrices are column major complex (double2 / float2).
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+namespace nh {
+
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2 };
+
+template <typename R> struct GemmD {
+  const cplx<R>* A; const cplx<R>* B; cplx<R>* C;
+  int m, n, k, lda, ldb, ldc;
+  int opA, opB;
+  R alpha, beta;
+};
+
+// dst(i,j) = alpha * rs[i] * op(src)(i,j) (+ beta * dst when beta != 0); op in {N, T, C};
+// rs == nullptr means no row scaling.
+template <typename R> struct CopyD {
+  const cplx<R>* src; cplx<R>* dst;
+  int m, n, lds, ldd, op;
+  R alpha, beta;
+  const R* rs = nullptr;
+};
+
+// dst block (ma*mb x na*nb) = alpha * kron(A, B); A == nullptr means the identity of size
+// ma (= na), likewise for B.  Entry ((i*mb + k), (j*nb + l)) = A(i,j) * B(k,l).
+template <typename R> struct KronD {
+  const cplx<R>* A; const cplx<R>* B; cplx<R>* dst;
+  int ma, na, lda, mb, nb, ldb, ldd;
+  R alpha;
+};
+
+// Row-wise Kronecker (face-splitting) product: dst(j, a*nb + s) = A(j, a) * B(j, s).
+template <typename R> struct FaceD {
+  const cplx<R>* A; const cplx<R>* B; cplx<R>* dst;
+  int m, na, nb, lda, ldb, ldd;
+};
+
+// dst(i, :) = src(idx[i] + base, :) for i < m, n columns.
+template <typename R> struct GatherD {
+  const cplx<R>* src; cplx<R>* dst; const int* idx;
+  int m, n, lds, ldd, base;
+};
+
+// In-place Householder QR of A (m x n).  Output: R in the upper trapezoid of A, explicit
+// unit-lower-trapezoidal reflectors in V (m x min(m,n), caller zero-fills), real tau and
+// the per-panel compact-WY factors Tp (nb x nb for every panel, stacked by panel).
+template <typename R> struct QRD {
+  cplx<R>* A; int lda; int m, n;
+  cplx<R>* V; int ldv;
+  R* tau;
+  cplx<R>* Tp;   // ceil(k/nb) blocks of nb*nb
+  cplx<R>* W;    // scratch 2*nb x n
+};
+
+// A QR factor kept for later applications: Q = H_0 ... H_{k-1}, applied panel by panel.
+template <typename R> struct QFac {
+  cplx<R>* V = nullptr; int ldv = 1; int m = 0, k = 0;
+  cplx<R>* Tp = nullptr;
+};
+
+template <typename R> class Ops {
+ public:
+  explicit Ops(cudaStream_t s, Arena* scratch) : st_(s), ar_(scratch) {}
+  cudaStream_t stream() const { return st_; }
+  Arena* scratch() { return ar_; }
+  static constexpr int NB = 32;   // Householder panel width
+
+  void gemm(const std::vector<GemmD<R>>& d);
+  void copy(const std::vector<CopyD<R>>& d);
+  void kron(const std::vector<KronD<R>>& d);
+  void face(const std::vector<FaceD<R>>& d);
+  void gather(const std::vector<GatherD<R>>& d);
+  void set_identity(const std::vector<Mat<R>>& d);   // zero then unit diagonal
+  // Householder QR of every A in place; returns the stored factors (V, Tp from the arena `keep`).
+  std::vector<QFac<R>> qr(const std::vector<Mat<R>>& A, Arena& keep);
+  // C <- Q C (conj=false) or Q^* C (conj=true), from the left.  C has Q.m rows.
+  void apply_q_left(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
+  // C <- C Q (conj=false) or C Q^*, from the right.  C has Q.m columns.
+  void apply_q_right(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
+  // X <- inverse of the upper triangle of A (square); X must not alias A.
+  void trinv(const std::vector<Mat<R>>& A, const std::vector<Mat<R>>& X);
+  // Truncated SVD through the conjugate transpose Ct = C^* (w x r) of each C (r x w).
+  // Ct is overwritten.  Returns left singular vectors P (r x rank) allocated from `keep`
+  // and the retained singular values (rank, host copy) with sigma_i > eps * sigma_1.
+  void tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep,
+               std::vector<Mat<R>>& P, std::vector<std::vector<double>>& S);
+
+  int launches() const { return launches_; }
+  void count(int n = 1) { launches_ += n; }
+
+ private:
+  template <typename D> D* upload(const std::vector<D>& v);
+  cudaStream_t st_;
+  Arena* ar_;
+  int launches_ = 0;
+};
+
+}  // namespace nh

@@ -1,0 +1,51 @@
+// NUDFT-specific kernels: kernel-entry evaluation of the transformed 1D matrices, twiddle
+// tables for the exact apply, point binning (stable counting sort) and DFT matrices.
+#pragma once
+#include "la.cuh"
+
+namespace nh {
+
+// out(i, k) = Psi(x[idx ? idx[i] : i], k0 + k; n), i < m, k < nk.
+// Psi(gamma, xi) = (1/n) sum_l (gamma/xi)^l = exp(-i pi (n-1) t) sin(pi n t) / (n sin(pi t)),
+// t = x - k/n reduced to [-1/2, 1/2); Psi = 1 at t = 0.
+template <typename R> struct PsiD {
+  const double* x; int m; int k0, nk, n; cplx<R>* out; int ld;
+};
+template <typename R> void psi_eval(Ops<R>& ops, const std::vector<PsiD<R>>& d);
+
+// tab(j, k) = exp(-2 pi i k x_j), j < M, k < n (FP64)
+void twiddle_table(cudaStream_t st, const double* x, int M, int n, double2* tab);
+// out_j(q) = sum_k A(j, k) T(j, k) for every column q of T (T has M rows, nk cols per column block)
+void rowdot(cudaStream_t st, const double2* A, int lda, const double2* T, int ldt, int M, int nk, int nrhs,
+            double2* out, int ldo);
+// Z(j, k) = f_j * conj(A(j, k)) for k < n
+void scale_rows_conj(cudaStream_t st, const double2* A, int lda, const double2* f, int M, int n, double2* Z,
+                     int ldz);
+void scale_rows_conj_multi(cudaStream_t st, const double2* A, int lda, const double2* f, int ldf, int M, int n,
+                           int nrhs, double2* Z, int ldz);
+// F(k, l) = exp(sign * 2 pi i k l / n) * scale, n x n
+template <typename R> void dft_matrix(cudaStream_t st, int n, int sign, double scale, cplx<R>* F);
+
+// Stable counting sort of keys[0..M) in [0, nkeys): perm[pos] = j, counts[key] (device).
+void counting_sort(cudaStream_t st, Arena& ar, const int* keys, int M, int nkeys, int* perm, int* counts);
+// keys: key2d (Morton leaf), keyx (x bin), keyy (y bin)
+void bin_points(cudaStream_t st, const double* x, const double* y, int M, int nx, int ny, const int* leafx,
+                const int* leafy, int L, int* key2d, int* keyx, int* keyy);
+// out[i] = in[perm[i]] (double), out_pos[i] = inv[perm[i]]
+void permute_double(cudaStream_t st, const double* in, const int* perm, int M, double* out);
+void inverse_perm(cudaStream_t st, const int* perm, int M, int* inv);
+void compose(cudaStream_t st, const int* a, const int* b, int M, int* out);   // out[i] = a[b[i]]
+// complex precision conversion with row gather: dst(i, q) = (R) src(idx ? idx[i] : i, q) * scale
+template <typename RS, typename RD>
+void convert_gather(cudaStream_t st, const cplx<RS>* src, int lds, const int* idx, int m, int n, cplx<RD>* dst,
+                    int ldd, double scale);
+// dst(idx[i], q) = src(i, q) (scatter), with precision conversion and scale
+template <typename RS, typename RD>
+void convert_scatter(cudaStream_t st, const cplx<RS>* src, int lds, const int* idx, int m, int n, cplx<RD>* dst,
+                     int ldd, double scale);
+// y(:, q) += alpha * x(:, q) in double
+void axpy2(cudaStream_t st, int m, int n, double alpha, const double2* x, int ldx, double2* y, int ldy);
+// per-column sums of |x|^2 (double), out[q]
+void colnorm2(cudaStream_t st, int m, int n, const double2* x, int ldx, double* out);
+
+}  // namespace nh

@@ -1,0 +1,54 @@
+"""C-ABI boundary checks that need no GPU: the library loads, exports every entry point the
+public header declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nudft2_hss.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nudft2_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def cdll():
+    from paper_2607_00928_b300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ["nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_free"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(cdll):
+    missing = [f for f in declared_functions() if not hasattr(cdll, f)]
+    assert not missing, missing
+
+
+def test_invalid_arguments_are_rejected_on_the_host(cdll):
+    from paper_2607_00928_b300.binding import EINVAL, ESTATE, Opts
+    cdll.nudft2_hss_build.restype = ctypes.c_int
+    cdll.nudft2_hss_factor.restype = ctypes.c_int
+    cdll.nudft2_last_error.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    # NULL points
+    assert cdll.nudft2_hss_build(None, None, ctypes.c_int64(512), 16, 16, None, None, ctypes.byref(h)) == EINVAL
+    # M < N (checked before any device access)
+    fake = ctypes.c_void_p(1)
+    assert cdll.nudft2_hss_build(fake, fake, ctypes.c_int64(100), 16, 16, None, None, ctypes.byref(h)) == EINVAL
+    assert b"M >= N" in cdll.nudft2_last_error()
+    # eps outside (0, 1)
+    o = Opts(2.0, 0, 64, 0, 1e-8, 4, 0)
+    assert cdll.nudft2_hss_build(fake, fake, ctypes.c_int64(512), 16, 16, ctypes.byref(o), None,
+                                 ctypes.byref(h)) == EINVAL
+    # factor on a NULL handle is an ordering error
+    assert cdll.nudft2_hss_factor(None, None) == ESTATE

@@ -1,0 +1,147 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the C-ABI.
+
+Tolerances (FP64 mode, HSS tolerance eps = 1e-10): kernel entries and the exact apply are
+direct FP64 evaluations, checked to 1e-12 relative; the HSS solution is checked to the 1e-8
+relative 2-norm error of the target (the HSS approximation error is (1+C) eps by Thm. 3.7 and
+the jittered grids here have cond(A) ~ 2-3, so the solve error is ~1e-10).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc  # noqa: E402
+from synthetic import WORKLOADS, complex_normal, jittered_grid, make_workload, noise_like  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_00928_b300 as m
+    m.lib()
+    return m
+
+
+def relerr_cols(a, b):
+    return np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0))
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------------ kernel entries (Sec. 2.4)
+@pytest.mark.parametrize("n,M", [(16, 300), (37, 257), (128, 1000)])
+def test_psi_eval_matches_oracle(nh, n, M):
+    x, _ = jittered_grid(M, 1, -0.45, 0.45, 100 + n)
+    G = to_np(nh.psi_eval(torch.from_numpy(x), n))
+    ref = orc.tilde_1d(x, n)
+    assert np.max(np.abs(G - ref)) < 1e-12
+
+
+def test_psi_eval_unperturbed_grid_identity(nh):
+    n = 64
+    x = np.arange(n) / n
+    G = to_np(nh.psi_eval(torch.from_numpy(x), n))
+    assert np.max(np.abs(G - np.eye(n))) < 1e-14
+
+
+# ------------------------------------------------------------------ exact apply (Eq. 1)
+@pytest.mark.parametrize("nx,ny,mx,my,s", [(16, 16, 32, 16, 1), (24, 10, 40, 13, 3), (64, 32, 128, 40, 2)])
+def test_exact_apply_forward_and_adjoint(nh, nx, ny, mx, my, s):
+    x, y = jittered_grid(mx, my, -0.3, 0.3, nx * 7 + ny)
+    h = nh.NudftHSS(x, y, nx, ny, levels=1)
+    c = complex_normal((nx * ny, s), 5)
+    f = to_np(h.apply(nh.EXACT_FWD, torch.from_numpy(c)))
+    assert relerr_cols(f, orc.forward(x, y, c, nx, ny)) < 1e-12
+    g = complex_normal((x.size, s), 6)
+    a = to_np(h.apply(nh.EXACT_ADJ, torch.from_numpy(g)))
+    assert relerr_cols(a, orc.adjoint(x, y, g, nx, ny)) < 1e-12
+    h.close()
+
+
+# ------------------------------------------------------------------ HSS approximation (Thm. 3.7)
+@pytest.mark.parametrize("name", ["fp64_n16", "fp64_n32"])
+def test_hss_forward_map_error_bound(nh, name):
+    """FAST_FWD applies A_fast = G~_hss F; ||A_fast - A|| / ||A|| stays within (1+C) eps."""
+    w = WORKLOADS[name]
+    x, y, _ = make_workload(w)
+    h = nh.NudftHSS(x, y, w.nx, w.ny, eps=w.eps, levels=w.levels)
+    c = complex_normal((w.N, 4), 77)
+    fa = to_np(h.apply(nh.FAST_FWD, torch.from_numpy(c)))
+    fe = orc.forward(x, y, c, w.nx, w.ny)
+    assert relerr_cols(fa, fe) < 100 * w.eps
+    h.close()
+
+
+# ------------------------------------------------------------------ end-to-end solve
+def _dense_ref(w, f):
+    x, y, _ = make_workload(w)
+    A = orc.nudft_matrix(x, y, w.nx, w.ny)
+    c, _, rmin = orc.lstsq(A, f)
+    assert rmin > 0
+    return c
+
+
+@pytest.mark.parametrize("name", ["fp64_n16", "fp64_n32"])
+def test_solve_fp64_matches_dense_oracle(nh, name):
+    w = WORKLOADS[name]
+    x, y, ct = make_workload(w)
+    f0 = orc.forward(x, y, ct, w.nx, w.ny)
+    f = f0 + noise_like(f0, 1e-6, 99)              # inconsistent data: LS solution != c_true
+    cref = _dense_ref(w, f)
+    h = nh.NudftHSS(x, y, w.nx, w.ny, eps=w.eps, levels=w.levels).factor()
+    c = to_np(h.solve(torch.from_numpy(f)))
+    assert relerr_cols(c, cref) < 1e-8
+    info = h.info()
+    assert info["max_rank"] > 0
+    h.close()
+
+
+def test_solve_rectangular_grid_ragged_leaves(nh):
+    """nx != ny and leaves with uneven point counts; columns split 3/3 at the leaves."""
+    nx, ny = 24, 12
+    x, y = jittered_grid(48, 14, -0.35, 0.35, 123)
+    c0 = complex_normal((nx * ny, 2), 124)
+    f = orc.forward(x, y, c0, nx, ny)
+    A = orc.nudft_matrix(x, y, nx, ny)
+    cref, _, _ = orc.lstsq(A, f)
+    h = nh.NudftHSS(x, y, nx, ny, eps=1e-10, levels=2).factor()
+    c = to_np(h.solve(torch.from_numpy(f)))
+    assert relerr_cols(c, cref) < 1e-8
+    h.close()
+
+
+def test_solve_mixed_precision_refines_to_fp64(nh):
+    w = WORKLOADS["fp64_n32"]
+    x, y, ct = make_workload(w)
+    f = orc.forward(x, y, ct, w.nx, w.ny)
+    h = nh.NudftHSS(x, y, w.nx, w.ny, eps=1e-6, levels=w.levels, prec="mixed", refine_tol=1e-10,
+                    refine_max=10).factor()
+    c = to_np(h.solve(torch.from_numpy(f)))
+    info = h.info()
+    assert info["refine_relres"] <= 1e-10
+    assert relerr_cols(c, ct) < 1e-8
+    h.close()
+
+
+def test_solve_before_factor_is_an_ordering_error(nh):
+    w = WORKLOADS["fp64_n16"]
+    x, y, _ = make_workload(w)
+    h = nh.NudftHSS(x, y, w.nx, w.ny, levels=w.levels)
+    with pytest.raises(nh.NudftError) as e:
+        h.solve(torch.zeros(w.M, dtype=torch.complex128))
+    assert e.value.code == 6
+    h.close()
+
+
+def test_points_outside_unit_square_rejected(nh):
+    x, y = jittered_grid(32, 16, -0.25, 0.25, 1)
+    x = x.copy()
+    x[3] = 1.0
+    with pytest.raises(nh.NudftError) as e:
+        nh.NudftHSS(x, y, 16, 16, levels=2)
+    assert e.value.code == 1
