@@ -1,0 +1,314 @@
+"""Benchmark of the 2D type-II inverse NUDFT direct solver (HSS face splitting + URV) on B300.
+
+One step = the whole hot path on one synthetic problem: HSS construction (t_c), URV
+factorization (t_f) and the solve of every right-hand side (t_s; in MIXED mode including
+the FP64 iterative refinement with the exact apply), Algorithm 1 of Li & Liu.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  value = right-hand sides solved per second over whole steps
+(offline stage included), summed over ranks; the paper-style split t_c / t_f / t_s and the
+online solve rate are reported alongside.  Multi-GPU runs are independent replicas (the path
+has no exchange step).  --impl reference times the FP64 CPU oracle (dense Householder least
+squares) on a bounded sample of the same workload family and scales it to the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import WORKLOADS, make_workload, noise_like  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FFMA_TFLOPS_NOMINAL = 148 * 128 * 2 * 2.032e9 / 1e12     # FP32 CUDA-core FMA peak at max SM clock
+DFMA_TFLOPS_NOMINAL = 1.25                                 # B300 FP64 rate
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------------ oracle arm
+def oracle_sample(reps: int = 1):
+    """Dense FP64 Householder least squares of the oracle on the 16x16 workload (M=512)."""
+    import oracle as orc
+    w = WORKLOADS["fp64_n16"]
+    x, y, ct = make_workload(w)
+    f = orc.forward(x, y, ct, w.nx, w.ny)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        A = orc.nudft_matrix(x, y, w.nx, w.ny)
+        orc.lstsq(A, f)
+    dt = (time.perf_counter() - t0) / reps
+    return dt, w
+
+
+def oracle_scaled_rate(w_target, dt, w_sample, nrhs):
+    """Scale the sample time by the dense-QR cost model M N^2 to the target workload."""
+    scale = (w_target.M * w_target.N ** 2) / (w_sample.M * w_sample.N ** 2)
+    t_target = dt * scale
+    return nrhs / t_target, t_target, scale
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(th) if th else os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample()
+    ts = []
+    for _ in range(args.steps):
+        dt, ws = oracle_sample()
+        ts.append(dt)
+    dt = statistics.median(ts)
+    rate, t_target, scale = oracle_scaled_rate(w, dt, ws, w.nrhs)
+    sample = (f"oracle dense Householder LS (FP64, numpy) at N={ws.N}, M={ws.M}, 1 RHS, {dt:.3f} s median of "
+              f"{args.steps}; scaled by M*N^2 (x{scale:.3g}) to N={w.N}, M={w.M}")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_target * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, args),
+            "cpu_baseline": {"value": rate, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "2D inverse-NUDFT solves/s (build+factor+solve per step), N=256^2 mixed / FP64"
+
+
+def config_of(w, args):
+    return {"workload": w.name, "nx": w.nx, "ny": w.ny, "M": w.M, "N": w.N, "nrhs": w.nrhs, "levels": w.levels,
+            "eps": (args.eps if args.eps else w.eps), "precision": "mixed" if w.mixed else "fp64",
+            "grid": f"jittered {w.mx}x{w.my}, theta~U{list(w.theta)}", "l2": "working set > L2 (126 MB); no flush",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------------------------------ our arm
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2607_00928_b300 as nh
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    x, y, ct = make_workload(w)
+    eps = args.eps if args.eps else (1e-6 if w.mixed else w.eps)
+    prec = "mixed" if w.mixed else "fp64"
+    xt = torch.from_numpy(x).to(dev)
+    yt = torch.from_numpy(y).to(dev)
+    ctt = torch.from_numpy(ct).to(dev)
+    # right-hand side f = A c_true (+ noise) formed with the exact FP64 apply of the library
+    h0 = nh.NudftHSS(xt, yt, w.nx, w.ny, eps=eps, levels=1)
+    f = h0.apply(nh.EXACT_FWD, ctt)
+    h0.close()
+    if w.noise:
+        f = f + torch.from_numpy(noise_like(f.cpu().numpy(), w.noise, w.seed + 7)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = nh.NudftHSS(xt, yt, w.nx, w.ny, eps=eps, levels=w.levels, prec=prec, refine_tol=1e-8, refine_max=10,
+                        profile=True)
+        h.factor()
+        c = h.solve(f)
+        inf = h.info()
+        inf["kstats"] = h.kstats()
+        h.close()
+        return c, inf
+
+    for _ in range(args.warmup):
+        c, inf = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        c, inf = step()
+        infos.append(inf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    rel = float(torch.max(torch.linalg.norm(c - ctt, dim=0) / torch.linalg.norm(ctt, dim=0)).item())
+    launches = sum(i["launches"] for i in infos)
+    t_c = statistics.median(i["t_build_ms"] for i in infos)
+    t_f = statistics.median(i["t_factor_ms"] for i in infos)
+    t_s = statistics.median(i["t_solve_ms"] for i in infos)
+
+    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    fh = f.cpu().pin_memory()
+    ch = torch.empty((w.N, w.nrhs), dtype=torch.complex128).pin_memory()
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(max(1, min(args.steps, 2))):
+        t0 = time.perf_counter()
+        xd = xh.to(dev, non_blocking=True)
+        yd = yh.to(dev, non_blocking=True)
+        fd = fh.to(dev, non_blocking=True)
+        h = nh.NudftHSS(xd, yd, w.nx, w.ny, eps=eps, levels=w.levels, prec=prec, refine_tol=1e-8, refine_max=10)
+        h.factor()
+        cd = h.solve(fd)
+        h.close()
+        ch.copy_(cd, non_blocking=True)
+        torch.cuda.synchronize()
+        te.append(time.perf_counter() - t0)
+    t_e2e = statistics.median(te)
+    h2d = x.nbytes + y.nbytes + fh.numel() * 16
+    d2h = ch.numel() * 16
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, ws = oracle_sample()
+        rate, t_target, scale = oracle_scaled_rate(w, dt, ws, w.nrhs)
+        cpu = {"value": rate, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": (f"oracle dense Householder LS at N={ws.N}, M={ws.M} took {dt:.3f} s; scaled by M*N^2 "
+                          f"(x{scale:.3g}) to N={w.N}, M={w.M}, {w.nrhs} RHS")}
+
+    pk, src = peaks()
+    kst = {}
+    for i in infos:
+        for k, v in i["kstats"].items():
+            a = kst.setdefault(k, {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+            for f2 in a:
+                a[f2] += v[f2]
+    roof = roofline(kst, w, pk, src)
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * w.nrhs / (ms / 1e3), "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if w.mixed else "f64", "data": "synthetic",
+                "config": config_of(w, args),
+                "t_build_ms": t_c, "t_factor_ms": t_f, "t_solve_ms": t_s,
+                "online_solves_per_s": w.nrhs / (t_s / 1e3) if t_s > 0 else None,
+                "rel_err_vs_c_true": rel, "max_rank": infos[-1]["max_rank"],
+                "level_rank": infos[-1]["level_rank"], "refine_iters": infos[-1]["refine_iters"],
+                "refine_relres": infos[-1]["refine_relres"],
+                "e2e": {"value": world * w.nrhs / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def roofline(kst, w, pk, src):
+    """Dominant kernel class against its pipe peak (FP32 FFMA or FP64 DFMA; complex GEMMs run on CUDA cores)."""
+    if not kst:
+        return None
+    dom = max(kst.items(), key=lambda kv: kv[1]["ms"])
+    name, s = dom
+    if s["ms"] <= 0 or s["launches"] == 0:
+        return None
+    achieved = s["flops"] / (s["ms"] / 1e3) / 1e12
+    peak = FFMA_TFLOPS_NOMINAL if w.mixed else DFMA_TFLOPS_NOMINAL
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "launches": s["launches"],
+            "avg_launch_ms": s["ms"] / s["launches"],
+            "peak_source": ("FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz" if w.mixed
+                            else "FP64 B300 nominal 1.25 TFLOP/s"),
+            "peaks_file": src}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=os.environ.get("NUDFT_BENCH_WORKLOAD", "mixed_n256"))
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

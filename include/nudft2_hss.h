@@ -67,6 +67,17 @@ typedef struct {
   unsigned flags;      /* reserved, 0                                                              */
 } nudft2_opts;
 
+/* opts.flags bits */
+#define NUDFT2_FLAG_PROFILE 1u   /* time every launch of the main kernel classes with CUDA events */
+
+/* Accumulated device time of one kernel class (NUDFT2_FLAG_PROFILE), with its algorithmic
+ * flop and byte counts summed over launches. */
+typedef struct {
+  char name[16];
+  double ms, flops, bytes;
+  int launches;
+} nudft2_kstat;
+
 typedef struct {
   int64_t M;
   int nx, ny, levels, prec;
@@ -108,6 +119,11 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
 
 /* Statistics of the handle (ranks, stage times, memory).  Errors: EINVAL (NULL). */
 nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);
+
+/* Per-class kernel statistics recorded since build (needs NUDFT2_FLAG_PROFILE; synchronises
+ * the recorded events).  Writes at most max entries to out and their count to *n.
+ * Errors: EINVAL (NULL arguments). */
+nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int* n);
 
 /* Release every device allocation of the handle.  NULL is ignored. */
 void nudft2_hss_free(nudft2_hss_t h);

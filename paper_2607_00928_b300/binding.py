@@ -34,6 +34,14 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int)]
 
 
+class KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("launches", ctypes.c_int)]
+
+
+FLAG_PROFILE = 1
+
+
 class NudftError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -60,9 +68,10 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_free.argtypes = [vp]
     L.nudft2_hss_free.restype = None
     L.nudft2_psi_eval.argtypes = [vp, i64, ci, vp, vp]
+    L.nudft2_hss_kstats.argtypes = [vp, ctypes.POINTER(KStat), ci, ctypes.POINTER(ci)]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_psi_eval"):
+              "nudft2_psi_eval", "nudft2_hss_kstats"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -99,14 +108,16 @@ class NudftHSS:
     """Handle of one point set: build (Alg. 1 steps 1-3), factor (step 4), solve (step 5)."""
 
     def __init__(self, x, y, nx: int, ny: int, eps: float = 1e-10, levels: int = 0, leaf: int = 64,
-                 prec: str = "fp64", refine_tol: float = 1e-8, refine_max: int = 8, stream=None):
+                 prec: str = "fp64", refine_tol: float = 1e-8, refine_max: int = 8, stream=None,
+                 profile: bool = False):
         self._h = ctypes.c_void_p()
         self.x = torch.as_tensor(x).to(device="cuda", dtype=torch.float64).contiguous()
         self.y = torch.as_tensor(y).to(device="cuda", dtype=torch.float64).contiguous()
         self.M = self.x.numel()
         self.nx, self.ny, self.N = nx, ny, nx * ny
         self.stream = stream
-        o = Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max, 0)
+        o = Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
+                 FLAG_PROFILE if profile else 0)
         _check(lib().nudft2_hss_build(ctypes.c_void_p(self.x.data_ptr()), ctypes.c_void_p(self.y.data_ptr()),
                                       self.M, nx, ny, ctypes.byref(o), _stream(stream), ctypes.byref(self._h)))
 
@@ -142,6 +153,14 @@ class NudftHSS:
                 "level_rank": list(i.level_rank)[: i.levels + 1], "t_build_ms": i.t_build_ms,
                 "t_factor_ms": i.t_factor_ms, "t_solve_ms": i.t_solve_ms, "refine_iters": i.refine_iters,
                 "refine_relres": i.refine_relres, "device_bytes": i.device_bytes, "launches": i.launches}
+
+    def kstats(self) -> dict:
+        """Per kernel class: device ms, algorithmic flops and bytes, launches (profile=True)."""
+        arr = (KStat * 8)()
+        n = ctypes.c_int()
+        _check(lib().nudft2_hss_kstats(self._h, arr, 8, ctypes.byref(n)))
+        return {arr[i].name.decode(): {"ms": arr[i].ms, "flops": arr[i].flops, "bytes": arr[i].bytes,
+                                       "launches": arr[i].launches} for i in range(n.value)}
 
     def close(self):
         if self._h:

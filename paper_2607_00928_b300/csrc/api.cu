@@ -198,11 +198,15 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     dft_matrix<double>(h->st, nx, -1, 1.0, h->Fxf);
     dft_matrix<double>(h->st, ny, -1, 1.0, h->Fyf);
     h->ops->count(8);
+    const bool prof = (opt.flags & NUDFT2_FLAG_PROFILE) != 0;
+    h->ops->prof.on = prof;
     if (opt.prec == NUDFT2_FP64) {
       h->h64.reset(new Hss<double>(h->st, &h->pl));
+      h->h64->ops().prof.on = prof;
       h->h64->build(opt.eps);
     } else {
       h->h32.reset(new Hss<float>(h->st, &h->pl));
+      h->h32->ops().prof.on = prof;
       h->h32->build(opt.eps);
     }
     NH_CK(cudaStreamSynchronize(h->st));
@@ -352,6 +356,35 @@ nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info) {
     info->refine_relres = h->relres;
     info->device_bytes = h->keep.reserved() + h->scr.reserved() + (h->h64 ? h->h64->bytes() : h->h32->bytes());
     info->launches = h->ops->launches() + (h->h64 ? h->h64->ops().launches() : h->h32->ops().launches());
+  });
+}
+
+nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int* n) {
+  return guard([&] {
+    NH_REQUIRE(h && out && n && max >= 0, ST_EINVAL, "kstats: NULL argument");
+    Prof* ps[2] = {&h->ops->prof, h->h64 ? &h->h64->ops().prof : &h->h32->ops().prof};
+    KStat acc[K_NCLASS];
+    for (Prof* p : ps) {
+      p->collect();
+      for (int c = 0; c < K_NCLASS; ++c) {
+        acc[c].ms += p->stats[c].ms;
+        acc[c].flops += p->stats[c].flops;
+        acc[c].bytes += p->stats[c].bytes;
+        acc[c].launches += p->stats[c].launches;
+      }
+    }
+    int k = 0;
+    for (int c = 0; c < K_NCLASS && k < max; ++c) {
+      if (acc[c].launches == 0) continue;
+      std::memset(&out[k], 0, sizeof(out[k]));
+      std::strncpy(out[k].name, kclass_name(c), sizeof(out[k].name) - 1);
+      out[k].ms = acc[c].ms;
+      out[k].flops = acc[c].flops;
+      out[k].bytes = acc[c].bytes;
+      out[k].launches = acc[c].launches;
+      ++k;
+    }
+    *n = k;
   });
 }
 

@@ -38,6 +38,49 @@ static int* upload_ints(Arena* ar, cudaStream_t st, const std::vector<int>& v) {
   return d;
 }
 
+// =============================================================================== profiling
+const char* kclass_name(int c) {
+  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other"};
+  return (c >= 0 && c < K_NCLASS) ? n[c] : "?";
+}
+Prof::~Prof() {
+  for (auto e : pool_) cudaEventDestroy(e);
+  for (auto& p : pend_) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+}
+cudaEvent_t Prof::get() {
+  if (!pool_.empty()) { cudaEvent_t e = pool_.back(); pool_.pop_back(); return e; }
+  cudaEvent_t e;
+  NH_CK(cudaEventCreate(&e));
+  return e;
+}
+void Prof::begin(cudaStream_t st) {
+  if (!on) return;
+  cur_ = get();
+  NH_CK(cudaEventRecord(cur_, st));
+}
+void Prof::end(cudaStream_t st, int cls, double flops, double bytes) {
+  if (!on || !cur_) return;
+  cudaEvent_t b = get();
+  NH_CK(cudaEventRecord(b, st));
+  pend_.push_back({cls, cur_, b, flops, bytes});
+  cur_ = nullptr;
+  if (pend_.size() > 4096) collect();
+}
+void Prof::collect() {
+  for (auto& p : pend_) {
+    NH_CK(cudaEventSynchronize(p.b));
+    float ms = 0;
+    NH_CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    stats[p.cls].ms += ms;
+    stats[p.cls].flops += p.flops;
+    stats[p.cls].bytes += p.bytes;
+    stats[p.cls].launches += 1;
+    pool_.push_back(p.a);
+    pool_.push_back(p.b);
+  }
+  pend_.clear();
+}
+
 // =============================================================================== GEMM
 // C = alpha op(A) op(B) + beta C.  One CTA per BM x BN output tile of one problem; tiles of
 // all problems are numbered consecutively (exclusive prefix `pre`).
@@ -134,8 +177,16 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
   if (d.empty()) return;
   GemmD<R>* dd = upload(d);
   int* dp = upload_ints(ar_, st_, pre);
+  double fl = 0, by = 0;
+  if (prof.on)
+    for (const auto& g : d) {
+      fl += 8.0 * g.m * g.n * std::max(g.k, 0);
+      by += (double)sizeof(cplx<R>) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != R(0) ? 2.0 : 1.0) * g.m * g.n);
+    }
+  prof.begin(st_);
   k_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
+  prof.end(st_, K_GEMM, fl, by);
   count();
 }
 
@@ -485,8 +536,18 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   if (kmax == 0) { ar_->release(mk); return out; }
   QRD<R>* dd = upload(d);
   for (int j0 = 0; j0 < kmax; j0 += NB) {
+    double fl = 0;
+    if (prof.on)
+      for (const auto& q : d) {
+        const int k = std::min(q.m, q.n);
+        if (j0 >= k) continue;
+        const double b = std::min(NB, k - j0), mm = q.m - j0;
+        fl += 8.0 * mm * b * b + 8.0 * mm * b * b / 2;   // panel reflections + V_p^* V_p
+      }
+    prof.begin(st_);
     k_qr_panel<R><<<(int)d.size(), 256, 0, st_>>>(dd, j0, NB);
     NH_LAUNCH_CK();
+    prof.end(st_, K_QR_PANEL, fl, 0);
     count();
     // trailing update A2 <- Q_p^* A2 = A2 - V_p T_p^* (V_p^* A2)
     std::vector<GemmD<R>> g1, g2, g3;
@@ -850,12 +911,18 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     const R tol = (R)(4.0 * u * std::sqrt((double)std::max(rmax, 1)));
     for (int sweep = 0; sweep < 40; ++sweep) {
       NH_CK(cudaMemsetAsync(offs, 0, nm * sizeof(unsigned), st_));
+      double fl = 0;
+      if (prof.on)
+        for (size_t q = 0; q < jd.size(); ++q)
+          if (!hdone[jmap[q]]) fl += 40.0 * jd[q].r * ((double)jd[q].k * (jd[q].k - 1) / 2.0);
+      prof.begin(st_);
       for (int rd = 0; rd < maxblk - 1; ++rd) {
         dim3 grid(maxblk / 2, (unsigned)jd.size());
         k_jacobi_round<R><<<grid, 512, 0, st_>>>(djd, rd, tol);
         NH_LAUNCH_CK();
         count();
       }
+      prof.end(st_, K_JACOBI, fl, 0);
       NH_CK(cudaMemcpyAsync(hoff.data(), offs, nm * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
       NH_CK(cudaStreamSynchronize(st_));
       bool all = true;

@@ -66,9 +66,33 @@ template <typename R> struct QFac {
   cplx<R>* Tp = nullptr;
 };
 
+// Per-kernel-class accounting (CUDA events around each launch on the launching stream),
+// enabled per handle for measurement runs.  flops are the algorithmic counts of the launch.
+enum KClass { K_GEMM = 0, K_QR_PANEL = 1, K_JACOBI = 2, K_OTHER = 3, K_NCLASS = 4 };
+struct KStat { double ms = 0, flops = 0, bytes = 0; int launches = 0; };
+const char* kclass_name(int c);
+
+class Prof {
+ public:
+  ~Prof();
+  bool on = false;
+  void begin(cudaStream_t st);
+  void end(cudaStream_t st, int cls, double flops, double bytes);
+  void collect();   // synchronises the recorded events and accumulates
+  KStat stats[K_NCLASS];
+
+ private:
+  struct Pend { int cls; cudaEvent_t a, b; double flops, bytes; };
+  cudaEvent_t get();
+  std::vector<cudaEvent_t> pool_;
+  std::vector<Pend> pend_;
+  cudaEvent_t cur_ = nullptr;
+};
+
 template <typename R> class Ops {
  public:
   explicit Ops(cudaStream_t s, Arena* scratch) : st_(s), ar_(scratch) {}
+  Prof prof;
   cudaStream_t stream() const { return st_; }
   Arena* scratch() { return ar_; }
   static constexpr int NB = 32;   // Householder panel width
