@@ -89,6 +89,10 @@ WORKLOADS = {
     "grad_n128": Workload("grad_n128", 128, 128, 256, 128, (-0.3, 0.3), 16, 4, 1e-10, seed=5),
     # mid-size case the dense oracle finishes in seconds: several tiles, ragged leaves
     "fp64_n32": Workload("fp64_n32", 32, 32, 64, 32, (-0.3, 0.3), 3, 3, 1e-10, seed=11),
+    # intermediate sizes of the same recipe (scaling and profiling cases)
+    "fp64_n64": Workload("fp64_n64", 64, 64, 128, 64, (-0.3, 0.3), 4, 3, 1e-10, seed=12),
+    "mixed_n64": Workload("mixed_n64", 64, 64, 128, 64, (-0.3, 0.3), 16, 3, 1e-10, mixed=True, seed=13),
+    "mixed_n128": Workload("mixed_n128", 128, 128, 256, 128, (-0.3, 0.3), 16, 4, 1e-10, mixed=True, seed=14),
 }
 
 
