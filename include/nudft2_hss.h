@@ -133,6 +133,21 @@ void nudft2_hss_free(nudft2_hss_t h);
  * d_x: M points (device), d_out: M x n complex128 column major (ld M).  Errors: EINVAL. */
 nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, void* stream);
 
+/* Building blocks, exposed for unit tests of the batched dense kernels.
+ * prec: NUDFT2_FP64 (complex128 buffers) or NUDFT2_MIXED (complex64 buffers).
+ *
+ * nudft2_la_tsvd: truncated SVD of C (r x w) given Ct = C^* (w x r, ld ldct, overwritten):
+ * left singular vectors with sigma_i > eps * sigma_1 (the recompression rule of Sec. 2.2) go
+ * to d_p (r x min(r,w) capacity, ld ldp), their number to *rank, all min(r,w) sorted singular
+ * values to h_sigma (host, double).  Errors: EINVAL. */
+nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t ldct, double eps, void* d_p,
+                             int64_t ldp, int* rank, double* h_sigma, void* stream);
+
+/* nudft2_la_qr: Householder QR of A (m x n, ld lda) in place (R in the upper trapezoid) and the
+ * explicit unitary factor Q (m x m, ld ldq) written to d_q.  Errors: EINVAL. */
+nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
+                           void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* nudft2_last_error(void);
 

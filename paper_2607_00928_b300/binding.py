@@ -69,9 +69,12 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_free.restype = None
     L.nudft2_psi_eval.argtypes = [vp, i64, ci, vp, vp]
     L.nudft2_hss_kstats.argtypes = [vp, ctypes.POINTER(KStat), ci, ctypes.POINTER(ci)]
+    L.nudft2_la_tsvd.argtypes = [ci, vp, i64, i64, i64, ctypes.c_double, vp, i64, ctypes.POINTER(ci),
+                                 ctypes.POINTER(ctypes.c_double), vp]
+    L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_psi_eval", "nudft2_hss_kstats"):
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -102,6 +105,33 @@ def psi_eval(x: torch.Tensor, n: int) -> torch.Tensor:
     _check(lib().nudft2_psi_eval(ctypes.c_void_p(x.data_ptr()), x.numel(), n, ctypes.c_void_p(out.data_ptr()),
                                  _stream()))
     return out.t()
+
+
+def la_tsvd(C: torch.Tensor, eps: float):
+    """Truncated SVD of C (r x w) by the library's QR + one-sided Jacobi: (P, sigma)."""
+    r, w = C.shape
+    dt = C.dtype
+    prec = FP64 if dt == torch.complex128 else MIXED
+    ct = torch.conj_physical(C).contiguous()        # row-major (r, w) of conj(C) == column-major C^* (w x r)
+    p = min(r, w)
+    P = torch.zeros((max(p, 1), r), dtype=dt, device="cuda")
+    rank = ctypes.c_int()
+    sig = (ctypes.c_double * max(p, 1))()
+    _check(lib().nudft2_la_tsvd(prec, ctypes.c_void_p(ct.data_ptr()), w, r, max(w, 1), eps,
+                                ctypes.c_void_p(P.data_ptr()), r, ctypes.byref(rank), sig, _stream()))
+    return P[: rank.value].t(), [sig[i] for i in range(p)]
+
+
+def la_qr(A: torch.Tensor):
+    """Householder QR of A (m x n) by the library: (Q m x m, R m x n)."""
+    m, n = A.shape
+    dt = A.dtype
+    prec = FP64 if dt == torch.complex128 else MIXED
+    a = A.t().contiguous()                          # column major
+    q = torch.empty((m, m), dtype=dt, device="cuda")
+    _check(lib().nudft2_la_qr(prec, ctypes.c_void_p(a.data_ptr()), m, n, m, ctypes.c_void_p(q.data_ptr()), m,
+                              _stream()))
+    return q.t(), torch.triu(a.t())
 
 
 class NudftHSS:

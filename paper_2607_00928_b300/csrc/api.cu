@@ -128,6 +128,48 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
   h->scr.release(mk);
 }
 
+// ----------------------------------------------------------------------------- LA test hooks
+template <typename R>
+static void la_tsvd(void* d_ct, int w, int r, int ldct, double eps, void* d_p, int ldp, int* rank, double* sig,
+                    cudaStream_t st) {
+  Arena scr, keep;
+  scr.set_stream(st);
+  keep.set_stream(st);
+  Ops<R> ops(st, &scr);
+  Mat<R> Ct;
+  Ct.p = (cplx<R>*)d_ct; Ct.m = w; Ct.n = r; Ct.ld = ldct;
+  std::vector<Mat<R>> P;
+  std::vector<std::vector<double>> S;
+  // all singular values: truncate at the smallest positive threshold, then apply eps on the host
+  ops.tsvd_ct({Ct}, 1e-300, keep, P, S);
+  const int p = std::min(w, r);
+  int rk = 0;
+  for (size_t i = 0; i < S[0].size(); ++i)
+    if (S[0][i] > eps * S[0][0]) rk++;
+  for (int i = 0; i < p; ++i) sig[i] = i < (int)S[0].size() ? S[0][i] : 0.0;
+  if (rk > 0)
+    NH_CK(cudaMemcpy2DAsync(d_p, (size_t)ldp * sizeof(cplx<R>), P[0].p, (size_t)P[0].ld * sizeof(cplx<R>),
+                            (size_t)r * sizeof(cplx<R>), rk, cudaMemcpyDeviceToDevice, st));
+  *rank = rk;
+  NH_CK(cudaStreamSynchronize(st));
+}
+
+template <typename R>
+static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, cudaStream_t st) {
+  Arena scr, keep;
+  scr.set_stream(st);
+  keep.set_stream(st);
+  Ops<R> ops(st, &scr);
+  Mat<R> A;
+  A.p = (cplx<R>*)d_a; A.m = m; A.n = n; A.ld = lda;
+  auto Q = ops.qr({A}, keep);
+  Mat<R> Qm;
+  Qm.p = (cplx<R>*)d_q; Qm.m = m; Qm.n = m; Qm.ld = ldq;
+  ops.set_identity({Qm});
+  ops.apply_q_left(Q, {Qm}, false);
+  NH_CK(cudaStreamSynchronize(st));
+}
+
 // ----------------------------------------------------------------------------- C-ABI
 extern "C" {
 
@@ -385,6 +427,28 @@ nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int*
       ++k;
     }
     *n = k;
+  });
+}
+
+nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t ldct, double eps, void* d_p,
+                             int64_t ldp, int* rank, double* h_sigma, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(d_ct && d_p && rank && h_sigma && w >= 0 && r >= 0 && ldct >= std::max<int64_t>(w, 1) &&
+                   ldp >= std::max<int64_t>(r, 1) && eps > 0,
+               ST_EINVAL, "la_tsvd: bad arguments");
+    if (prec == NUDFT2_FP64)
+      la_tsvd<double>(d_ct, (int)w, (int)r, (int)ldct, eps, d_p, (int)ldp, rank, h_sigma, (cudaStream_t)stream);
+    else
+      la_tsvd<float>(d_ct, (int)w, (int)r, (int)ldct, eps, d_p, (int)ldp, rank, h_sigma, (cudaStream_t)stream);
+  });
+}
+
+nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
+                           void* stream) {
+  return guard([&] {
+    NH_REQUIRE(d_a && d_q && m >= 1 && n >= 1 && lda >= m && ldq >= m, ST_EINVAL, "la_qr: bad arguments");
+    if (prec == NUDFT2_FP64) la_qr<double>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, (cudaStream_t)stream);
+    else la_qr<float>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, (cudaStream_t)stream);
   });
 }
 

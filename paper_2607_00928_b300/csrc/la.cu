@@ -3,9 +3,15 @@
 // data-movement kernels the HSS construction needs.  See la.cuh for the contracts.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "la.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nh {
 
@@ -88,6 +94,7 @@ template <typename R, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, const int* __restrict__ pre,
                                               int np) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
+  constexpr int LA = BM * BK / 256, LB = BN * BK / 256;   // elements each thread stages per k tile
   __shared__ cplx<R> As[BK][BM + 1];
   __shared__ cplx<R> Bs[BK][BN + 1];
   const int pi = find_prob(pre, np, blockIdx.x);
@@ -101,32 +108,53 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TN; ++b) acc[a][b] = czero<R>();
-
-  for (int k0 = 0; k0 < g.k; k0 += BK) {
-    // A tile: op(A)(i, kk), i in [row0, row0+BM), kk in [k0, k0+BK)
-    for (int e = tid; e < BM * BK; e += 256) {
+  cplx<R> ra[LA], rb[LB];
+  // stage k tile starting at k0 into registers (op applied, zero padded)
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + q * 256;
       int ii, kk;
       if (g.opA == OP_N) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
       const int gi = row0 + ii, gk = k0 + kk;
       cplx<R> v = czero<R>();
-      if (gi < g.m && gk < g.k) {
-        v = (g.opA == OP_N) ? g.A[(size_t)gi + (size_t)gk * g.lda]
-                            : ld_op<R>(g.A + (size_t)gk + (size_t)gi * g.lda, g.opA);
-      }
-      As[kk][ii] = v;
+      if (gi < g.m && gk < g.k)
+        v = (g.opA == OP_N) ? g.A[(size_t)gi + (size_t)gk * g.lda] : ld_op<R>(g.A + (size_t)gk + (size_t)gi * g.lda, g.opA);
+      ra[q] = v;
     }
-    for (int e = tid; e < BN * BK; e += 256) {
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + q * 256;
       int jj, kk;
       if (g.opB == OP_N) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
       const int gj = col0 + jj, gk = k0 + kk;
       cplx<R> v = czero<R>();
-      if (gj < g.n && gk < g.k) {
-        v = (g.opB == OP_N) ? g.B[(size_t)gk + (size_t)gj * g.ldb]
-                            : ld_op<R>(g.B + (size_t)gj + (size_t)gk * g.ldb, g.opB);
-      }
-      Bs[kk][jj] = v;
+      if (gj < g.n && gk < g.k)
+        v = (g.opB == OP_N) ? g.B[(size_t)gk + (size_t)gj * g.ldb] : ld_op<R>(g.B + (size_t)gj + (size_t)gk * g.ldb, g.opB);
+      rb[q] = v;
     }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + q * 256;
+      int ii, kk;
+      if (g.opA == OP_N) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
+      As[kk][ii] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + q * 256;
+      int jj, kk;
+      if (g.opB == OP_N) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
+      Bs[kk][jj] = rb[q];
+    }
+  };
+  if (g.k > 0) load(0);
+  for (int k0 = 0; k0 < g.k; k0 += BK) {
+    store();
     __syncthreads();
+    if (k0 + BK < g.k) load(k0 + BK);      // global loads of the next tile overlap the FMAs below
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       cplx<R> av[TM], bv[TN];
@@ -166,15 +194,40 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
   std::vector<GemmD<R>> d;
   d.reserve(d0.size());
   std::vector<int> pre;
-  int tiles = 0;
+  int tiles = 0, tiles_big = 0;
+  double work = 0, work_big_ok = 0;
   for (const auto& g : d0) {
     if (g.m <= 0 || g.n <= 0) continue;
     if (g.k <= 0 && g.beta == R(1)) continue;
     d.push_back(g);
     pre.push_back(tiles);
     tiles += ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
+    tiles_big += ((g.m + 127) / 128) * ((g.n + 127) / 128);
+    const double w = (double)g.m * g.n * std::max(g.k, 1);
+    work += w;
+    if (g.m >= 128 && g.n >= 128) work_big_ok += w;
   }
   if (d.empty()) return;
+  // FP32 batches dominated by large products use 128 x 128 tiles (8 x 8 complex per thread)
+  if constexpr (sizeof(R) == 4) if (work_big_ok >= 0.8 * work && tiles_big >= 2 * 148) {
+    std::vector<int> preb;
+    int t = 0;
+    for (const auto& g : d) {
+      preb.push_back(t);
+      t += ((g.m + 127) / 128) * ((g.n + 127) / 128);
+    }
+    GemmD<R>* dd = upload(d);
+    int* dp = upload_ints(ar_, st_, preb);
+    double fl = 0;
+    if (prof.on)
+      for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
+    prof.begin(st_);
+    k_gemm<R, 8, 8, 8><<<t, 256, 0, st_>>>(dd, dp, (int)d.size());
+    NH_LAUNCH_CK();
+    prof.end(st_, K_GEMM, fl, 0);
+    count();
+    return;
+  }
   GemmD<R>* dd = upload(d);
   int* dp = upload_ints(ar_, st_, pre);
   double fl = 0, by = 0;
@@ -507,6 +560,154 @@ __global__ void __launch_bounds__(256) k_qr_panel(const QRD<R>* __restrict__ ds,
   }
 }
 
+// Cluster-cooperative panel factorization: rows [j0, m) of the panel are split into QCS
+// slabs, one per CTA of the cluster.  Per column: partial norms -> cluster barrier -> every CTA
+// forms the same reflector from the gathered partials (fixed order, so identical) -> partial
+// dots of the remaining panel columns -> cluster barrier -> update own rows.  The compact-WY T
+// of the panel comes from the cluster-reduced Gram V_p^* V_p.
+template <typename R>
+__global__ void __launch_bounds__(256) k_qr_panel_cl(const QRD<R>* __restrict__ ds, int j0, int nb, int qcs) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const QRD<R> q = ds[blockIdx.x / qcs];
+  const int k = min(q.m, q.n);
+  if (j0 >= k) return;                       // uniform over the cluster
+  const int b = min(nb, k - j0);
+  const int rows = q.m - j0;
+  const int per = (rows + qcs - 1) / qcs;
+  const int lo = j0 + crank * per, hi = min(q.m, lo + per);
+  __shared__ R pn[2][8];                     // partial norm^2 per warp
+  __shared__ R pd[2][32][2];                 // partial dots per panel column
+  __shared__ cplx<R> Ts[32][33];
+  __shared__ cplx<R> Ys[32][33];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // partial norm of the first column
+  auto part_norm = [&](int col, int buf) {
+    R s = 0;
+    for (int i = max(lo, col) + tid; i < hi; i += 256) s += abs2(q.A[(size_t)i + (size_t)col * q.lda]);
+    s = warp_sum(s);
+    if (lane == 0) pn[buf][warp] = s;
+  };
+  part_norm(j0, 0);
+  for (int jj = 0; jj < b; ++jj) {
+    const int col = j0 + jj;
+    const int buf = jj & 1;
+    cluster.sync();
+    // gather ||x||^2
+    R nrm2 = 0;
+    {
+      R v = 0;
+      for (int e = lane; e < qcs * 8; e += 32) {
+        const R* p = cluster.map_shared_rank(&pn[buf][0], e / 8);
+        v += p[e % 8];
+      }
+      nrm2 = warp_sum(v);                    // same value in every warp and CTA
+    }
+    cplx<R>* x = q.A + (size_t)col * q.lda;
+    const cplx<R> a0 = x[col];
+    const R nrm = sqrt(nrm2);
+    const R aa = sqrt(abs2(a0));
+    const cplx<R> ph = aa > R(0) ? mkc(a0.x / aa, a0.y / aa) : mkc(R(1), R(0));
+    cplx<R> v0 = mkc(R(0), R(0));
+    R tau = R(2);
+    if (nrm > R(0)) {
+      v0 = a0 + nrm * ph;
+      tau = R(2) / (R(1) + (nrm2 - aa * aa) / abs2(v0));
+    }
+    const R v0a2 = abs2(v0);
+    cplx<R>* vcol = q.V + (size_t)col * q.ldv;
+    // write own rows of v (row col belongs to the slab containing it)
+    for (int i = max(lo, col) + tid; i < hi; i += 256) {
+      if (i == col) {
+        vcol[i] = mkc(R(1), R(0));     // x[col] <- R_kk only after the next barrier (others read a0)
+        q.tau[col] = tau;
+      } else {
+        const cplx<R> xv = x[i];
+        vcol[i] = (v0a2 > R(0)) ? mkc((xv.x * v0.x + xv.y * v0.y) / v0a2, (xv.y * v0.x - xv.x * v0.y) / v0a2)
+                                : mkc(R(0), R(0));
+        x[i] = mkc(R(0), R(0));
+      }
+    }
+    __syncthreads();
+    // partial dots w_c = v^* A(:, c) over own rows, one warp per column
+    for (int c = col + 1 + warp; c < j0 + b; c += 8) {
+      const cplx<R>* y = q.A + (size_t)c * q.lda;
+      cplx<R> w = czero<R>();
+      for (int i = max(lo, col) + lane; i < hi; i += 32) cfmac(w, vcol[i], y[i]);
+      w.x = warp_sum(w.x);
+      w.y = warp_sum(w.y);
+      if (lane == 0) { pd[buf][c - j0][0] = w.x; pd[buf][c - j0][1] = w.y; }
+    }
+    cluster.sync();
+    if (tid == 0 && col >= lo && col < hi) x[col] = (nrm > R(0)) ? mkc(-nrm * ph.x, -nrm * ph.y) : mkc(R(0), R(0));
+    // gather dots and update own rows; then the partial norm of the next column
+    for (int c = col + 1 + warp; c < j0 + b; c += 8) {
+      R wx = 0, wy = 0;
+      if (lane < qcs) {
+        const R* p = cluster.map_shared_rank(&pd[buf][c - j0][0], lane);
+        wx = p[0];
+        wy = p[1];
+      }
+      wx = warp_sum(wx);
+      wy = warp_sum(wy);
+      const cplx<R> w = mkc(tau * wx, tau * wy);
+      cplx<R>* y = q.A + (size_t)c * q.lda;
+      for (int i = max(lo, col) + lane; i < hi; i += 32) y[i] = y[i] - vcol[i] * w;
+    }
+    __syncthreads();
+    if (jj + 1 < b) part_norm(col + 1, buf ^ 1);
+  }
+  // Gram Y = V_p^* V_p over own rows (strict upper part), cluster-reduced
+  for (int p = warp; p < b * b; p += 8) {
+    const int i = p / b, j = p % b;
+    if (i >= j) continue;
+    const cplx<R>* vi = q.V + (size_t)(j0 + i) * q.ldv;
+    const cplx<R>* vj = q.V + (size_t)(j0 + j) * q.ldv;
+    cplx<R> w = czero<R>();
+    for (int r = max(lo, j0 + j) + lane; r < hi; r += 32) cfmac(w, vi[r], vj[r]);
+    w.x = warp_sum(w.x);
+    w.y = warp_sum(w.y);
+    if (lane == 0) Ys[i][j] = w;
+  }
+  cluster.sync();
+  if (crank == 0) {
+    for (int e = tid; e < b * b; e += 256) {
+      const int i = e / b, j = e % b;
+      if (i >= j) continue;
+      cplx<R> acc = czero<R>();
+      for (int rk = 0; rk < qcs; ++rk) {
+        const cplx<R>* p = cluster.map_shared_rank(&Ys[i][j], rk);
+        acc = acc + *p;
+      }
+      Ts[i][j] = acc;       // staged: Gram in the strict upper part of Ts
+    }
+  }
+  cluster.sync();            // peers may exit only after rank 0 has read their Gram partials
+  if (crank != 0) return;
+  for (int e = tid; e < 32 * 32; e += 256) {
+    const int i = e / 32, j = e % 32;
+    if (i < j && i < b && j < b) Ys[i][j] = Ts[i][j];
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * 33; e += 256) Ts[e / 33][e % 33] = czero<R>();
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    const R tj = q.tau[j0 + j];
+    if (tid < j) {
+      cplx<R> acc = czero<R>();
+      for (int l = tid; l < j; ++l) cfma(acc, Ts[tid][l], Ys[l][j]);
+      Ts[tid][j] = (-tj) * acc;
+    }
+    if (tid == 0) Ts[j][j] = mkc(tj, R(0));
+    __syncthreads();
+  }
+  cplx<R>* Tp = q.Tp + (size_t)(j0 / nb) * nb * nb;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    Tp[e] = (i < b && j < b) ? Ts[i][j] : czero<R>();
+  }
+}
+
 template <typename R>
 std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   std::vector<QFac<R>> out(A.size());
@@ -535,6 +736,11 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   }
   if (kmax == 0) { ar_->release(mk); return out; }
   QRD<R>* dd = upload(d);
+  // rows per CTA ~ 1024: tall panels are shared by a cluster of up to 8 CTAs
+  int mmax = 0;
+  for (auto& q : d) mmax = std::max(mmax, q.m);
+  int qcs = 1;
+  while (qcs < 8 && (long long)qcs * 1024 < mmax) qcs *= 2;
   for (int j0 = 0; j0 < kmax; j0 += NB) {
     double fl = 0;
     if (prof.on)
@@ -545,8 +751,23 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
         fl += 8.0 * mm * b * b + 8.0 * mm * b * b / 2;   // panel reflections + V_p^* V_p
       }
     prof.begin(st_);
-    k_qr_panel<R><<<(int)d.size(), 256, 0, st_>>>(dd, j0, NB);
-    NH_LAUNCH_CK();
+    if (qcs > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(d.size() * qcs));
+      cfg.blockDim = dim3(256);
+      cfg.stream = st_;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = qcs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      NH_CK(cudaLaunchKernelEx(&cfg, k_qr_panel_cl<R>, (const QRD<R>*)dd, j0, (int)NB, qcs));
+    } else {
+      k_qr_panel<R><<<(int)d.size(), 256, 0, st_>>>(dd, j0, NB);
+      NH_LAUNCH_CK();
+    }
     prof.end(st_, K_QR_PANEL, fl, 0);
     count();
     // trailing update A2 <- Q_p^* A2 = A2 - V_p T_p^* (V_p^* A2)
@@ -734,7 +955,30 @@ template <typename R> struct JacD {
   cplx<R>* X; int ld, r, k, nblk;   // nblk even
   unsigned* off;                    // max |gamma|/sqrt(alpha beta) of this sweep (float bits)
   const int* done;                  // converged flag from the previous sweep
+  R* amax;                          // max squared column norm at the start of the sweep
 };
+
+// Largest squared column norm of each matrix (one CTA per matrix): the scale below which a
+// column counts as numerically zero in the Jacobi sweeps.
+template <typename R> __global__ void __launch_bounds__(256) k_colmax(const JacD<R>* __restrict__ ds) {
+  const JacD<R> d = ds[blockIdx.x];
+  __shared__ R red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R m = 0;
+  for (int j = warp; j < d.k; j += 8) {
+    R acc = 0;
+    for (int i = lane; i < d.r; i += 32) acc += abs2(d.X[(size_t)i + (size_t)j * d.ld]);
+    acc = warp_sum(acc);
+    m = fmax(m, acc);
+  }
+  if (lane == 0) red[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R t = 0;
+    for (int w = 0; w < 8; ++w) t = fmax(t, red[w]);
+    *d.amax = t;
+  }
+}
 
 __device__ __forceinline__ void rr_pair(int p, int r, int n, int& a, int& b) {
   // circle method for n (even) players: player 0 fixed
@@ -743,7 +987,7 @@ __device__ __forceinline__ void rr_pair(int p, int r, int n, int& a, int& b) {
 }
 
 template <typename R>
-__device__ void jac_rotate(cplx<R>* xa, cplx<R>* xb, int r, R tol, unsigned* off) {
+__device__ void jac_rotate(cplx<R>* xa, cplx<R>* xb, int r, R tol, unsigned* off, R floor2) {
   const int lane = threadIdx.x & 31;
   R al = 0, be = 0;
   cplx<R> ga = czero<R>();
@@ -759,6 +1003,9 @@ __device__ void jac_rotate(cplx<R>* xa, cplx<R>* xb, int r, R tol, unsigned* off
   ga.y = warp_sum(ga.y);
   const R g = sqrt(abs2(ga));
   if (!(al > R(0)) || !(be > R(0)) || g == R(0)) return;
+  // a column below the noise floor is numerically zero: leave it out of rotations and of the
+  // convergence test (its direction is rounding noise and would only pollute the other column)
+  if (fmin(al, be) <= floor2) return;
   const R rel = g / sqrt(al * be);
   if (lane == 0) atomicMax(off, __float_as_uint((float)rel));
   if (rel <= tol) return;
@@ -777,7 +1024,7 @@ __device__ void jac_rotate(cplx<R>* xa, cplx<R>* xb, int r, R tol, unsigned* off
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) k_jacobi_round(const JacD<R>* __restrict__ ds, int round, R tol) {
+__global__ void __launch_bounds__(512) k_jacobi_round(const JacD<R>* __restrict__ ds, int round, R tol, R negl2) {
   const JacD<R> d = ds[blockIdx.y];
   if (*d.done) return;
   if (round >= d.nblk - 1 || (int)blockIdx.x >= d.nblk / 2) return;
@@ -803,9 +1050,117 @@ __global__ void __launch_bounds__(512) k_jacobi_round(const JacD<R>* __restrict_
     rr_pair(warp, ir, 32, a, b);
     if (a < n && b < n) {
       const int ca = min(cidx[a], cidx[b]), cb = max(cidx[a], cidx[b]);
-      jac_rotate<R>(d.X + (size_t)ca * d.ld, d.X + (size_t)cb * d.ld, d.r, tol, d.off);
+      jac_rotate<R>(d.X + (size_t)ca * d.ld, d.X + (size_t)cb * d.ld, d.r, tol, d.off, negl2 * (*d.amax));
     }
     __syncthreads();
+  }
+}
+
+// Cluster-resident variant: the 32 columns of a block pair live in shared memory, split by
+// rows over a cluster of JCS CTAs.  Each inner round needs the three dot products of every
+// column pair over all rows: every CTA writes its partials, one cluster barrier, then each
+// warp gathers the JCS partials over DSMEM in a fixed order, so all CTAs compute the same
+// rotation and apply it to their own rows.  Data leaves shared memory once per round.
+constexpr int JCS = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_jacobi_cluster(const JacD<R>* __restrict__ ds, int round, R tol, int rpc,
+                                                         R negl2) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const JacD<R> d = ds[blockIdx.y];
+  const int pair = blockIdx.x / JCS;
+  // every CTA of a cluster shares (blockIdx.y, pair), so these exits are cluster-uniform
+  if (*d.done) return;
+  if (round >= d.nblk - 1 || pair >= d.nblk / 2) return;
+  extern __shared__ unsigned char smraw_j[];
+  cplx<R>* S = (cplx<R>*)smraw_j;
+  __shared__ R part[2][16][4];
+  __shared__ int cidx[32];
+  __shared__ int nc_s;
+  int I, J;
+  rr_pair(pair, round, d.nblk, I, J);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int q = 0; q < 2; ++q) {
+      const int B = q ? J : I;
+      for (int j = B * 16; j < min(B * 16 + 16, d.k); ++j) cidx[c++] = j;
+    }
+    nc_s = c;
+  }
+  __syncthreads();
+  const int n = nc_s;
+  const int r0 = crank * rpc, r1 = min(d.r, r0 + rpc), rl = max(0, r1 - r0);
+  for (int e = threadIdx.x; e < n * rl; e += blockDim.x) {
+    const int c = e / rl, i = e - c * rl;
+    S[(size_t)c * rpc + i] = d.X[(size_t)(r0 + i) + (size_t)cidx[c] * d.ld];
+  }
+  cluster.sync();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int ir = 0; ir < 31; ++ir) {
+    const int buf = ir & 1;
+    int a, b;
+    rr_pair(warp, ir, 32, a, b);
+    const bool act = (a < n && b < n);
+    int sa = a, sb = b;
+    if (act && cidx[a] > cidx[b]) { sa = b; sb = a; }
+    R al = 0, be = 0;
+    cplx<R> ga = czero<R>();
+    if (act) {
+      const cplx<R>* xa = S + (size_t)sa * rpc;
+      const cplx<R>* xb = S + (size_t)sb * rpc;
+      for (int i = lane; i < rl; i += 32) {
+        const cplx<R> u = xa[i], v = xb[i];
+        al += abs2(u);
+        be += abs2(v);
+        cfmac(ga, u, v);
+      }
+    }
+    al = warp_sum(al);
+    be = warp_sum(be);
+    ga.x = warp_sum(ga.x);
+    ga.y = warp_sum(ga.y);
+    if (lane == 0) {
+      part[buf][warp][0] = al; part[buf][warp][1] = be; part[buf][warp][2] = ga.x; part[buf][warp][3] = ga.y;
+    }
+    cluster.sync();
+    R v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if (lane < JCS) {
+      const R* p = cluster.map_shared_rank(&part[buf][warp][0], lane);
+      v0 = p[0]; v1 = p[1]; v2 = p[2]; v3 = p[3];
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    v3 = warp_sum(v3);
+    if (act) {
+      const R g = sqrt(v2 * v2 + v3 * v3);
+      if (v0 > R(0) && v1 > R(0) && g > R(0) && fmin(v0, v1) > negl2 * (*d.amax)) {
+        const R rel = g / sqrt(v0 * v1);
+        if (crank == 0 && lane == 0) atomicMax(d.off, __float_as_uint((float)rel));
+        if (rel > tol) {
+          const R zeta = (v1 - v0) / (R(2) * g);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          const R c = R(1) / sqrt(R(1) + t * t);
+          const R s = c * t;
+          const cplx<R> se = mkc(s * v2 / g, s * v3 / g);
+          const cplx<R> sec = mkc(s * v2 / g, -s * v3 / g);
+          cplx<R>* xa = S + (size_t)sa * rpc;
+          cplx<R>* xb = S + (size_t)sb * rpc;
+          for (int i = lane; i < rl; i += 32) {
+            const cplx<R> u = xa[i], v = xb[i];
+            xa[i] = c * u - sec * v;
+            xb[i] = se * u + c * v;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  for (int e = threadIdx.x; e < n * rl; e += blockDim.x) {
+    const int c = e / rl, i = e - c * rl;
+    d.X[(size_t)(r0 + i) + (size_t)cidx[c] * d.ld] = S[(size_t)c * rpc + i];
   }
 }
 
@@ -890,6 +1245,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   std::vector<int> jmap;
   unsigned* offs = ar_->template arr<unsigned>(nm + 1);
   int* done = ar_->template arr<int>(nm + 1, true);
+  R* amaxv = ar_->template arr<R>(nm + 1, true);
   int maxblk = 0;
   for (size_t i = 0; i < nm; ++i) {
     const int p = X[i].n;
@@ -897,7 +1253,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     int nb = (p + 15) / 16;
     if (nb < 2) nb = 2;
     if (nb & 1) nb++;
-    jd.push_back({X[i].p, X[i].ld, X[i].m, p, nb, offs + i, done + i});
+    jd.push_back({X[i].p, X[i].ld, X[i].m, p, nb, offs + i, done + i, amaxv + i});
     jmap.push_back((int)i);
     maxblk = std::max(maxblk, nb);
   }
@@ -909,17 +1265,47 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     int rmax = 0;
     for (auto& j : jd) rmax = std::max(rmax, j.r);
     const R tol = (R)(4.0 * u * std::sqrt((double)std::max(rmax, 1)));
+    // cluster-resident rounds when a block pair's row slab fits in shared memory
+    const int rpc = (rmax + JCS - 1) / JCS;
+    const size_t jsmem = (size_t)32 * rpc * sizeof(cplx<R>);
+    const bool use_cluster = jsmem <= (size_t)200 * 1024 && std::getenv("NH_JACOBI_GLOBAL") == nullptr;
+    if (use_cluster)
+      NH_CK(cudaFuncSetAttribute(k_jacobi_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(jsmem, 1)));
+    // columns with norm <= delta * (largest column norm) are numerically zero; delta sits well
+    // below the truncation threshold eps so no retained direction is affected
+    const double delta = std::max(0.1 * eps, 8.0 * u);
+    const R negl2 = (R)(delta * delta);
     for (int sweep = 0; sweep < 40; ++sweep) {
       NH_CK(cudaMemsetAsync(offs, 0, nm * sizeof(unsigned), st_));
+      k_colmax<R><<<(int)jd.size(), 256, 0, st_>>>(djd);
+      NH_LAUNCH_CK();
+      count();
       double fl = 0;
       if (prof.on)
         for (size_t q = 0; q < jd.size(); ++q)
           if (!hdone[jmap[q]]) fl += 40.0 * jd[q].r * ((double)jd[q].k * (jd[q].k - 1) / 2.0);
       prof.begin(st_);
       for (int rd = 0; rd < maxblk - 1; ++rd) {
-        dim3 grid(maxblk / 2, (unsigned)jd.size());
-        k_jacobi_round<R><<<grid, 512, 0, st_>>>(djd, rd, tol);
-        NH_LAUNCH_CK();
+        if (use_cluster) {
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3((unsigned)(maxblk / 2 * JCS), (unsigned)jd.size());
+          cfg.blockDim = dim3(512);
+          cfg.dynamicSmemBytes = jsmem;
+          cfg.stream = st_;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeClusterDimension;
+          at[0].val.clusterDim.x = JCS;
+          at[0].val.clusterDim.y = 1;
+          at[0].val.clusterDim.z = 1;
+          cfg.attrs = at;
+          cfg.numAttrs = 1;
+          NH_CK(cudaLaunchKernelEx(&cfg, k_jacobi_cluster<R>, (const JacD<R>*)djd, rd, tol, rpc, negl2));
+        } else {
+          dim3 grid(maxblk / 2, (unsigned)jd.size());
+          k_jacobi_round<R><<<grid, 512, 0, st_>>>(djd, rd, tol, negl2);
+          NH_LAUNCH_CK();
+        }
         count();
       }
       prof.end(st_, K_JACOBI, fl, 0);
@@ -934,7 +1320,39 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         if ((double)f <= (double)tol) hdone[i] = 1; else all = false;
       }
       NH_CK(cudaMemcpyAsync(done, hdone.data(), nm * sizeof(int), cudaMemcpyHostToDevice, st_));
-      if (all) break;
+      if (all || sweep == 39) {
+        if (!all && std::getenv("NH_DUMP_TSVD")) {
+          // write the first unconverged matrix (after the sweeps) for offline analysis
+          for (size_t q = 0; q < jd.size(); ++q) {
+            if (hdone[jmap[q]]) continue;
+            const JacD<R>& j = jd[q];
+            std::vector<cplx<R>> hx((size_t)j.r * j.k);
+            NH_CK(cudaMemcpy2D(hx.data(), (size_t)j.r * sizeof(cplx<R>), j.X, (size_t)j.ld * sizeof(cplx<R>),
+                               (size_t)j.r * sizeof(cplx<R>), j.k, cudaMemcpyDeviceToHost));
+            FILE* fp = std::fopen(std::getenv("NH_DUMP_TSVD"), "wb");
+            if (fp) {
+              int hdr[3] = {j.r, j.k, (int)sizeof(R)};
+              std::fwrite(hdr, sizeof(int), 3, fp);
+              std::fwrite(hx.data(), sizeof(cplx<R>), hx.size(), fp);
+              std::fclose(fp);
+            }
+            break;
+          }
+        }
+        if (std::getenv("NH_DEBUG")) {
+          int unconv = 0;
+          float worst = 0;
+          for (size_t q = 0; q < jd.size(); ++q) {
+            const int i = jmap[q];
+            float f;
+            std::memcpy(&f, &hoff[i], 4);
+            if (!hdone[i]) { unconv++; worst = std::max(worst, f); }
+          }
+          std::fprintf(stderr, "[tsvd] mats=%zu rmax=%d kmax_blocks=%d sweeps=%d unconverged=%d worst_off=%.3e tol=%.3e\n",
+                       jd.size(), rmax, maxblk, sweep + 1, unconv, worst, (double)tol);
+        }
+        break;
+      }
     }
   }
   // 4. sort + count

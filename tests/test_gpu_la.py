@@ -1,0 +1,99 @@
+"""GPU unit tests of the batched dense kernels behind the HSS stages, against numpy/LAPACK.
+
+* Householder QR (single-CTA panels and cluster-cooperative panels for tall matrices):
+  Q R = A, Q^* Q = I, |R_ii| equal to LAPACK's.
+* Truncated SVD (QR + one-sided Jacobi, cluster-resident and global-memory variants):
+  singular values equal LAPACK's, P^* P = I, and the discarded part of C is below the
+  threshold -- the truncation rule of the recompression (Sec. 2.2).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_00928_b300 as m
+    m.lib()
+    return m
+
+
+def _rand(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def make_matrix(r, w, kind, seed):
+    p = min(r, w)
+    U, _ = np.linalg.qr(_rand((r, p), seed))
+    V, _ = np.linalg.qr(_rand((w, p), seed + 1))
+    if kind == "graded":
+        s = np.logspace(0, -14, p)
+    elif kind == "repeated":                         # Kronecker-like clusters of equal values
+        s = np.repeat(np.logspace(0, -8, max(1, p // 8)), 8)[:p]
+        s = np.concatenate([s, np.full(p - s.size, s[-1])]) if s.size < p else s
+    elif kind == "wide":                             # 1e0..1e-11, a gap, then a noise floor 1e-16..1e-20
+        q = (p * 5) // 6
+        s = np.concatenate([np.logspace(0.2, -11, q), np.logspace(-16, -20, p - q)])
+    else:                                            # numerically rank deficient: half the spectrum zero
+        s = np.concatenate([np.logspace(0, -6, p // 2), np.zeros(p - p // 2)])
+    return (U * s) @ V.conj().T
+
+
+CASES = [(64, 200, "graded"), (300, 120, "graded"), (520, 1500, "graded"), (1577, 3000, "graded"),
+         (400, 400, "repeated"), (256, 512, "rankdef"), (1024, 3000, "wide"), (300, 900, "wide")]
+
+
+@pytest.mark.parametrize("jacobi", ["cluster", "global"])
+@pytest.mark.parametrize("r,w,kind", CASES)
+def test_tsvd_fp64(nh, monkeypatch, jacobi, r, w, kind):
+    if jacobi == "global":
+        monkeypatch.setenv("NH_JACOBI_GLOBAL", "1")
+    C = make_matrix(r, w, kind, r + w)
+    eps = 1e-10
+    P, sig = nh.la_tsvd(torch.from_numpy(C).cuda(), eps)
+    P = P.cpu().numpy()
+    s_ref = np.linalg.svd(C, compute_uv=False)
+    k = P.shape[1]
+    assert abs(k - int(np.sum(s_ref > eps * s_ref[0]))) <= 1
+    assert np.max(np.abs(np.array(sig[:k]) - s_ref[:k])) < 1e-12 * s_ref[0]
+    assert np.max(np.abs(P.conj().T @ P - np.eye(k))) < 1e-12
+    resid = C - P @ (P.conj().T @ C)
+    assert np.linalg.norm(resid, 2) <= 2 * eps * s_ref[0] + 1e-13 * s_ref[0]
+
+
+@pytest.mark.parametrize("r,w", [(300, 120), (1577, 3000)])
+def test_tsvd_fp32(nh, r, w):
+    C = make_matrix(r, w, "graded", 5).astype(np.complex64)
+    eps = 1e-5
+    P, sig = nh.la_tsvd(torch.from_numpy(C).cuda(), eps)
+    P = P.cpu().numpy().astype(np.complex128)
+    C64 = C.astype(np.complex128)
+    s_ref = np.linalg.svd(C64, compute_uv=False)
+    k = P.shape[1]
+    assert abs(k - int(np.sum(s_ref > eps * s_ref[0]))) <= 2
+    assert np.max(np.abs(np.array(sig[:k]) - s_ref[:k])) < 1e-5 * s_ref[0]
+    assert np.max(np.abs(P.conj().T @ P - np.eye(k))) < 1e-5
+    resid = C64 - P @ (P.conj().T @ C64)
+    assert np.linalg.norm(resid, 2) <= 5 * eps * s_ref[0]
+
+
+@pytest.mark.parametrize("m,n", [(100, 60), (40, 100), (2000, 300), (5000, 100), (9000, 40)])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_qr(nh, m, n, dtype):
+    A = _rand((m, n), m + n)
+    dt = torch.complex128 if dtype == "fp64" else torch.complex64
+    tol = 1e-12 if dtype == "fp64" else 2e-5
+    Q, R = nh.la_qr(torch.from_numpy(A).to(dt).cuda())
+    Q = Q.cpu().numpy().astype(np.complex128)
+    R = R.cpu().numpy().astype(np.complex128)
+    A64 = A.astype(dt == torch.complex128 and np.complex128 or np.complex64).astype(np.complex128)
+    assert np.max(np.abs(Q @ R - A64)) < tol * np.max(np.abs(A64)) * 10
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(m))) < tol * 10
+    p = min(m, n)
+    Rl = np.linalg.qr(A64, mode="r")
+    assert np.max(np.abs(np.abs(np.diag(R[:p, :p])) - np.abs(np.diag(Rl[:p, :p])))) < tol * 10 * np.max(np.abs(A64)) * np.sqrt(m)

@@ -145,3 +145,21 @@ def test_points_outside_unit_square_rejected(nh):
     with pytest.raises(nh.NudftError) as e:
         nh.NudftHSS(x, y, 16, 16, levels=2)
     assert e.value.code == 1
+
+
+# ------------------------------------------------------------------ URV exactness (Sec. 2.3)
+@pytest.mark.parametrize("name,levels", [("fp64_n32", 3), ("fp64_n32", 2), ("fp64_n64", 3)])
+def test_urv_solves_its_own_hss_matrix_exactly(nh, name, levels):
+    """For f' = A_fast c (consistent with the HSS matrix), the URV least-squares solution is c.
+
+    Isolates the URV factorization and sweeps from the approximation error of the HSS
+    construction: only rounding remains (the HSS matrix has full column rank here).
+    """
+    w = WORKLOADS[name]
+    x, y, ct = make_workload(w)
+    h = nh.NudftHSS(x, y, w.nx, w.ny, eps=w.eps, levels=levels).factor()
+    c = torch.from_numpy(ct).cuda()
+    fa = h.apply(nh.FAST_FWD, c)
+    c2 = h.solve(fa)
+    assert relerr_cols(to_np(c2), ct) < 1e-10
+    h.close()
