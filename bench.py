@@ -189,9 +189,7 @@ def run_ours(args, w):
     yt = torch.from_numpy(y).to(dev)
     ctt = torch.from_numpy(ct).to(dev)
     # right-hand side f = A c_true (+ noise) formed with the exact FP64 apply of the library
-    h0 = nh.NudftHSS(xt, yt, w.nx, w.ny, eps=eps, levels=1)
-    f = h0.apply(nh.EXACT_FWD, ctt)
-    h0.close()
+    f = nh.exact_apply(xt, yt, w.nx, w.ny, nh.EXACT_FWD, ctt)
     if w.noise:
         f = f + torch.from_numpy(noise_like(f.cpu().numpy(), w.noise, w.seed + 7)).to(dev)
     stream = torch.cuda.current_stream()

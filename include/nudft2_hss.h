@@ -128,6 +128,14 @@ nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int*
 /* Release every device allocation of the handle.  NULL is ignored. */
 void nudft2_hss_free(nudft2_hss_t h);
 
+/* Direct O(MN) apply of A (Eq. 1) without building an HSS approximation, in FP64:
+ * op = NUDFT2_EXACT_FWD: d_out (M x nrhs, ld ldo >= M) = A d_in (N x nrhs, ld ldi >= N);
+ * op = NUDFT2_EXACT_ADJ: d_out (N x nrhs) = A^* d_in (M x nrhs).  Complex128, column major,
+ * lexicographic frequency order ky + kx*ny.  Allocates and frees its own workspace.
+ * Errors: EINVAL (bad sizes or op), ENOMEM, ECUDA. */
+nudft2_status nudft2_exact_apply(const double* d_x, const double* d_y, int64_t M, int nx, int ny, int op,
+                                 const void* d_in, int64_t ldi, int nrhs, void* d_out, int64_t ldo, void* stream);
+
 /* Entries of the transformed 1D matrix A^x (F^x)^{-1} (Sec. 2.4, the Cauchy-like kernel
  * Psi(gamma_j, xi_k) = (1/n)((gamma_j/xi_k)^n - 1)/((gamma_j/xi_k) - 1), Psi = 1 at gamma = xi).
  * d_x: M points (device), d_out: M x n complex128 column major (ld M).  Errors: EINVAL. */
@@ -144,9 +152,11 @@ nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t
                              int64_t ldp, int* rank, double* h_sigma, void* stream);
 
 /* nudft2_la_qr: Householder QR of A (m x n, ld lda) in place (R in the upper trapezoid) and the
- * explicit unitary factor Q (m x m, ld ldq) written to d_q.  Errors: EINVAL. */
+ * explicit unitary factor Q (m x m, ld ldq) written to d_q, applying the reflectors panel by panel
+ * (grouped = 0) or through the merged 256-column compact-WY blocks (grouped = 1).
+ * Errors: EINVAL. */
 nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
-                           void* stream);
+                           int grouped, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* nudft2_last_error(void);

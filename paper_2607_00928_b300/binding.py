@@ -71,10 +71,11 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_kstats.argtypes = [vp, ctypes.POINTER(KStat), ci, ctypes.POINTER(ci)]
     L.nudft2_la_tsvd.argtypes = [ci, vp, i64, i64, i64, ctypes.c_double, vp, i64, ctypes.POINTER(ci),
                                  ctypes.POINTER(ctypes.c_double), vp]
-    L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, vp]
+    L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, ci, vp]
+    L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr"):
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_exact_apply"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -107,6 +108,22 @@ def psi_eval(x: torch.Tensor, n: int) -> torch.Tensor:
     return out.t()
 
 
+def exact_apply(x, y, nx: int, ny: int, op: int, v: torch.Tensor) -> torch.Tensor:
+    """Direct FP64 apply of A (op=EXACT_FWD, v: (N,s)) or A^* (op=EXACT_ADJ, v: (M,s)) without an HSS."""
+    x = torch.as_tensor(x).to(device="cuda", dtype=torch.float64).contiguous()
+    y = torch.as_tensor(y).to(device="cuda", dtype=torch.float64).contiguous()
+    M, N = x.numel(), nx * ny
+    rows_in, rows_out = (N, M) if op == EXACT_FWD else (M, N)
+    squeeze = v.dim() == 1
+    vc = _colmajor(v, rows_in)
+    s = vc.shape[0]
+    out = torch.empty((s, rows_out), dtype=torch.complex128, device="cuda")
+    _check(lib().nudft2_exact_apply(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), M, nx, ny, op,
+                                    ctypes.c_void_p(vc.data_ptr()), rows_in, s, ctypes.c_void_p(out.data_ptr()),
+                                    rows_out, _stream()))
+    return out[0] if squeeze else out.t()
+
+
 def la_tsvd(C: torch.Tensor, eps: float):
     """Truncated SVD of C (r x w) by the library's QR + one-sided Jacobi: (P, sigma)."""
     r, w = C.shape
@@ -122,7 +139,7 @@ def la_tsvd(C: torch.Tensor, eps: float):
     return P[: rank.value].t(), [sig[i] for i in range(p)]
 
 
-def la_qr(A: torch.Tensor):
+def la_qr(A: torch.Tensor, grouped: bool = False):
     """Householder QR of A (m x n) by the library: (Q m x m, R m x n)."""
     m, n = A.shape
     dt = A.dtype
@@ -130,7 +147,7 @@ def la_qr(A: torch.Tensor):
     a = A.t().contiguous()                          # column major
     q = torch.empty((m, m), dtype=dt, device="cuda")
     _check(lib().nudft2_la_qr(prec, ctypes.c_void_p(a.data_ptr()), m, n, m, ctypes.c_void_p(q.data_ptr()), m,
-                              _stream()))
+                              int(grouped), _stream()))
     return q.t(), torch.triu(a.t())
 
 

@@ -57,46 +57,61 @@ static GemmD<double> g64(const double2* A, int lda, int opA, const double2* B, i
 }
 
 // ----------------------------------------------------------------------------- exact apply (Eq. 1)
+// Twiddle tables Ax(j,k) = exp(-2 pi i k x_j) (M x nx), Ay (M x ny), caller point order.
+struct Exact {
+  int M, nx, ny;
+  const double2 *Ax, *Ay;
+};
+
 // f_j = sum_kx Ax(j,kx) sum_ky Ay(j,ky) c(kx,ky): inner sum as a GEMM Ay * C (C viewed ny x nx).
-static void exact_fwd(nudft2_hss_s* h, const double2* c, int64_t ldc, int s, double2* f, int64_t ldf) {
-  const int M = h->M, nx = h->nx, ny = h->ny, N = h->N;
+static void exact_fwd_impl(Ops<double>& ops, Arena& scr, cudaStream_t st, const Exact& e, const double2* c,
+                           int64_t ldc, int s, double2* f, int64_t ldf) {
+  const int M = e.M, nx = e.nx, ny = e.ny, N = nx * ny;
   const int sc = std::max(1, std::min(s, (int)std::max<int64_t>(1, ((int64_t)1 << 31) / ((int64_t)M * nx * 16))));
-  auto mk = h->scr.mark();
-  double2* T = h->scr.arr<double2>((size_t)M * nx * sc);
-  double2* Cc = (ldc == N) ? nullptr : h->scr.arr<double2>((size_t)N * sc);
+  auto mk = scr.mark();
+  double2* T = scr.arr<double2>((size_t)M * nx * sc);
+  double2* Cc = (ldc == N) ? nullptr : scr.arr<double2>((size_t)N * sc);
   for (int q0 = 0; q0 < s; q0 += sc) {
     const int qs = std::min(sc, s - q0);
     const double2* C = c + (size_t)q0 * ldc;
     if (Cc) {
       NH_CK(cudaMemcpy2DAsync(Cc, N * sizeof(double2), C, ldc * sizeof(double2), N * sizeof(double2), qs,
-                              cudaMemcpyDeviceToDevice, h->st));
+                              cudaMemcpyDeviceToDevice, st));
       C = Cc;
     }
-    h->ops->gemm({g64(h->Ay, M, OP_N, C, ny, OP_N, T, M, M, nx * qs, ny)});
-    rowdot(h->st, h->Ax, M, T, M, M, nx, qs, f + (size_t)q0 * ldf, (int)ldf);
-    h->ops->count();
+    ops.gemm({GemmD<double>{e.Ay, C, T, M, nx * qs, ny, M, ny, M, OP_N, OP_N, 1.0, 0.0}});
+    rowdot(st, e.Ax, M, T, M, M, nx, qs, f + (size_t)q0 * ldf, (int)ldf);
+    ops.count();
   }
-  h->scr.release(mk);
+  scr.release(mk);
 }
 
 // (A^* f)(kx, ky) = sum_j conj(Ay(j,ky)) * (f_j conj(Ax(j,kx))): GEMM Ay^* Z, Z = f o conj(Ax).
-static void exact_adj(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* out, int64_t ldo) {
-  const int M = h->M, nx = h->nx, ny = h->ny, N = h->N;
+static void exact_adj_impl(Ops<double>& ops, Arena& scr, cudaStream_t st, const Exact& e, const double2* f,
+                           int64_t ldf, int s, double2* out, int64_t ldo) {
+  const int M = e.M, nx = e.nx, ny = e.ny, N = nx * ny;
   const int sc = std::max(1, std::min(s, (int)std::max<int64_t>(1, ((int64_t)1 << 31) / ((int64_t)M * nx * 16))));
-  auto mk = h->scr.mark();
-  double2* Z = h->scr.arr<double2>((size_t)M * nx * sc);
-  double2* Oc = (ldo == N) ? nullptr : h->scr.arr<double2>((size_t)N * sc);
+  auto mk = scr.mark();
+  double2* Z = scr.arr<double2>((size_t)M * nx * sc);
+  double2* Oc = (ldo == N) ? nullptr : scr.arr<double2>((size_t)N * sc);
   for (int q0 = 0; q0 < s; q0 += sc) {
     const int qs = std::min(sc, s - q0);
-    nh::scale_rows_conj_multi(h->st, h->Ax, M, f + (size_t)q0 * ldf, (int)ldf, M, nx, qs, Z, M);
-    h->ops->count();
+    scale_rows_conj_multi(st, e.Ax, M, f + (size_t)q0 * ldf, (int)ldf, M, nx, qs, Z, M);
+    ops.count();
     double2* O = Oc ? Oc : out + (size_t)q0 * ldo;
-    h->ops->gemm({g64(h->Ay, M, OP_C, Z, M, OP_N, O, ny, ny, nx * qs, M)});
+    ops.gemm({GemmD<double>{e.Ay, Z, O, ny, nx * qs, M, M, M, ny, OP_C, OP_N, 1.0, 0.0}});
     if (Oc)
       NH_CK(cudaMemcpy2DAsync(out + (size_t)q0 * ldo, ldo * sizeof(double2), Oc, N * sizeof(double2),
-                              N * sizeof(double2), qs, cudaMemcpyDeviceToDevice, h->st));
+                              N * sizeof(double2), qs, cudaMemcpyDeviceToDevice, st));
   }
-  h->scr.release(mk);
+  scr.release(mk);
+}
+
+static void exact_fwd(nudft2_hss_s* h, const double2* c, int64_t ldc, int s, double2* f, int64_t ldf) {
+  exact_fwd_impl(*h->ops, h->scr, h->st, Exact{h->M, h->nx, h->ny, h->Ax, h->Ay}, c, ldc, s, f, ldf);
+}
+static void exact_adj(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* out, int64_t ldo) {
+  exact_adj_impl(*h->ops, h->scr, h->st, Exact{h->M, h->nx, h->ny, h->Ax, h->Ay}, f, ldf, s, out, ldo);
 }
 
 // c = F^{-1} y per column: C = Fy^{-1} Y Fx^{-1} with Y viewed ny x nx (lexicographic order)
@@ -155,7 +170,7 @@ static void la_tsvd(void* d_ct, int w, int r, int ldct, double eps, void* d_p, i
 }
 
 template <typename R>
-static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, cudaStream_t st) {
+static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, int grouped, cudaStream_t st) {
   Arena scr, keep;
   scr.set_stream(st);
   keep.set_stream(st);
@@ -163,6 +178,7 @@ static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, cudaStre
   Mat<R> A;
   A.p = (cplx<R>*)d_a; A.m = m; A.n = n; A.ld = lda;
   auto Q = ops.qr({A}, keep);
+  if (grouped) ops.group_wy(Q, keep);
   Mat<R> Qm;
   Qm.p = (cplx<R>*)d_q; Qm.m = m; Qm.n = m; Qm.ld = ldq;
   ops.set_identity({Qm});
@@ -183,6 +199,33 @@ nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, 
     Ops<double> ops((cudaStream_t)stream, &scr);
     psi_eval<double>(ops, {PsiD<double>{d_x, (int)M, 0, n, n, (double2*)d_out, (int)M}});
     NH_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+nudft2_status nudft2_exact_apply(const double* d_x, const double* d_y, int64_t M, int nx, int ny, int op,
+                                 const void* d_in, int64_t ldi, int nrhs, void* d_out, int64_t ldo, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(d_x && d_y && d_in && d_out && M >= 1 && nx >= 1 && ny >= 1 && nrhs >= 0 && M < (1LL << 31),
+               ST_EINVAL, "exact_apply: bad arguments");
+    NH_REQUIRE(op == NUDFT2_EXACT_FWD || op == NUDFT2_EXACT_ADJ, ST_EINVAL, "exact_apply: op must be EXACT_FWD/ADJ");
+    const int64_t N = (int64_t)nx * ny;
+    NH_REQUIRE(op == NUDFT2_EXACT_FWD ? (ldi >= N && ldo >= M) : (ldi >= M && ldo >= N), ST_EINVAL,
+               "exact_apply: leading dimension too small");
+    if (nrhs == 0) return;
+    cudaStream_t st = (cudaStream_t)stream;
+    Arena scr;
+    scr.set_stream(st);
+    Ops<double> ops(st, &scr);
+    double2* Ax = scr.arr<double2>((size_t)M * nx);
+    double2* Ay = scr.arr<double2>((size_t)M * ny);
+    twiddle_table(st, d_x, (int)M, nx, Ax);
+    twiddle_table(st, d_y, (int)M, ny, Ay);
+    const Exact e{(int)M, nx, ny, Ax, Ay};
+    if (op == NUDFT2_EXACT_FWD)
+      exact_fwd_impl(ops, scr, st, e, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
+    else
+      exact_adj_impl(ops, scr, st, e, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
+    NH_CK(cudaStreamSynchronize(st));
   });
 }
 
@@ -444,11 +487,13 @@ nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t
 }
 
 nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
-                           void* stream) {
+                           int grouped, void* stream) {
   return guard([&] {
     NH_REQUIRE(d_a && d_q && m >= 1 && n >= 1 && lda >= m && ldq >= m, ST_EINVAL, "la_qr: bad arguments");
-    if (prec == NUDFT2_FP64) la_qr<double>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, (cudaStream_t)stream);
-    else la_qr<float>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, (cudaStream_t)stream);
+    if (prec == NUDFT2_FP64)
+      la_qr<double>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, grouped, (cudaStream_t)stream);
+    else
+      la_qr<float>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, grouped, (cudaStream_t)stream);
   });
 }
 

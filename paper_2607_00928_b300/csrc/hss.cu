@@ -783,13 +783,14 @@ template <typename R> void Hss<R>::factor() {
     }
     if (!Aq.empty()) {
       auto Q = ops_.qr(Aq, keep_);
+      ops_.group_wy(Q, keep_);
       for (size_t i = 0; i < qi.size(); ++i) t_[l][qi[i]].Om = Q[i];
     }
     // 2. basis elimination: V = Q_v [V2; 0] (standard QR; columns of D Q_v reordered so the
     //    eliminated block comes first, Sec. 2.3 Eq. for basis elimination)
     {
-      NH_REQUIRE(true, 0, "");
       auto Q = ops_.qr(Vs, keep_);
+      ops_.group_wy(Q, keep_);
       std::vector<CopyD<R>> c2;
       std::vector<Mat<R>> Dc;
       for (int p = 0; p < nn; ++p) {
@@ -816,6 +817,7 @@ template <typename R> void Hss<R>::factor() {
         A2.push_back(nd.Wk.block(0, 0, nd.mc, nd.ku + nd.kv));
       }
       auto Q = ops_.qr(A1, keep_);
+      ops_.group_wy(Q, keep_);
       for (int p = 0; p < nn; ++p) t_[l][p].P = Q[p];
       // [U1; U2], [D12; D22] = P^* [U D~2]
       ops_.apply_q_left(Q, A2, true);
@@ -865,6 +867,7 @@ template <typename R> void Hss<R>::factor() {
     ops_.gemm(g1);
     ops_.gemm(g2);
     auto Q = ops_.qr({Droot_}, keep_);
+    ops_.group_wy(Q, keep_);
     Proot_ = Q[0];
     Rinv_ = keep_.mat<R>(cols, cols);
     ops_.trinv({Droot_.block(0, 0, cols, cols)}, {Rinv_});

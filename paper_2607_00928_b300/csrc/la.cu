@@ -90,17 +90,32 @@ void Prof::collect() {
 // =============================================================================== GEMM
 // C = alpha op(A) op(B) + beta C.  One CTA per BM x BN output tile of one problem; tiles of
 // all problems are numbered consecutively (exclusive prefix `pre`).
+// Split-k: problem pi has ks[pi] k-chunks; chunk s writes its unscaled partial tile to
+// ws[pi] + s*m*n and k_gemm_reduce sums the chunks in order (deterministic).
 template <typename R, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, const int* __restrict__ pre,
-                                              int np) {
+                                              int np, const int* __restrict__ ks, cplx<R>* const* __restrict__ ws) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
   constexpr int LA = BM * BK / 256, LB = BN * BK / 256;   // elements each thread stages per k tile
   __shared__ cplx<R> As[BK][BM + 1];
   __shared__ cplx<R> Bs[BK][BN + 1];
   const int pi = find_prob(pre, np, blockIdx.x);
-  const GemmD<R> g = ds[pi];
-  const int lt = blockIdx.x - pre[pi];
+  GemmD<R> g = ds[pi];
+  int lt = blockIdx.x - pre[pi];
   const int tiles_m = (g.m + BM - 1) / BM;
+  const int tiles_mn = tiles_m * ((g.n + BN - 1) / BN);
+  const int nsplit = ks ? ks[pi] : 1;
+  const int split = lt / tiles_mn;
+  lt -= split * tiles_mn;
+  int kbeg = 0;
+  if (nsplit > 1) {
+    const int kc = (((g.k + nsplit - 1) / nsplit) + BK - 1) / BK * BK;
+    kbeg = split * kc;
+    const int kend = min(g.k, kbeg + kc);
+    g.A = (g.opA == OP_N) ? g.A + (size_t)kbeg * g.lda : g.A + kbeg;
+    g.B = (g.opB == OP_N) ? g.B + kbeg : g.B + (size_t)kbeg * g.ldb;
+    g.k = max(0, kend - kbeg);
+  }
   const int row0 = (lt % tiles_m) * BM, col0 = (lt / tiles_m) * BN;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   cplx<R> acc[TM][TN];
@@ -169,6 +184,20 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
     }
     __syncthreads();
   }
+  if (nsplit > 1) {
+    cplx<R>* w = ws[pi] + (size_t)split * g.m * g.n;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      const int i = row0 + ty + 16 * a;
+      if (i >= g.m) continue;
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        const int j = col0 + tx + 16 * b;
+        if (j < g.n) w[(size_t)i + (size_t)j * g.m] = acc[a][b];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < TM; ++a) {
     const int i = row0 + ty + 16 * a;
@@ -183,6 +212,27 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
       *c = v;
     }
   }
+}
+
+// C = alpha * sum_s ws[s] + beta * C for the split problems (elements numbered per problem).
+template <typename R>
+__global__ void k_gemm_reduce(const GemmD<R>* __restrict__ ds, const int* __restrict__ ks,
+                              cplx<R>* const* __restrict__ ws, const int* __restrict__ epre, int np) {
+  const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pi = find_prob(epre, np, blockIdx.x * blockDim.x);
+  // a block may straddle problems: resolve per element
+  int p = pi;
+  while (p + 1 < np && epre[p + 1] <= e0) ++p;
+  const GemmD<R> g = ds[p];
+  const int e = e0 - epre[p];
+  if (ks[p] <= 1 || e >= g.m * g.n) return;
+  const int i = e % g.m, j = e / g.m;
+  cplx<R> s = czero<R>();
+  for (int q = 0; q < ks[p]; ++q) s = s + ws[p][(size_t)q * g.m * g.n + e];
+  cplx<R>* c = g.C + (size_t)i + (size_t)j * g.ldc;
+  cplx<R> v = g.alpha * s;
+  if (g.beta != R(0)) v = v + g.beta * (*c);
+  *c = v;
 }
 
 template <typename R> struct GemmCfg;
@@ -222,14 +272,39 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
     if (prof.on)
       for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
     prof.begin(st_);
-    k_gemm<R, 8, 8, 8><<<t, 256, 0, st_>>>(dd, dp, (int)d.size());
+    k_gemm<R, 8, 8, 8><<<t, 256, 0, st_>>>(dd, dp, (int)d.size(), nullptr, nullptr);
     NH_LAUNCH_CK();
     prof.end(st_, K_GEMM, fl, 0);
     count();
     return;
   }
+  // split long reductions when the output tiles alone cannot fill the GPU
+  std::vector<int> ks(d.size(), 1);
+  bool any_split = false;
+  if (tiles < 2 * 148) {
+    constexpr int BK = GemmCfg<R>::BK;
+    for (size_t i = 0; i < d.size(); ++i) {
+      const GemmD<R>& g = d[i];
+      const int t = ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
+      const int want = std::max(1, (2 * 148) / std::max(tiles, 1));
+      const int kmax_split = std::max(1, g.k / (8 * BK));     // keep >= 8 k tiles per chunk
+      const int sp = std::min(want, kmax_split);
+      if (sp > 1 && (long long)sp * t <= 4096) { ks[i] = sp; any_split = true; }
+    }
+  }
+  std::vector<int> pre2;
+  std::vector<cplx<R>*> wsp(d.size(), nullptr);
+  int tiles2 = 0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const GemmD<R>& g = d[i];
+    pre2.push_back(tiles2);
+    tiles2 += ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN) * ks[i];
+    if (ks[i] > 1) wsp[i] = (cplx<R>*)ar_->alloc((size_t)ks[i] * g.m * g.n * sizeof(cplx<R>));
+  }
   GemmD<R>* dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(ar_, st_, pre2);
+  int* dks = any_split ? upload_ints(ar_, st_, ks) : nullptr;
+  cplx<R>* const* dws = any_split ? upload(wsp) : nullptr;
   double fl = 0, by = 0;
   if (prof.on)
     for (const auto& g : d) {
@@ -237,8 +312,27 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
       by += (double)sizeof(cplx<R>) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != R(0) ? 2.0 : 1.0) * g.m * g.n);
     }
   prof.begin(st_);
-  k_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
+  k_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK><<<tiles2, 256, 0, st_>>>(dd, dp, (int)d.size(), dks, dws);
   NH_LAUNCH_CK();
+  if (any_split) {
+    std::vector<int> epre;
+    int ne = 0;
+    for (size_t i = 0; i < d.size(); ++i) { epre.push_back(ne); ne += (ks[i] > 1) ? d[i].m * d[i].n : 0; }
+    // elements of unsplit problems are skipped inside the kernel; number only the split ones
+    std::vector<GemmD<R>> ds2;
+    std::vector<int> ks2, ep2;
+    std::vector<cplx<R>*> ws2;
+    int n2 = 0;
+    for (size_t i = 0; i < d.size(); ++i)
+      if (ks[i] > 1) { ds2.push_back(d[i]); ks2.push_back(ks[i]); ws2.push_back(wsp[i]); ep2.push_back(n2); n2 += d[i].m * d[i].n; }
+    auto dd2 = upload(ds2);
+    int* dk2 = upload_ints(ar_, st_, ks2);
+    cplx<R>* const* dw2 = upload(ws2);
+    int* de2 = upload_ints(ar_, st_, ep2);
+    k_gemm_reduce<R><<<(n2 + 255) / 256, 256, 0, st_>>>(dd2, dk2, dw2, de2, (int)ds2.size());
+    NH_LAUNCH_CK();
+    count();
+  }
   prof.end(st_, K_GEMM, fl, by);
   count();
 }
@@ -797,32 +891,85 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   return out;
 }
 
+// S = strictly-upper(Y) + diag(1/tau), tau read from the diagonal of the panel T blocks.
+template <typename R> struct GrpD { cplx<R>* Y; const cplx<R>* Tp; int w, g0, ldy; };
+template <typename R> __global__ void k_group_s(const GrpD<R>* __restrict__ ds, int nb) {
+  const GrpD<R> d = ds[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.w * d.w) return;
+  const int i = e % d.w, j = e / d.w;
+  cplx<R>& y = d.Y[(size_t)i + (size_t)j * d.ldy];
+  if (i > j) y = czero<R>();
+  else if (i == j) {
+    const int c = d.g0 + i, p = c / nb, o = c % nb;
+    const R tau = d.Tp[(size_t)p * nb * nb + o + (size_t)o * nb].x;
+    y = mkc(R(1) / tau, R(0));
+  }
+}
+
+template <typename R> void Ops<R>::group_wy(std::vector<QFac<R>>& Q, Arena& keep) {
+  auto mk = ar_->mark();
+  std::vector<GemmD<R>> g;
+  std::vector<GrpD<R>> gd;
+  std::vector<Mat<R>> S, T;
+  int wmax = 0;
+  for (auto& q : Q) {
+    if (q.k <= NB) continue;                      // a single panel is already one block
+    const int ng = (q.k + GW - 1) / GW;
+    q.Tg = (cplx<R>*)keep.alloc((size_t)ng * GW * GW * sizeof(cplx<R>));
+    for (int gi = 0; gi < ng; ++gi) {
+      const int g0 = gi * GW, w = std::min(GW, q.k - g0);
+      Mat<R> Sm = ar_->template mat<R>(w, w);
+      const cplx<R>* Vg = q.V + (size_t)g0 + (size_t)g0 * q.ldv;
+      g.push_back({Vg, Vg, Sm.p, w, w, q.m - g0, q.ldv, q.ldv, Sm.ld, OP_C, OP_N, R(1), R(0)});
+      gd.push_back({Sm.p, q.Tp, w, g0, Sm.ld});
+      S.push_back(Sm);
+      Mat<R> Tm;
+      Tm.p = q.Tg + (size_t)gi * GW * GW; Tm.m = w; Tm.n = w; Tm.ld = GW;
+      T.push_back(Tm);
+      wmax = std::max(wmax, w);
+    }
+  }
+  if (g.empty()) { ar_->release(mk); return; }
+  gemm(g);
+  auto dg = upload(gd);
+  dim3 grid((wmax * wmax + 255) / 256, (unsigned)gd.size());
+  k_group_s<R><<<grid, 256, 0, st_>>>(dg, NB);
+  NH_LAUNCH_CK();
+  count();
+  trinv(S, T);
+  ar_->release(mk);
+}
+
 template <typename R>
 void Ops<R>::apply_q_left(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj) {
-  // Q = Q_0 Q_1 ... (panels); Q^* C applies panels in increasing order, Q C in decreasing order.
+  // Q = Q_0 Q_1 ... (blocks of BW columns: panels, or merged groups when Tg is present);
+  // Q^* C applies blocks in increasing order, Q C in decreasing order.
+  auto bw = [](const QFac<R>& q) { return q.Tg ? GW : NB; };
   int pmax = 0;
-  for (auto& q : Q) pmax = std::max(pmax, (q.k + NB - 1) / NB);
+  for (auto& q : Q) pmax = std::max(pmax, (q.k + bw(q) - 1) / bw(q));
   if (pmax == 0) return;
   auto mk = ar_->mark();
   std::vector<cplx<R>*> W1(Q.size()), W2(Q.size());
   for (size_t i = 0; i < Q.size(); ++i) {
-    W1[i] = (cplx<R>*)ar_->alloc((size_t)NB * std::max(C[i].n, 1) * sizeof(cplx<R>));
-    W2[i] = (cplx<R>*)ar_->alloc((size_t)NB * std::max(C[i].n, 1) * sizeof(cplx<R>));
+    W1[i] = (cplx<R>*)ar_->alloc((size_t)bw(Q[i]) * std::max(C[i].n, 1) * sizeof(cplx<R>));
+    W2[i] = (cplx<R>*)ar_->alloc((size_t)bw(Q[i]) * std::max(C[i].n, 1) * sizeof(cplx<R>));
   }
   for (int s = 0; s < pmax; ++s) {
     std::vector<GemmD<R>> g1, g2, g3;
     for (size_t i = 0; i < Q.size(); ++i) {
       const QFac<R>& q = Q[i];
-      const int np = (q.k + NB - 1) / NB;
+      const int B = bw(q);
+      const int np = (q.k + B - 1) / B;
       if (s >= np || C[i].n <= 0) continue;
       const int p = conj ? s : (np - 1 - s);
-      const int j0 = p * NB, b = std::min(NB, q.k - j0), mm = q.m - j0;
+      const int j0 = p * B, b = std::min(B, q.k - j0), mm = q.m - j0;
       const cplx<R>* Vp = q.V + (size_t)j0 + (size_t)j0 * q.ldv;
-      const cplx<R>* Tp = q.Tp + (size_t)p * NB * NB;
+      const cplx<R>* Tp = (q.Tg ? q.Tg : q.Tp) + (size_t)p * B * B;
       cplx<R>* Cp = C[i].p + j0;
-      g1.push_back({Vp, Cp, W1[i], b, C[i].n, mm, q.ldv, C[i].ld, NB, OP_C, OP_N, R(1), R(0)});
-      g2.push_back({Tp, W1[i], W2[i], b, C[i].n, b, NB, NB, NB, conj ? OP_C : OP_N, OP_N, R(1), R(0)});
-      g3.push_back({Vp, W2[i], Cp, mm, C[i].n, b, q.ldv, NB, C[i].ld, OP_N, OP_N, R(-1), R(1)});
+      g1.push_back({Vp, Cp, W1[i], b, C[i].n, mm, q.ldv, C[i].ld, B, OP_C, OP_N, R(1), R(0)});
+      g2.push_back({Tp, W1[i], W2[i], b, C[i].n, b, B, B, B, conj ? OP_C : OP_N, OP_N, R(1), R(0)});
+      g3.push_back({Vp, W2[i], Cp, mm, C[i].n, b, q.ldv, B, C[i].ld, OP_N, OP_N, R(-1), R(1)});
     }
     gemm(g1);
     gemm(g2);
@@ -833,31 +980,33 @@ void Ops<R>::apply_q_left(const std::vector<QFac<R>>& Q, const std::vector<Mat<R
 
 template <typename R>
 void Ops<R>::apply_q_right(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj) {
-  // C Q = C - (C V) T V^* per panel, panels in increasing order; C Q^* in decreasing order.
+  // C Q = C - (C V) T V^* per block, blocks in increasing order; C Q^* in decreasing order.
+  auto bw = [](const QFac<R>& q) { return q.Tg ? GW : NB; };
   int pmax = 0;
-  for (auto& q : Q) pmax = std::max(pmax, (q.k + NB - 1) / NB);
+  for (auto& q : Q) pmax = std::max(pmax, (q.k + bw(q) - 1) / bw(q));
   if (pmax == 0) return;
   auto mk = ar_->mark();
   std::vector<cplx<R>*> W1(Q.size()), W2(Q.size());
   for (size_t i = 0; i < Q.size(); ++i) {
     const int ld = std::max(C[i].m, 1);
-    W1[i] = (cplx<R>*)ar_->alloc((size_t)ld * NB * sizeof(cplx<R>));
-    W2[i] = (cplx<R>*)ar_->alloc((size_t)ld * NB * sizeof(cplx<R>));
+    W1[i] = (cplx<R>*)ar_->alloc((size_t)ld * bw(Q[i]) * sizeof(cplx<R>));
+    W2[i] = (cplx<R>*)ar_->alloc((size_t)ld * bw(Q[i]) * sizeof(cplx<R>));
   }
   for (int s = 0; s < pmax; ++s) {
     std::vector<GemmD<R>> g1, g2, g3;
     for (size_t i = 0; i < Q.size(); ++i) {
       const QFac<R>& q = Q[i];
-      const int np = (q.k + NB - 1) / NB;
+      const int B = bw(q);
+      const int np = (q.k + B - 1) / B;
       if (s >= np || C[i].m <= 0) continue;
       const int p = conj ? (np - 1 - s) : s;
-      const int j0 = p * NB, b = std::min(NB, q.k - j0), nn = q.m - j0;
+      const int j0 = p * B, b = std::min(B, q.k - j0), nn = q.m - j0;
       const int ld = std::max(C[i].m, 1);
       const cplx<R>* Vp = q.V + (size_t)j0 + (size_t)j0 * q.ldv;
-      const cplx<R>* Tp = q.Tp + (size_t)p * NB * NB;
+      const cplx<R>* Tp = (q.Tg ? q.Tg : q.Tp) + (size_t)p * B * B;
       cplx<R>* Cp = C[i].p + (size_t)j0 * C[i].ld;   // columns j0.. of C
       g1.push_back({Cp, Vp, W1[i], C[i].m, b, nn, C[i].ld, q.ldv, ld, OP_N, OP_N, R(1), R(0)});
-      g2.push_back({W1[i], Tp, W2[i], C[i].m, b, b, ld, NB, ld, OP_N, conj ? OP_C : OP_N, R(1), R(0)});
+      g2.push_back({W1[i], Tp, W2[i], C[i].m, b, b, ld, B, ld, OP_N, conj ? OP_C : OP_N, R(1), R(0)});
       g3.push_back({W2[i], Vp, Cp, C[i].m, nn, b, ld, q.ldv, C[i].ld, OP_N, OP_C, R(-1), R(1)});
     }
     gemm(g1);
@@ -1208,7 +1357,10 @@ __global__ void __launch_bounds__(256) k_svd_sort(const SortD<R>* __restrict__ d
 }
 
 // P(:, i) = X(:, order[i]) / sig[i], i < rank
-template <typename R> struct SelD { const cplx<R>* X; int ld, r; const R* sig; const int* order; cplx<R>* P; int ldp, rank; };
+template <typename R> struct SelD {
+  const cplx<R>* X; int ld, r; const R* sig; const int* order; cplx<R>* P; int ldp, rank;
+  const int* rowperm;   // P(rowperm[t], i) = X(t, order[i]) / sig[i]
+};
 
 template <typename R> __global__ void k_svd_select(const SelD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
   const int pi = find_prob(pre, np, blockIdx.x);
@@ -1216,8 +1368,148 @@ template <typename R> __global__ void k_svd_select(const SelD<R>* __restrict__ d
   const int i = blockIdx.x - pre[pi];   // one CTA per selected column
   const int c = d.order[i];
   const R inv = R(1) / d.sig[i];
-  for (int t = threadIdx.x; t < d.r; t += blockDim.x)
-    d.P[(size_t)t + (size_t)i * d.ldp] = inv * d.X[(size_t)t + (size_t)c * d.ld];
+  for (int t = threadIdx.x; t < d.r; t += blockDim.x) {
+    const int row = d.rowperm ? d.rowperm[t] : t;
+    d.P[(size_t)row + (size_t)i * d.ldp] = inv * d.X[(size_t)t + (size_t)c * d.ld];
+  }
+}
+
+// =============================================================================== pivoted QR
+// Householder QR with column pivoting (Businger-Golub): before step k the column of largest
+// remaining norm is swapped to position k.  Partial norms are downdated after every step and
+// recomputed when cancellation makes the downdate unreliable (the LAPACK xLAQP2 rule).  Used to
+// precondition the one-sided Jacobi SVD: on R^* of a pivoted QR the Jacobi sweeps converge
+// even for strongly graded matrices.
+template <typename R> struct QpD {
+  cplx<R>* A; int lda, m, n;
+  int* perm;       // perm[i] = original column at position i
+  R* vn1; R* vn2;  // partial norms and norms at the last recomputation
+  cplx<R>* v;      // reflector of the current step (m entries)
+  R* tau;          // tau of the current step
+};
+
+template <typename R> __global__ void __launch_bounds__(256) k_qp_init(const QpD<R>* __restrict__ ds) {
+  const QpD<R> d = ds[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + warp;
+  if (j >= d.n) return;
+  R s = 0;
+  for (int i = lane; i < d.m; i += 32) s += abs2(d.A[(size_t)i + (size_t)j * d.lda]);
+  s = warp_sum(s);
+  if (lane == 0) { d.perm[j] = j; d.vn1[j] = sqrt(s); d.vn2[j] = sqrt(s); }
+}
+
+// step k, part 1: pivot, swap, reflector (one CTA per matrix)
+template <typename R> __global__ void __launch_bounds__(256) k_qp_pivot(const QpD<R>* __restrict__ ds, int k) {
+  const QpD<R> d = ds[blockIdx.x];
+  if (k >= min(d.m, d.n)) return;
+  __shared__ R bv[256];
+  __shared__ int bi[256];
+  __shared__ R red[32];
+  __shared__ int jp_s;
+  __shared__ cplx<R> v0_s;
+  __shared__ R nrm_s, tau_s;
+  const int tid = threadIdx.x;
+  R best = -1;
+  int bj = k;
+  for (int j = k + tid; j < d.n; j += 256) {
+    const R v = d.vn1[j];
+    if (v > best) { best = v; bj = j; }
+  }
+  bv[tid] = best;
+  bi[tid] = bj;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) {
+      const R a = bv[tid], b = bv[tid + o];
+      const int ia = bi[tid], ib = bi[tid + o];
+      if (b > a || (b == a && ib < ia)) { bv[tid] = b; bi[tid] = ib; }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) jp_s = bi[0];
+  __syncthreads();
+  const int jp = jp_s;
+  if (jp != k) {
+    cplx<R>* a = d.A + (size_t)k * d.lda;
+    cplx<R>* b = d.A + (size_t)jp * d.lda;
+    for (int i = tid; i < d.m; i += 256) { const cplx<R> t = a[i]; a[i] = b[i]; b[i] = t; }
+    if (tid == 0) {
+      const int tp = d.perm[k]; d.perm[k] = d.perm[jp]; d.perm[jp] = tp;
+      R t = d.vn1[k]; d.vn1[k] = d.vn1[jp]; d.vn1[jp] = t;
+      t = d.vn2[k]; d.vn2[k] = d.vn2[jp]; d.vn2[jp] = t;
+    }
+  }
+  __syncthreads();
+  cplx<R>* x = d.A + (size_t)k * d.lda;
+  R s = 0;
+  for (int i = k + tid; i < d.m; i += 256) s += abs2(x[i]);
+  s = warp_sum(s);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    R t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    const R nrm = sqrt(t);
+    const cplx<R> a0 = x[k];
+    const R aa = sqrt(abs2(a0));
+    const cplx<R> ph = aa > R(0) ? mkc(a0.x / aa, a0.y / aa) : mkc(R(1), R(0));
+    if (nrm == R(0)) {
+      v0_s = mkc(R(0), R(0));
+      tau_s = R(0);                          // nothing to annihilate: H = I
+    } else {
+      v0_s = a0 + nrm * ph;
+      tau_s = R(2) / (R(1) + (t - aa * aa) / abs2(v0_s));
+    }
+    nrm_s = nrm;
+    *d.tau = tau_s;
+    x[k] = (nrm > R(0)) ? mkc(-nrm * ph.x, -nrm * ph.y) : a0;
+    d.v[k] = mkc(R(1), R(0));
+  }
+  __syncthreads();
+  const cplx<R> v0 = v0_s;
+  const R v0a2 = abs2(v0);
+  for (int i = k + 1 + tid; i < d.m; i += 256) {
+    const cplx<R> xv = x[i];
+    d.v[i] = (v0a2 > R(0)) ? mkc((xv.x * v0.x + xv.y * v0.y) / v0a2, (xv.y * v0.x - xv.x * v0.y) / v0a2)
+                           : mkc(R(0), R(0));
+    x[i] = mkc(R(0), R(0));
+  }
+}
+
+// step k, part 2: apply the reflector to columns k+1.. and downdate their norms (warp per column)
+template <typename R> __global__ void __launch_bounds__(256) k_qp_update(const QpD<R>* __restrict__ ds, int k, R tol3z) {
+  const QpD<R> d = ds[blockIdx.y];
+  if (k >= min(d.m, d.n)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = k + 1 + blockIdx.x * 8 + warp;
+  if (j >= d.n) return;
+  const R tau = *d.tau;
+  cplx<R>* y = d.A + (size_t)j * d.lda;
+  if (tau != R(0)) {
+    cplx<R> w = czero<R>();
+    for (int i = k + lane; i < d.m; i += 32) cfmac(w, d.v[i], y[i]);
+    w.x = warp_sum(w.x);
+    w.y = warp_sum(w.y);
+    w = tau * w;
+    for (int i = k + lane; i < d.m; i += 32) y[i] = y[i] - d.v[i] * w;
+  }
+  __syncwarp();
+  R vn1 = d.vn1[j];
+  if (vn1 != R(0)) {
+    const R a = sqrt(abs2(y[k])) / vn1;
+    R temp = fmax(R(0), (R(1) + a) * (R(1) - a));
+    const R ratio = vn1 / d.vn2[j];
+    if (temp * ratio * ratio <= tol3z) {
+      R s = 0;
+      for (int i = k + 1 + lane; i < d.m; i += 32) s += abs2(y[i]);
+      s = warp_sum(s);
+      vn1 = sqrt(s);
+      if (lane == 0) { d.vn1[j] = vn1; d.vn2[j] = vn1; }
+    } else if (lane == 0) {
+      d.vn1[j] = vn1 * sqrt(temp);
+    }
+  }
 }
 
 template <typename R>
@@ -1227,11 +1519,51 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   P.assign(nm, Mat<R>());
   S.assign(nm, {});
   auto mk = ar_->mark();
-  // 1. QR of Ct (w x r) -> R factor (p x r), p = min(w, r)
-  Arena tmpk;
-  tmpk.set_stream(st_);
-  auto fac = qr(Ct, tmpk);
-  // 2. X = R^* (r x p), lower part of R ignored (k_qr zeroes it)
+  // 1. pivoted QR of Ct (w x r): Ct Pi = Q R, R (p x r), p = min(w, r).  Then
+  //    C = Pi R^* Q^*, so the left singular vectors of C are Pi times those of R^*.
+  std::vector<QpD<R>> qp;
+  std::vector<int*> perms(nm, nullptr);
+  int pmax = 0, nmax = 0;
+  for (size_t i = 0; i < nm; ++i) {
+    const int w = Ct[i].m, r = Ct[i].n;
+    perms[i] = ar_->template arr<int>(std::max(r, 1));
+    if (w <= 0 || r <= 0) continue;
+    QpD<R> q;
+    q.A = Ct[i].p; q.lda = Ct[i].ld; q.m = w; q.n = r;
+    q.perm = perms[i];
+    q.vn1 = ar_->template arr<R>(r);
+    q.vn2 = ar_->template arr<R>(r);
+    q.v = ar_->template arr<cplx<R>>(w);
+    q.tau = ar_->template arr<R>(1);
+    qp.push_back(q);
+    pmax = std::max(pmax, std::min(w, r));
+    nmax = std::max(nmax, r);
+  }
+  if (!qp.empty()) {
+    auto dq = upload(qp);
+    const R tol3z = (R)std::sqrt(sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.960464477539063e-08);
+    dim3 gi((nmax + 7) / 8, (unsigned)qp.size());
+    k_qp_init<R><<<gi, 256, 0, st_>>>(dq);
+    NH_LAUNCH_CK();
+    count();
+    double fl = 0;
+    if (prof.on)
+      for (auto& q : qp) fl += 8.0 * (double)q.m * q.n * std::min(q.m, q.n);
+    prof.begin(st_);
+    for (int k = 0; k < pmax; ++k) {
+      k_qp_pivot<R><<<(int)qp.size(), 256, 0, st_>>>(dq, k);
+      NH_LAUNCH_CK();
+      const int cols = nmax - k - 1;
+      if (cols > 0) {
+        dim3 gu((cols + 7) / 8, (unsigned)qp.size());
+        k_qp_update<R><<<gu, 256, 0, st_>>>(dq, k, tol3z);
+        NH_LAUNCH_CK();
+      }
+      count(2);
+    }
+    prof.end(st_, K_QR_PANEL, fl, 0);
+  }
+  // 2. X = R^* (r x p) (the pivoted QR zeroes the part below the diagonal)
   std::vector<Mat<R>> X(nm);
   std::vector<CopyD<R>> cp;
   for (size_t i = 0; i < nm; ++i) {
@@ -1258,6 +1590,15 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     maxblk = std::max(maxblk, nb);
   }
   const double u = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+  std::vector<std::vector<cplx<R>>> init_copy;
+  if (std::getenv("NH_DUMP_TSVD")) {
+    NH_CK(cudaStreamSynchronize(st_));
+    for (auto& j : jd) {
+      init_copy.emplace_back((size_t)j.r * j.k);
+      NH_CK(cudaMemcpy2D(init_copy.back().data(), (size_t)j.r * sizeof(cplx<R>), j.X, (size_t)j.ld * sizeof(cplx<R>),
+                         (size_t)j.r * sizeof(cplx<R>), j.k, cudaMemcpyDeviceToHost));
+    }
+  }
   if (!jd.empty()) {
     auto djd = upload(jd);
     std::vector<unsigned> hoff(nm);
@@ -1268,13 +1609,13 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     // cluster-resident rounds when a block pair's row slab fits in shared memory
     const int rpc = (rmax + JCS - 1) / JCS;
     const size_t jsmem = (size_t)32 * rpc * sizeof(cplx<R>);
-    const bool use_cluster = jsmem <= (size_t)200 * 1024 && std::getenv("NH_JACOBI_GLOBAL") == nullptr;
+    const bool use_cluster = jsmem <= (size_t)200 * 1024 && std::getenv("NH_JACOBI_CLUSTER") != nullptr;
     if (use_cluster)
       NH_CK(cudaFuncSetAttribute(k_jacobi_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(jsmem, 1)));
     // columns with norm <= delta * (largest column norm) are numerically zero; delta sits well
     // below the truncation threshold eps so no retained direction is affected
-    const double delta = std::max(0.1 * eps, 8.0 * u);
+    const double delta = 0.1 * eps;
     const R negl2 = (R)(delta * delta);
     for (int sweep = 0; sweep < 40; ++sweep) {
       NH_CK(cudaMemsetAsync(offs, 0, nm * sizeof(unsigned), st_));
@@ -1311,6 +1652,15 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
       prof.end(st_, K_JACOBI, fl, 0);
       NH_CK(cudaMemcpyAsync(hoff.data(), offs, nm * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
       NH_CK(cudaStreamSynchronize(st_));
+      if (std::getenv("NH_DEBUG") && std::atoi(std::getenv("NH_DEBUG")) >= 2) {
+        float w = 0;
+        for (size_t q = 0; q < jd.size(); ++q) {
+          float f;
+          std::memcpy(&f, &hoff[jmap[q]], 4);
+          if (!hdone[jmap[q]]) w = std::max(w, f);
+        }
+        std::fprintf(stderr, "[tsvd] sweep %d max_off %.3e (rmax %d)\n", sweep, w, rmax);
+      }
       bool all = true;
       for (size_t q = 0; q < jd.size(); ++q) {
         const int i = jmap[q];
@@ -1326,9 +1676,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
           for (size_t q = 0; q < jd.size(); ++q) {
             if (hdone[jmap[q]]) continue;
             const JacD<R>& j = jd[q];
-            std::vector<cplx<R>> hx((size_t)j.r * j.k);
-            NH_CK(cudaMemcpy2D(hx.data(), (size_t)j.r * sizeof(cplx<R>), j.X, (size_t)j.ld * sizeof(cplx<R>),
-                               (size_t)j.r * sizeof(cplx<R>), j.k, cudaMemcpyDeviceToHost));
+            std::vector<cplx<R>>& hx = init_copy[q];    // the input of the sweeps
             FILE* fp = std::fopen(std::getenv("NH_DUMP_TSVD"), "wb");
             if (fp) {
               int hdr[3] = {j.r, j.k, (int)sizeof(R)};
@@ -1392,7 +1740,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     const int rk = (X[i].n > 0 && r > 0) ? hr[i] : 0;
     P[i] = keep.template mat<R>(r, rk);
     if (rk > 0) {
-      sel.push_back({X[i].p, X[i].ld, r, sig[i], order[i], P[i].p, P[i].ld, rk});
+      sel.push_back({X[i].p, X[i].ld, r, sig[i], order[i], P[i].p, P[i].ld, rk, perms[i]});
       pre.push_back(tot);
       tot += rk;
       hs[i].resize(rk);
@@ -1408,7 +1756,6 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   }
   NH_CK(cudaStreamSynchronize(st_));
   for (size_t i = 0; i < nm; ++i) S[i].assign(hs[i].begin(), hs[i].end());
-  tmpk.free_all();
   ar_->release(mk);
 }
 

@@ -60,10 +60,12 @@ template <typename R> struct QRD {
   cplx<R>* W;    // scratch 2*nb x n
 };
 
-// A QR factor kept for later applications: Q = H_0 ... H_{k-1}, applied panel by panel.
+// A QR factor kept for later applications: Q = H_0 ... H_{k-1}, applied panel by panel, or
+// -- after group_wy() -- by groups of GW columns with one merged compact-WY T per group.
 template <typename R> struct QFac {
   cplx<R>* V = nullptr; int ldv = 1; int m = 0, k = 0;
   cplx<R>* Tp = nullptr;
+  cplx<R>* Tg = nullptr;   // ceil(k/GW) blocks of GW*GW when grouped
 };
 
 // Per-kernel-class accounting (CUDA events around each launch on the launching stream),
@@ -96,6 +98,7 @@ template <typename R> class Ops {
   cudaStream_t stream() const { return st_; }
   Arena* scratch() { return ar_; }
   static constexpr int NB = 32;   // Householder panel width
+  static constexpr int GW = 256;  // columns per merged compact-WY group used for applications
 
   void gemm(const std::vector<GemmD<R>>& d);
   void copy(const std::vector<CopyD<R>>& d);
@@ -105,6 +108,9 @@ template <typename R> class Ops {
   void set_identity(const std::vector<Mat<R>>& d);   // zero then unit diagonal
   // Householder QR of every A in place; returns the stored factors (V, Tp from the arena `keep`).
   std::vector<QFac<R>> qr(const std::vector<Mat<R>>& A, Arena& keep);
+  // Merge the panel T's of every factor into one T per group of GW columns:
+  // T_g = (striu(V_g^* V_g) + diag(1/tau))^{-1} (the compact-WY identity), from `keep`.
+  void group_wy(std::vector<QFac<R>>& Q, Arena& keep);
   // C <- Q C (conj=false) or Q^* C (conj=true), from the left.  C has Q.m rows.
   void apply_q_left(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
   // C <- C Q (conj=false) or C Q^*, from the right.  C has Q.m columns.

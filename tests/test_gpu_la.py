@@ -51,8 +51,8 @@ CASES = [(64, 200, "graded"), (300, 120, "graded"), (520, 1500, "graded"), (1577
 @pytest.mark.parametrize("jacobi", ["cluster", "global"])
 @pytest.mark.parametrize("r,w,kind", CASES)
 def test_tsvd_fp64(nh, monkeypatch, jacobi, r, w, kind):
-    if jacobi == "global":
-        monkeypatch.setenv("NH_JACOBI_GLOBAL", "1")
+    if jacobi == "cluster":
+        monkeypatch.setenv("NH_JACOBI_CLUSTER", "1")
     C = make_matrix(r, w, kind, r + w)
     eps = 1e-10
     P, sig = nh.la_tsvd(torch.from_numpy(C).cuda(), eps)
@@ -82,13 +82,14 @@ def test_tsvd_fp32(nh, r, w):
     assert np.linalg.norm(resid, 2) <= 5 * eps * s_ref[0]
 
 
-@pytest.mark.parametrize("m,n", [(100, 60), (40, 100), (2000, 300), (5000, 100), (9000, 40)])
+@pytest.mark.parametrize("m,n,grouped", [(100, 60, False), (40, 100, False), (2000, 300, False), (5000, 100, False),
+                                         (9000, 40, False), (2000, 600, True), (700, 700, True), (300, 1000, True)])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
-def test_qr(nh, m, n, dtype):
+def test_qr(nh, m, n, grouped, dtype):
     A = _rand((m, n), m + n)
     dt = torch.complex128 if dtype == "fp64" else torch.complex64
     tol = 1e-12 if dtype == "fp64" else 2e-5
-    Q, R = nh.la_qr(torch.from_numpy(A).to(dt).cuda())
+    Q, R = nh.la_qr(torch.from_numpy(A).to(dt).cuda(), grouped=grouped)
     Q = Q.cpu().numpy().astype(np.complex128)
     R = R.cpu().numpy().astype(np.complex128)
     A64 = A.astype(dt == torch.complex128 and np.complex128 or np.complex64).astype(np.complex128)

@@ -163,3 +163,14 @@ def test_urv_solves_its_own_hss_matrix_exactly(nh, name, levels):
     c2 = h.solve(fa)
     assert relerr_cols(to_np(c2), ct) < 1e-10
     h.close()
+
+
+def test_standalone_exact_apply_matches_oracle(nh):
+    nx, ny = 20, 12
+    x, y = jittered_grid(37, 13, -0.3, 0.3, 444)
+    c = complex_normal((nx * ny, 3), 445)
+    f = to_np(nh.exact_apply(x, y, nx, ny, nh.EXACT_FWD, torch.from_numpy(c)))
+    assert relerr_cols(f, orc.forward(x, y, c, nx, ny)) < 1e-12
+    g = complex_normal((x.size, 2), 446)
+    a = to_np(nh.exact_apply(x, y, nx, ny, nh.EXACT_ADJ, torch.from_numpy(g)))
+    assert relerr_cols(a, orc.adjoint(x, y, g, nx, ny)) < 1e-12
