@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -15,10 +16,24 @@ using namespace nh;
 
 static thread_local std::string g_err;
 
+// One captured URV solve (Sec. 2.3 sweeps) for a fixed number of right-hand sides: fixed
+// input/output buffers, the instantiated graph and the pinned descriptor copies it reads.
+template <typename R> struct SolveGraph {
+  cplx<R>* f2 = nullptr;
+  cplx<R>* yt = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool failed = false;
+  PinnedPool pool;
+  ~SolveGraph() { if (exec) cudaGraphExecDestroy(exec); }
+};
+
 struct nudft2_hss_s {
   nudft2_opts opt{};
   int M = 0, nx = 0, ny = 0, L = 0, N = 0;
-  cudaStream_t st = 0;
+  cudaStream_t st = 0;             // handle-owned stream (capturable); callers' streams are joined by events
+  cudaEvent_t join = nullptr;
+  std::map<int, std::unique_ptr<SolveGraph<double>>> g64;
+  std::map<int, std::unique_ptr<SolveGraph<float>>> g32;
   Arena keep{(size_t)64 << 20};
   Arena scr{(size_t)256 << 20};
   Plan pl;
@@ -131,16 +146,66 @@ static void dft2(nudft2_hss_s* h, const double2* y, int64_t ldy, int s, double2*
   h->scr.release(mk);
 }
 
+template <typename R> static std::map<int, std::unique_ptr<SolveGraph<R>>>& graphs(nudft2_hss_s* h);
+template <> std::map<int, std::unique_ptr<SolveGraph<double>>>& graphs<double>(nudft2_hss_s* h) { return h->g64; }
+template <> std::map<int, std::unique_ptr<SolveGraph<float>>>& graphs<float>(nudft2_hss_s* h) { return h->g32; }
+
+// G~_hss^+ f through the URV sweeps, f in caller point order, result in lexicographic column
+// order.  The sweeps of each right-hand-side count are captured once into a CUDA graph (after
+// one ordinary run that sizes the scratch arena) and replayed afterwards.
 template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, const double2* f, int64_t ldf, int s,
                                                 double2* ylex) {
   const int M = h->M, N = h->N;
-  auto mk = h->scr.mark();
-  cplx<R>* f2 = h->scr.arr<cplx<R>>((size_t)M * s);
-  cplx<R>* yt = h->scr.arr<cplx<R>>((size_t)N * s);
-  convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, f2, M, 1.0);
-  H.solve(f2, M, s, yt, N);
-  convert_scatter<R, double>(h->st, yt, N, h->pl.colmap, N, s, ylex, N, 1.0);
-  h->scr.release(mk);
+  auto& gm = graphs<R>(h);
+  auto it = gm.find(s);
+  SolveGraph<R>* G = nullptr;
+  if (it == gm.end()) {
+    auto g = std::make_unique<SolveGraph<R>>();
+    g->f2 = h->keep.arr<cplx<R>>((size_t)M * s);
+    g->yt = h->keep.arr<cplx<R>>((size_t)N * s);
+    G = g.get();
+    gm[s] = std::move(g);
+    convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, G->f2, M, 1.0);
+    H.solve(G->f2, M, s, G->yt, N);            // ordinary run: result used, arenas sized
+    convert_scatter<R, double>(h->st, G->yt, N, h->pl.colmap, N, s, ylex, N, 1.0);
+    // capture the sweeps for the next calls
+    const bool prof = H.ops().prof.on;
+    H.ops().prof.on = false;
+    H.ops().set_capture(&G->pool);
+    H.freeze_scratch(true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        H.solve(G->f2, M, s, G->yt, N);
+      } catch (Error&) {
+        G->failed = true;
+      }
+      e = cudaStreamEndCapture(h->st, &graph);
+      if (e == cudaSuccess && !G->failed) e = cudaGraphInstantiate(&G->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) { G->failed = true; cudaGetLastError(); }
+    H.freeze_scratch(false);
+    H.ops().set_capture(nullptr);
+    H.ops().prof.on = prof;
+    return;
+  }
+  G = it->second.get();
+  convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, G->f2, M, 1.0);
+  if (G->exec && !G->failed) {
+    NH_CK(cudaGraphLaunch(G->exec, h->st));
+    H.ops().count();
+  } else {
+    H.solve(G->f2, M, s, G->yt, N);
+  }
+  convert_scatter<R, double>(h->st, G->yt, N, h->pl.colmap, N, s, ylex, N, 1.0);
+}
+
+// Make the handle's stream wait for the work the caller queued on its own stream.
+static void enter(nudft2_hss_s* h, void* user_stream) {
+  NH_CK(cudaEventRecord(h->join, (cudaStream_t)user_stream));
+  NH_CK(cudaStreamWaitEvent(h->st, h->join, 0));
 }
 
 // ----------------------------------------------------------------------------- LA test hooks
@@ -201,6 +266,8 @@ nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, 
     NH_CK(cudaStreamSynchronize((cudaStream_t)stream));
   });
 }
+
+void nudft2_hss_free(nudft2_hss_t h);
 
 nudft2_status nudft2_exact_apply(const double* d_x, const double* d_y, int64_t M, int nx, int ny, int op,
                                  const void* d_in, int64_t ldi, int nrhs, void* d_out, int64_t ldo, void* stream) {
@@ -264,7 +331,9 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     h = new nudft2_hss_s();
     h->opt = opt;
     h->M = (int)M; h->nx = nx; h->ny = ny; h->L = L; h->N = nx * ny;
-    h->st = (cudaStream_t)stream;
+    NH_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    NH_CK(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+    enter(h, stream);
     h->keep.set_stream(h->st);
     h->scr.set_stream(h->st);
     h->ops.reset(new Ops<double>(h->st, &h->scr));
@@ -298,14 +367,18 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     h->t_build = now_ms() - t0;
     *out = h;
   });
-  if (st != NUDFT2_OK && h) delete h;
+  if (st != NUDFT2_OK && h) {
+    const std::string msg = g_err;
+    nudft2_hss_free(h);
+    g_err = msg;
+  }
   return st;
 }
 
 nudft2_status nudft2_hss_factor(nudft2_hss_t h, void* stream) {
   return guard([&] {
     NH_REQUIRE(h != nullptr, ST_ESTATE, "factor: no handle (build first)");
-    (void)stream;
+    enter(h, stream);
     const double t0 = now_ms();
     if (h->h64) h->h64->factor();
     else h->h32->factor();
@@ -364,7 +437,7 @@ nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int
     NH_REQUIRE(h != nullptr, ST_ESTATE, "solve: no handle");
     NH_REQUIRE(h->factored, ST_ESTATE, "solve before factor");
     NH_REQUIRE(nrhs >= 0 && d_f && d_c && ldf >= h->M && ldc >= h->N, ST_EINVAL, "solve: bad arguments");
-    (void)stream;
+    enter(h, stream);
     if (nrhs == 0) return;
     const double t0 = now_ms();
     do_solve(h, (const double2*)d_f, ldf, nrhs, (double2*)d_c, ldc);
@@ -378,7 +451,7 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
   return guard([&] {
     NH_REQUIRE(h != nullptr, ST_ESTATE, "apply: no handle");
     NH_REQUIRE(nrhs >= 0 && d_in && d_out, ST_EINVAL, "apply: bad arguments");
-    (void)stream;
+    enter(h, stream);
     if (nrhs == 0) return;
     const int M = h->M, N = h->N;
     switch (op) {
@@ -500,7 +573,12 @@ nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t ld
 void nudft2_hss_free(nudft2_hss_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
-  delete h;
+  cudaStream_t st = h->st;
+  cudaEvent_t ev = h->join;
+  delete h;                       // arenas release their chunks on st
+  cudaStreamSynchronize(st);
+  if (ev) cudaEventDestroy(ev);
+  if (st) cudaStreamDestroy(st);
 }
 
 }  // extern "C"

@@ -109,6 +109,8 @@ class Arena {
   explicit Arena(size_t chunk = (size_t)256 << 20) : chunk_(chunk) {}
   ~Arena() { free_all(); }
   void set_stream(cudaStream_t s) { st_ = s; }
+  // While frozen (during CUDA-graph capture) the arena may only reuse chunks it already owns.
+  void freeze(bool f) { frozen_ = f; }
   void* alloc(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
@@ -125,6 +127,7 @@ class Arena {
         cur_++;
       }
     }
+    if (frozen_) throw Error(ST_ENOMEM, "arena is frozen during graph capture and has no room left");
     size_t sz = bytes > chunk_ ? bytes : chunk_;
     void* p = nullptr;
     NH_CK(cudaMallocAsync(&p, sz, st_));
@@ -175,6 +178,22 @@ class Arena {
   std::vector<Chunk> chunks_;
   size_t cur_ = 0, chunk_, total_ = 0;
   cudaStream_t st_ = 0;
+  bool frozen_ = false;
+};
+
+// Pinned host memory that stays valid as long as the object lives: descriptors uploaded while a
+// CUDA graph is captured are copied from here at every replay.
+class PinnedPool {
+ public:
+  ~PinnedPool() { for (void* p : blocks_) cudaFreeHost(p); }
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    NH_CK(cudaMallocHost(&p, bytes > 0 ? bytes : 1));
+    blocks_.push_back(p);
+    return p;
+  }
+ private:
+  std::vector<void*> blocks_;
 };
 
 }  // namespace nh

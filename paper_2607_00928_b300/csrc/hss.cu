@@ -1017,8 +1017,7 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
       cp.push_back({Cl[L][p].p, ytree + pl_->c0[L][p], pl_->nc[L][p], s, Cl[L][p].ld, ldy, OP_N, R(1), R(0)});
     ops_.copy(cp);
   }
-  NH_CK(cudaStreamSynchronize(st_));
-  scr_.release(mk);
+  scr_.release(mk);   // no synchronisation here: the solve is captured into a CUDA graph
 }
 
 // ------------------------------------------------------------------------------- HSS matvec

@@ -77,6 +77,8 @@ template <typename R> class Hss {
   std::vector<int> level_ranks() const;
   size_t bytes() const { return keep_.reserved(); }
   Ops<R>& ops() { return ops_; }
+  // While a solve is captured into a CUDA graph the scratch arena must not grow.
+  void freeze_scratch(bool f) { scr_.freeze(f); }
   bool factored = false;
 
  private:

@@ -32,16 +32,24 @@ __device__ __forceinline__ int find_prob(const int* pre, int n, int t) {
   return lo;
 }
 
-template <typename R> template <typename D> D* Ops<R>::upload(const std::vector<D>& v) {
-  D* d = (D*)ar_->alloc(v.size() * sizeof(D));
-  NH_CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(D), cudaMemcpyHostToDevice, st_));
+template <typename R> void* Ops<R>::stage(const void* src, size_t bytes) {
+  void* d = ar_->alloc(bytes);
+  const void* from = src;
+  if (pool_) {                      // graph capture: copy from memory that outlives the graph
+    void* h = pool_->alloc(bytes);
+    std::memcpy(h, src, bytes);
+    from = h;
+  }
+  NH_CK(cudaMemcpyAsync(d, from, bytes, cudaMemcpyHostToDevice, st_));
   return d;
 }
 
-static int* upload_ints(Arena* ar, cudaStream_t st, const std::vector<int>& v) {
-  int* d = (int*)ar->alloc(v.size() * sizeof(int));
-  NH_CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  return d;
+template <typename R> template <typename D> D* Ops<R>::upload(const std::vector<D>& v) {
+  return (D*)stage(v.data(), v.size() * sizeof(D));
+}
+
+template <typename R> int* Ops<R>::upload_ints(const std::vector<int>& v) {
+  return (int*)stage(v.data(), v.size() * sizeof(int));
 }
 
 // =============================================================================== profiling
@@ -267,7 +275,7 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
       t += ((g.m + 127) / 128) * ((g.n + 127) / 128);
     }
     GemmD<R>* dd = upload(d);
-    int* dp = upload_ints(ar_, st_, preb);
+    int* dp = upload_ints(preb);
     double fl = 0;
     if (prof.on)
       for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
@@ -302,8 +310,8 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
     if (ks[i] > 1) wsp[i] = (cplx<R>*)ar_->alloc((size_t)ks[i] * g.m * g.n * sizeof(cplx<R>));
   }
   GemmD<R>* dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre2);
-  int* dks = any_split ? upload_ints(ar_, st_, ks) : nullptr;
+  int* dp = upload_ints(pre2);
+  int* dks = any_split ? upload_ints(ks) : nullptr;
   cplx<R>* const* dws = any_split ? upload(wsp) : nullptr;
   double fl = 0, by = 0;
   if (prof.on)
@@ -326,9 +334,9 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
     for (size_t i = 0; i < d.size(); ++i)
       if (ks[i] > 1) { ds2.push_back(d[i]); ks2.push_back(ks[i]); ws2.push_back(wsp[i]); ep2.push_back(n2); n2 += d[i].m * d[i].n; }
     auto dd2 = upload(ds2);
-    int* dk2 = upload_ints(ar_, st_, ks2);
+    int* dk2 = upload_ints(ks2);
     cplx<R>* const* dw2 = upload(ws2);
-    int* de2 = upload_ints(ar_, st_, ep2);
+    int* de2 = upload_ints(ep2);
     k_gemm_reduce<R><<<(n2 + 255) / 256, 256, 0, st_>>>(dd2, dk2, dw2, de2, (int)ds2.size());
     NH_LAUNCH_CK();
     count();
@@ -388,7 +396,7 @@ template <typename R> void Ops<R>::copy(const std::vector<CopyD<R>>& d0) {
   }
   if (d.empty()) return;
   auto dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(pre);
   k_copy<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
   count();
@@ -427,7 +435,7 @@ template <typename R> void Ops<R>::kron(const std::vector<KronD<R>>& d0) {
   }
   if (d.empty()) return;
   auto dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(pre);
   k_kron<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
   count();
@@ -463,7 +471,7 @@ template <typename R> void Ops<R>::face(const std::vector<FaceD<R>>& d0) {
   }
   if (d.empty()) return;
   auto dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(pre);
   k_face<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
   count();
@@ -498,7 +506,7 @@ template <typename R> void Ops<R>::gather(const std::vector<GatherD<R>>& d0) {
   }
   if (d.empty()) return;
   auto dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(pre);
   k_gather<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
   count();
@@ -529,7 +537,7 @@ template <typename R> void Ops<R>::set_identity(const std::vector<Mat<R>>& d0) {
   }
   if (d.empty()) return;
   auto dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(pre);
   k_set_identity<R><<<tiles, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
   count();
@@ -1068,7 +1076,7 @@ void Ops<R>::trinv(const std::vector<Mat<R>>& A, const std::vector<Mat<R>>& X) {
   if (d.empty()) return;
   auto mk = ar_->mark();
   auto dd = upload(d);
-  int* dp = upload_ints(ar_, st_, pre);
+  int* dp = upload_ints(pre);
   k_trinv_diag<R><<<blocks, 256, 0, st_>>>(dd, dp, (int)d.size());
   NH_LAUNCH_CK();
   count();
@@ -1749,7 +1757,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   }
   if (!sel.empty()) {
     auto dsel = upload(sel);
-    int* dp = upload_ints(ar_, st_, pre);
+    int* dp = upload_ints(pre);
     k_svd_select<R><<<tot, 256, 0, st_>>>(dsel, dp, (int)sel.size());
     NH_LAUNCH_CK();
     count();

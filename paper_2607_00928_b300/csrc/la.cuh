@@ -125,11 +125,16 @@ template <typename R> class Ops {
 
   int launches() const { return launches_; }
   void count(int n = 1) { launches_ += n; }
+  // Capture mode: host->device descriptor copies are staged in `pool` (kept alive with the graph).
+  void set_capture(PinnedPool* pool) { pool_ = pool; }
+  int* upload_ints(const std::vector<int>& v);
 
  private:
   template <typename D> D* upload(const std::vector<D>& v);
+  void* stage(const void* src, size_t bytes);
   cudaStream_t st_;
   Arena* ar_;
+  PinnedPool* pool_ = nullptr;
   int launches_ = 0;
 };
 

@@ -174,3 +174,25 @@ def test_standalone_exact_apply_matches_oracle(nh):
     g = complex_normal((x.size, 2), 446)
     a = to_np(nh.exact_apply(x, y, nx, ny, nh.EXACT_ADJ, torch.from_numpy(g)))
     assert relerr_cols(a, orc.adjoint(x, y, g, nx, ny)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_repeated_solves_replay_the_captured_graph(nh, prec):
+    """The first solve of a right-hand-side count runs the sweeps and captures them into a CUDA
+    graph; later solves replay the graph.  Results must agree with the first solve and with the
+    dense oracle, for a second right-hand-side count too."""
+    w = WORKLOADS["fp64_n32"]
+    x, y, ct = make_workload(w)
+    f = orc.forward(x, y, ct, w.nx, w.ny)
+    eps = 1e-10 if prec == "fp64" else 1e-6
+    h = nh.NudftHSS(x, y, w.nx, w.ny, eps=eps, levels=w.levels, prec=prec, refine_tol=1e-10, refine_max=10).factor()
+    ft = torch.from_numpy(f)
+    c1 = to_np(h.solve(ft))
+    c2 = to_np(h.solve(ft))
+    c3 = to_np(h.solve(ft[:, :1]))
+    c4 = to_np(h.solve(ft[:, :1]))
+    assert relerr_cols(c1, ct) < 1e-8
+    assert relerr_cols(c2, c1) < 1e-13
+    assert relerr_cols(c4, c3) < 1e-13
+    assert relerr_cols(c3, ct[:, :1]) < 1e-8
+    h.close()
