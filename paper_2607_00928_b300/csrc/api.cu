@@ -22,6 +22,7 @@ template <typename R> struct SolveGraph {
   cplx<R>* f2 = nullptr;
   cplx<R>* yt = nullptr;
   cudaGraphExec_t exec = nullptr;
+  size_t kernels = 0;              // kernel nodes in the graph (for launch accounting)
   bool failed = false;
   PinnedPool pool;
   ~SolveGraph() { if (exec) cudaGraphExecDestroy(exec); }
@@ -182,7 +183,18 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
         G->failed = true;
       }
       e = cudaStreamEndCapture(h->st, &graph);
-      if (e == cudaSuccess && !G->failed) e = cudaGraphInstantiate(&G->exec, graph, 0);
+      if (e == cudaSuccess && !G->failed) {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+          std::vector<cudaGraphNode_t> nodes(nn);
+          cudaGraphGetNodes(graph, nodes.data(), &nn);
+          for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) G->kernels++;
+          }
+        }
+        e = cudaGraphInstantiate(&G->exec, graph, 0);
+      }
       if (graph) cudaGraphDestroy(graph);
     }
     if (e != cudaSuccess) { G->failed = true; cudaGetLastError(); }
@@ -195,7 +207,7 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
   convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, G->f2, M, 1.0);
   if (G->exec && !G->failed) {
     NH_CK(cudaGraphLaunch(G->exec, h->st));
-    H.ops().count();
+    H.ops().count((int)G->kernels);
   } else {
     H.solve(G->f2, M, s, G->yt, N);
   }

@@ -54,7 +54,7 @@ template <typename R> int* Ops<R>::upload_ints(const std::vector<int>& v) {
 
 // =============================================================================== profiling
 const char* kclass_name(int c) {
-  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other"};
+  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other", "qrcp"};
   return (c >= 0 && c < K_NCLASS) ? n[c] : "?";
 }
 Prof::~Prof() {
@@ -1520,6 +1520,13 @@ template <typename R> __global__ void __launch_bounds__(256) k_qp_update(const Q
   }
 }
 
+// |R_kk| of the pivoted QR (one thread per diagonal entry).
+template <typename R> __global__ void k_rdiag(const QpD<R>* __restrict__ ds, R* const* __restrict__ out) {
+  const QpD<R> d = ds[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < min(d.m, d.n)) out[blockIdx.y][k] = sqrt(abs2(d.A[(size_t)k + (size_t)k * d.lda]));
+}
+
 template <typename R>
 void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std::vector<Mat<R>>& P,
                      std::vector<std::vector<double>>& S) {
@@ -1569,13 +1576,54 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
       }
       count(2);
     }
-    prof.end(st_, K_QR_PANEL, fl, 0);
+    prof.end(st_, K_QRCP, fl, 0);
+  }
+  // 1b. pre-truncation: the pivoted QR reveals the rank, so rows of R with |R_kk| two decades
+  //     below the truncation threshold (and the trailing block under them) are dropped before
+  //     the Jacobi sweeps; they cannot reach the retained singular values.
+  std::vector<int> peff(nm, 0);
+  {
+    std::vector<R*> dgp;
+    std::vector<int> pq;
+    int pm = 0;
+    for (size_t i = 0, q = 0; i < nm; ++i) {
+      const int w = Ct[i].m, r = Ct[i].n;
+      peff[i] = std::min(w, r);
+      if (w <= 0 || r <= 0) continue;
+      dgp.push_back(ar_->template arr<R>(peff[i]));
+      pq.push_back((int)i);
+      pm = std::max(pm, peff[i]);
+      (void)q;
+    }
+    if (!dgp.empty()) {
+      auto dq = upload(qp);
+      auto dd = upload(dgp);
+      dim3 g((pm + 255) / 256, (unsigned)qp.size());
+      k_rdiag<R><<<g, 256, 0, st_>>>(dq, dd);
+      NH_LAUNCH_CK();
+      count();
+      std::vector<std::vector<R>> hd(dgp.size());
+      for (size_t q = 0; q < dgp.size(); ++q) {
+        hd[q].resize(peff[pq[q]]);
+        NH_CK(cudaMemcpyAsync(hd[q].data(), dgp[q], hd[q].size() * sizeof(R), cudaMemcpyDeviceToHost, st_));
+      }
+      NH_CK(cudaStreamSynchronize(st_));
+      for (size_t q = 0; q < dgp.size(); ++q) {
+        R mx = 0;
+        for (R v : hd[q]) mx = std::max(mx, v);
+        const double cut = 0.01 * eps * (double)mx;
+        int k = 0;   // keep through the last row above the cut (|R_kk| is only roughly monotone)
+        for (int j = 0; j < (int)hd[q].size(); ++j)
+          if ((double)hd[q][j] > cut) k = j + 1;
+        peff[pq[q]] = std::max(k, std::min(2, (int)hd[q].size()));
+      }
+    }
   }
   // 2. X = R^* (r x p) (the pivoted QR zeroes the part below the diagonal)
   std::vector<Mat<R>> X(nm);
   std::vector<CopyD<R>> cp;
   for (size_t i = 0; i < nm; ++i) {
-    const int w = Ct[i].m, r = Ct[i].n, p = std::min(w, r);
+    const int w = Ct[i].m, r = Ct[i].n, p = std::min(peff[i], std::min(w, r));
     X[i] = ar_->template mat<R>(r, p);
     if (r > 0 && p > 0) cp.push_back({Ct[i].p, X[i].p, r, p, Ct[i].ld, X[i].ld, OP_C, R(1), R(0)});
   }

@@ -70,7 +70,7 @@ template <typename R> struct QFac {
 
 // Per-kernel-class accounting (CUDA events around each launch on the launching stream),
 // enabled per handle for measurement runs.  flops are the algorithmic counts of the launch.
-enum KClass { K_GEMM = 0, K_QR_PANEL = 1, K_JACOBI = 2, K_OTHER = 3, K_NCLASS = 4 };
+enum KClass { K_GEMM = 0, K_QR_PANEL = 1, K_JACOBI = 2, K_OTHER = 3, K_QRCP = 4, K_NCLASS = 5 };
 struct KStat { double ms = 0, flops = 0, bytes = 0; int launches = 0; };
 const char* kclass_name(int c);
 
