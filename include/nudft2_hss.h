@@ -158,6 +158,21 @@ nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t
 nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
                            int grouped, void* stream);
 
+/* Allocation-free variant of the exact forward apply (NUDFT2_EXACT_FWD of nudft2_exact_apply):
+ * d_f (M x nrhs, ld ldf >= M) = A d_c (N x nrhs, ld ldc == N, complex128), in FP64.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory while they run -- e.g. code being captured into a CUDA graph (allocation is not
+ * capturable), serving loops that reserve all memory up front, or hosts whose own allocator
+ * owns the device.  It never calls cudaMalloc/cudaFree or any allocating routine; its workspace
+ * is one fixed 64 MiB device array inside the library (held by every GPU that loads it, until
+ * exit).  Limit: M*(2*nx + ny)*16 bytes must fit in 64 MiB minus 4 KiB; right-hand sides are
+ * processed in chunks that fit.  The first call on a device looks up the array's address with
+ * cudaGetSymbolAddress, so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the caller.
+ * Errors: EINVAL (bad sizes, ldc != nx*ny, workspace too small), ECUDA. */
+nudft2_status nudft2_exact_fwd_noalloc(const double* d_x, const double* d_y, int64_t M, int nx, int ny,
+                                       const void* d_c, int64_t ldc, int nrhs, void* d_f, int64_t ldf, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* nudft2_last_error(void);
 

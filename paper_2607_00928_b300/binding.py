@@ -73,9 +73,11 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, ci, vp]
     L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
+    L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_exact_apply"):
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_exact_apply",
+              "nudft2_exact_fwd_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L

@@ -14,7 +14,8 @@
 
 using namespace nh;
 
-static thread_local std::string g_err;
+thread_local std::string nudft2_err_tls;
+#define g_err nudft2_err_tls
 
 // One captured URV solve (Sec. 2.3 sweeps) for a fixed number of right-hand sides: fixed
 // input/output buffers, the instantiated graph and the pinned descriptor copies it reads.

@@ -1815,6 +1815,18 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   ar_->release(mk);
 }
 
+void gemm_launch_raw(const GemmD<double>* desc, const int* pre, int np, int tiles, cudaStream_t st) {
+  if (tiles <= 0) return;
+  k_gemm<double, GemmCfg<double>::TM, GemmCfg<double>::TN, GemmCfg<double>::BK><<<tiles, 256, 0, st>>>(
+      desc, pre, np, nullptr, nullptr);
+  NH_LAUNCH_CK();
+}
+
+int gemm_tiles(const GemmD<double>& g) {
+  constexpr int BM = 16 * GemmCfg<double>::TM, BN = 16 * GemmCfg<double>::TN;
+  return ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
+}
+
 template class Ops<double>;
 template class Ops<float>;
 

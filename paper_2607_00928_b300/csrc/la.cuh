@@ -91,6 +91,11 @@ class Prof {
   cudaEvent_t cur_ = nullptr;
 };
 
+// Launch the batched GEMM kernel on caller-provided device descriptors (no allocation, no
+// copies): desc[np] and the exclusive tile prefix pre[np] already live in device memory.
+void gemm_launch_raw(const GemmD<double>* desc, const int* pre, int np, int tiles, cudaStream_t st);
+int gemm_tiles(const GemmD<double>& g);
+
 template <typename R> class Ops {
  public:
   explicit Ops(cudaStream_t s, Arena* scratch) : st_(s), ar_(scratch) {}
