@@ -158,6 +158,18 @@ nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t
 nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
                            int grouped, void* stream);
 
+/* nudft2_la_gemm: the batched complex GEMM behind every generator product of the construction,
+ * factorization and solve:  C_b = alpha op_a(A_b) op_b(B_b) + beta C_b  for b < batch, with
+ * X_b = X + b * stride_x (elements).  op: 0 = none, 1 = transpose, 2 = conjugate transpose.
+ * All matrices column-major on the device (complex128 for NUDFT2_FP64, complex64 otherwise);
+ * op_a(A) is m x k, op_b(B) is k x n (k = 0 allowed: C = beta C; A and B may then be NULL).
+ * C must not overlap A or B.  Synchronises the stream.
+ * Errors: EINVAL (bad op, size or leading dimension), ECUDA. */
+nudft2_status nudft2_la_gemm(int prec, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
+                             const void* d_a, int64_t lda, int64_t stride_a, const void* d_b, int64_t ldb,
+                             int64_t stride_b, double beta, void* d_c, int64_t ldc, int64_t stride_c, int batch,
+                             void* stream);
+
 /* Allocation-free variant of the exact forward apply (NUDFT2_EXACT_FWD of nudft2_exact_apply):
  * d_f (M x nrhs, ld ldf >= M) = A d_c (N x nrhs, ld ldc == N, complex128), in FP64.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate device

@@ -5,5 +5,5 @@ constants of include/nudft2_hss.h.  All arithmetic runs in the CUDA library libn
 """
 from .binding import (  # noqa: F401
     EXACT_ADJ, EXACT_FWD, FAST_ADJ, FAST_FWD, FP64, MIXED, PINV, PINV_ADJ, LIB_PATH, NudftError, NudftHSS, lib,
-    exact_apply, la_qr, la_tsvd, psi_eval,
+    exact_apply, la_gemm, la_qr, la_tsvd, psi_eval,
 )

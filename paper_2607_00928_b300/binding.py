@@ -72,11 +72,13 @@ def lib() -> ctypes.CDLL:
     L.nudft2_la_tsvd.argtypes = [ci, vp, i64, i64, i64, ctypes.c_double, vp, i64, ctypes.POINTER(ci),
                                  ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, ci, vp]
+    L.nudft2_la_gemm.argtypes = [ci, ci, ci, i64, i64, i64, ctypes.c_double, vp, i64, i64, vp, i64, i64,
+                                 ctypes.c_double, vp, i64, i64, ci, vp]
     L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_exact_apply",
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
@@ -151,6 +153,35 @@ def la_qr(A: torch.Tensor, grouped: bool = False):
     _check(lib().nudft2_la_qr(prec, ctypes.c_void_p(a.data_ptr()), m, n, m, ctypes.c_void_p(q.data_ptr()), m,
                               int(grouped), _stream()))
     return q.t(), torch.triu(a.t())
+
+
+_OPS = {"N": 0, "T": 1, "C": 2}
+
+
+def la_gemm(A: torch.Tensor, B: torch.Tensor, opa: str = "N", opb: str = "N", alpha: float = 1.0,
+            beta: float = 0.0, C: torch.Tensor = None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C by the library's batched GEMM; A, B, C are (batch, rows, cols)
+    or (rows, cols) complex CUDA tensors (returned C is a new tensor unless C is given)."""
+    squeeze = A.dim() == 2
+    A3, B3 = (A[None], B[None]) if squeeze else (A, B)
+    dt = A3.dtype
+    prec = FP64 if dt == torch.complex128 else MIXED
+    nb = A3.shape[0]
+    m = A3.shape[1] if opa == "N" else A3.shape[2]
+    k = A3.shape[2] if opa == "N" else A3.shape[1]
+    n = B3.shape[2] if opb == "N" else B3.shape[1]
+    a = A3.transpose(1, 2).contiguous()             # column major per batch item
+    b = B3.transpose(1, 2).contiguous()
+    if C is None:
+        c = torch.zeros((nb, n, m), dtype=dt, device=A.device)
+    else:
+        c = (C[None] if squeeze else C).transpose(1, 2).contiguous()
+    _check(lib().nudft2_la_gemm(prec, _OPS[opa], _OPS[opb], m, n, k, float(alpha),
+                                ctypes.c_void_p(a.data_ptr()), max(a.shape[2], 1), a.shape[1] * a.shape[2],
+                                ctypes.c_void_p(b.data_ptr()), max(b.shape[2], 1), b.shape[1] * b.shape[2], float(beta),
+                                ctypes.c_void_p(c.data_ptr()), m, m * n, nb, _stream()))
+    out = c.transpose(1, 2)
+    return out[0] if squeeze else out
 
 
 class NudftHSS:

@@ -264,6 +264,21 @@ static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, int grou
   NH_CK(cudaStreamSynchronize(st));
 }
 
+template <typename R>
+static void la_gemm(int opa, int opb, int m, int n, int k, double alpha, const void* A, int lda, int64_t sa,
+                    const void* B, int ldb, int64_t sb, double beta, void* C, int ldc, int64_t sc, int batch,
+                    cudaStream_t st) {
+  Arena scr;
+  scr.set_stream(st);
+  Ops<R> ops(st, &scr);
+  std::vector<GemmD<R>> d((size_t)batch);
+  for (int b = 0; b < batch; ++b)
+    d[b] = {(const cplx<R>*)A + (size_t)b * sa, (const cplx<R>*)B + (size_t)b * sb, (cplx<R>*)C + (size_t)b * sc,
+            m, n, k, lda, ldb, ldc, opa, opb, (R)alpha, (R)beta};
+  ops.gemm(d);
+  NH_CK(cudaStreamSynchronize(st));   // the descriptor staging above lives on this host frame
+}
+
 // ----------------------------------------------------------------------------- C-ABI
 extern "C" {
 
@@ -580,6 +595,26 @@ nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t ld
       la_qr<double>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, grouped, (cudaStream_t)stream);
     else
       la_qr<float>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, grouped, (cudaStream_t)stream);
+  });
+}
+
+nudft2_status nudft2_la_gemm(int prec, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
+                             const void* d_a, int64_t lda, int64_t stride_a, const void* d_b, int64_t ldb,
+                             int64_t stride_b, double beta, void* d_c, int64_t ldc, int64_t stride_c, int batch,
+                             void* stream) {
+  return guard([&] {
+    const bool ok_op = opa >= 0 && opa <= 2 && opb >= 0 && opb <= 2;
+    const int64_t ra = opa == 0 ? m : k, rb = opb == 0 ? k : n;
+    NH_REQUIRE(ok_op && (k == 0 || (d_a && d_b)) && d_c && m >= 1 && n >= 1 && k >= 0 && batch >= 1 && lda >= std::max<int64_t>(ra, 1) &&
+                   ldb >= std::max<int64_t>(rb, 1) && ldc >= m && stride_a >= 0 && stride_b >= 0 && stride_c >= 0 &&
+                   m < (1LL << 31) && n < (1LL << 31) && k < (1LL << 31) && (int64_t)m * n < (1LL << 31),
+               ST_EINVAL, "la_gemm: bad arguments");
+    if (prec == NUDFT2_FP64)
+      la_gemm<double>(opa, opb, (int)m, (int)n, (int)k, alpha, d_a, (int)lda, stride_a, d_b, (int)ldb, stride_b,
+                      beta, d_c, (int)ldc, stride_c, batch, (cudaStream_t)stream);
+    else
+      la_gemm<float>(opa, opb, (int)m, (int)n, (int)k, alpha, d_a, (int)lda, stride_a, d_b, (int)ldb, stride_b,
+                     beta, d_c, (int)ldc, stride_c, batch, (cudaStream_t)stream);
   });
 }
 

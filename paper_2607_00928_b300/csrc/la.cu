@@ -100,7 +100,9 @@ void Prof::collect() {
 // all problems are numbered consecutively (exclusive prefix `pre`).
 // Split-k: problem pi has ks[pi] k-chunks; chunk s writes its unscaled partial tile to
 // ws[pi] + s*m*n and k_gemm_reduce sums the chunks in order (deterministic).
-template <typename R, int TM, int TN, int BK>
+// TA / TB: op(A) / op(B) reads the stored matrix transposed (op T or C); every problem of one
+// launch has the same layout class, so the staging index arithmetic is resolved at compile time.
+template <typename R, int TM, int TN, int BK, bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, const int* __restrict__ pre,
                                               int np, const int* __restrict__ ks, cplx<R>* const* __restrict__ ws) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
@@ -120,8 +122,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
     const int kc = (((g.k + nsplit - 1) / nsplit) + BK - 1) / BK * BK;
     kbeg = split * kc;
     const int kend = min(g.k, kbeg + kc);
-    g.A = (g.opA == OP_N) ? g.A + (size_t)kbeg * g.lda : g.A + kbeg;
-    g.B = (g.opB == OP_N) ? g.B + kbeg : g.B + (size_t)kbeg * g.ldb;
+    g.A = !TA ? g.A + (size_t)kbeg * g.lda : g.A + kbeg;
+    g.B = !TB ? g.B + kbeg : g.B + (size_t)kbeg * g.ldb;
     g.k = max(0, kend - kbeg);
   }
   const int row0 = (lt % tiles_m) * BM, col0 = (lt / tiles_m) * BN;
@@ -132,29 +134,30 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
 #pragma unroll
     for (int b = 0; b < TN; ++b) acc[a][b] = czero<R>();
   cplx<R> ra[LA], rb[LB];
-  // stage k tile starting at k0 into registers (op applied, zero padded)
+  // Stage the k tile starting at k0 into registers, zero padded.  The values are not touched
+  // here (no conjugation, no select), so the loads stay in flight across the FMA loop that
+  // follows; the op is applied when they are stored to shared memory.
+  const R sa = g.opA == OP_C ? R(-1) : R(1), sb = g.opB == OP_C ? R(-1) : R(1);
   auto load = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < LA; ++q) {
       const int e = tid + q * 256;
       int ii, kk;
-      if (g.opA == OP_N) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
+      if (!TA) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
       const int gi = row0 + ii, gk = k0 + kk;
-      cplx<R> v = czero<R>();
-      if (gi < g.m && gk < g.k)
-        v = (g.opA == OP_N) ? g.A[(size_t)gi + (size_t)gk * g.lda] : ld_op<R>(g.A + (size_t)gk + (size_t)gi * g.lda, g.opA);
-      ra[q] = v;
+      const size_t off = !TA ? (size_t)gi + (size_t)gk * g.lda : (size_t)gk + (size_t)gi * g.lda;
+      ra[q] = czero<R>();
+      if (gi < g.m && gk < g.k) ra[q] = g.A[off];
     }
 #pragma unroll
     for (int q = 0; q < LB; ++q) {
       const int e = tid + q * 256;
       int jj, kk;
-      if (g.opB == OP_N) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
+      if (!TB) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
       const int gj = col0 + jj, gk = k0 + kk;
-      cplx<R> v = czero<R>();
-      if (gj < g.n && gk < g.k)
-        v = (g.opB == OP_N) ? g.B[(size_t)gk + (size_t)gj * g.ldb] : ld_op<R>(g.B + (size_t)gj + (size_t)gk * g.ldb, g.opB);
-      rb[q] = v;
+      const size_t off = !TB ? (size_t)gk + (size_t)gj * g.ldb : (size_t)gj + (size_t)gk * g.ldb;
+      rb[q] = czero<R>();
+      if (gj < g.n && gk < g.k) rb[q] = g.B[off];
     }
   };
   auto store = [&]() {
@@ -162,15 +165,15 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
     for (int q = 0; q < LA; ++q) {
       const int e = tid + q * 256;
       int ii, kk;
-      if (g.opA == OP_N) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
-      As[kk][ii] = ra[q];
+      if (!TA) { ii = e % BM; kk = e / BM; } else { kk = e % BK; ii = e / BK; }
+      As[kk][ii] = mkc(ra[q].x, sa * ra[q].y);
     }
 #pragma unroll
     for (int q = 0; q < LB; ++q) {
       const int e = tid + q * 256;
       int jj, kk;
-      if (g.opB == OP_N) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
-      Bs[kk][jj] = rb[q];
+      if (!TB) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
+      Bs[kk][jj] = mkc(rb[q].x, sb * rb[q].y);
     }
   };
   if (g.k > 0) load(0);
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
     store();
     __syncthreads();
     if (k0 + BK < g.k) load(k0 + BK);      // global loads of the next tile overlap the FMAs below
-#pragma unroll
+#pragma unroll(TM * TN >= 64 ? 2 : BK)
     for (int kk = 0; kk < BK; ++kk) {
       cplx<R> av[TM], bv[TN];
 #pragma unroll
@@ -247,16 +250,77 @@ template <typename R> struct GemmCfg;
 template <> struct GemmCfg<double> { static constexpr int TM = 2, TN = 2, BK = 16; };
 template <> struct GemmCfg<float> { static constexpr int TM = 4, TN = 4, BK = 16; };
 
+template <typename R, int TM, int TN, int BK>
+static void launch_gemm(int cls, int grid, cudaStream_t st, const GemmD<R>* dd, const int* dp, int np, const int* ks,
+                        cplx<R>* const* ws) {
+  switch (cls) {
+    case 0: k_gemm<R, TM, TN, BK, false, false><<<grid, 256, 0, st>>>(dd, dp, np, ks, ws); break;
+    case 1: k_gemm<R, TM, TN, BK, false, true><<<grid, 256, 0, st>>>(dd, dp, np, ks, ws); break;
+    case 2: k_gemm<R, TM, TN, BK, true, false><<<grid, 256, 0, st>>>(dd, dp, np, ks, ws); break;
+    default: k_gemm<R, TM, TN, BK, true, true><<<grid, 256, 0, st>>>(dd, dp, np, ks, ws); break;
+  }
+  NH_LAUNCH_CK();
+}
+
 template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
+  std::vector<GemmD<R>> part[4];
+  for (const auto& g : d0) {
+    if (g.m <= 0 || g.n <= 0) continue;
+    if (g.k <= 0 && g.beta == R(1)) continue;
+    part[(g.opA != OP_N ? 2 : 0) + (g.opB != OP_N ? 1 : 0)].push_back(g);
+  }
+  for (int c = 0; c < 4; ++c)
+    if (!part[c].empty()) gemm_class(part[c], c);
+}
+
+// Diagnostics (environment NH_GEMM_LOG): one line per batched launch with its shape summary and
+// device time; skipped while the stream is being captured.
+struct GemmLog {
+  bool on = false;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  const char* path = "tiles64";
+  int cls = 0, np = 0, mx = 0, nx = 0, kx = 0;
+  double fl = 0;
+  GemmLog(cudaStream_t s) : st(s) {
+    if (!std::getenv("NH_GEMM_LOG")) return;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    on = true;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  ~GemmLog() {
+    if (!on) return;
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    std::fprintf(stderr, "[gemm] cls=%d path=%s np=%d m=%d n=%d k=%d gflop=%.3f ms=%.4f tflops=%.2f\n", cls, path, np, mx,
+                 nx, kx, fl * 1e-9, ms, fl / std::max(ms, 1e-6f) * 1e-9);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, int cls) {
   constexpr int BM = 16 * GemmCfg<R>::TM, BN = 16 * GemmCfg<R>::TN;
+  GemmLog glog(st_);
+  if (glog.on) {
+    glog.cls = cls;
+    glog.np = (int)d0.size();
+    for (const auto& g : d0) {
+      glog.mx = std::max(glog.mx, g.m); glog.nx = std::max(glog.nx, g.n); glog.kx = std::max(glog.kx, g.k);
+      glog.fl += 8.0 * g.m * g.n * std::max(g.k, 0);
+    }
+  }
   std::vector<GemmD<R>> d;
   d.reserve(d0.size());
   std::vector<int> pre;
   int tiles = 0, tiles_big = 0;
   double work = 0, work_big_ok = 0;
   for (const auto& g : d0) {
-    if (g.m <= 0 || g.n <= 0) continue;
-    if (g.k <= 0 && g.beta == R(1)) continue;
     d.push_back(g);
     pre.push_back(tiles);
     tiles += ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
@@ -280,8 +344,8 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
     if (prof.on)
       for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
     prof.begin(st_);
-    k_gemm<R, 8, 8, 8><<<t, 256, 0, st_>>>(dd, dp, (int)d.size(), nullptr, nullptr);
-    NH_LAUNCH_CK();
+    launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
+    glog.path = "tiles128";
     prof.end(st_, K_GEMM, fl, 0);
     count();
     return;
@@ -320,8 +384,8 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
       by += (double)sizeof(cplx<R>) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != R(0) ? 2.0 : 1.0) * g.m * g.n);
     }
   prof.begin(st_);
-  k_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK><<<tiles2, 256, 0, st_>>>(dd, dp, (int)d.size(), dks, dws);
-  NH_LAUNCH_CK();
+  launch_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK>(cls, tiles2, st_, dd, dp, (int)d.size(), dks, dws);
+  if (any_split) glog.path = "splitk";
   if (any_split) {
     std::vector<int> epre;
     int ne = 0;
@@ -1218,13 +1282,12 @@ __global__ void __launch_bounds__(512) k_jacobi_round(const JacD<R>* __restrict_
 // column pair over all rows: every CTA writes its partials, one cluster barrier, then each
 // warp gathers the JCS partials over DSMEM in a fixed order, so all CTAs compute the same
 // rotation and apply it to their own rows.  Data leaves shared memory once per round.
-constexpr int JCS = 8;
-
 template <typename R>
 __global__ void __launch_bounds__(512) k_jacobi_cluster(const JacD<R>* __restrict__ ds, int round, R tol, int rpc,
                                                          R negl2) {
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
+  const int JCS = (int)cluster.num_blocks();     // 8 or 16 CTAs share the rows of a block pair
   const JacD<R> d = ds[blockIdx.y];
   const int pair = blockIdx.x / JCS;
   // every CTA of a cluster shares (blockIdx.y, pair), so these exits are cluster-uniform
@@ -1319,6 +1382,248 @@ __global__ void __launch_bounds__(512) k_jacobi_cluster(const JacD<R>* __restric
     const int c = e / rl, i = e - c * rl;
     d.X[(size_t)(r0 + i) + (size_t)cidx[c] * d.ld] = S[(size_t)c * rpc + i];
   }
+}
+
+// Blocked one-sided Jacobi step (hierarchical blocking): the up to 64 columns of a block pair
+// (two blocks of 32) are orthogonalized together.  Their Gram matrix G = X_P^* X_P is formed
+// in one pass over the rows; a cyclic two-sided Jacobi on G in shared memory accumulates the
+// unitary V with V^* G V diagonal; a second pass applies X_P <- X_P V.  The rotations on G are
+// exactly the one-sided rotations of the column pairs (same angle formula as jac_rotate), only
+// evaluated on the Gram entries instead of re-reading the columns, so the data are read twice
+// per block pair instead of once per column pair.  The convergence measure of a pair is taken
+// from the freshly formed G; a pair within tol_out is left untouched, the inner rotations go
+// down to tol < tol_out.  The gap keeps pairs whose cosines sit at the rounding level of the
+// Gram (a few u sqrt(r)) from being reprocessed sweep after sweep.
+template <typename R> struct JbCfg {
+  static constexpr int W = 64;                           // columns per block pair
+  static constexpr int T = sizeof(R) == 4 ? 64 : 32;     // rows per staged chunk
+  static constexpr int LDX = T + 1, LDG = W + 1;         // padded strides (bank spread)
+  static constexpr int KP = T / 16;                      // chunk rows per thread in the update
+  static constexpr int PF = W * T / 256;                 // chunk elements each thread stages
+  static constexpr size_t smem = (size_t)(2 * W * LDG + W * LDX) * sizeof(cplx<R>);
+};
+
+template <typename R>
+__device__ __forceinline__ void jb_load(const JacD<R>& d, const int* cidx, int r0, cplx<R> (&pf)[JbCfg<R>::PF]) {
+  constexpr int T = JbCfg<R>::T;
+#pragma unroll
+  for (int q = 0; q < JbCfg<R>::PF; ++q) {
+    const int e = threadIdx.x + 256 * q, c = e / T, k = e - c * T, row = r0 + k, col = cidx[c];
+    pf[q] = (col >= 0 && row < d.r) ? d.X[(size_t)row + (size_t)col * d.ld] : czero<R>();
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void jb_stage(cplx<R>* Xs, const cplx<R> (&pf)[JbCfg<R>::PF]) {
+  constexpr int T = JbCfg<R>::T, LDX = JbCfg<R>::LDX;
+#pragma unroll
+  for (int q = 0; q < JbCfg<R>::PF; ++q) {
+    const int e = threadIdx.x + 256 * q, c = e / T, k = e - c * T;
+    Xs[c * LDX + k] = pf[q];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    k_jacobi_blk(const JacD<R>* __restrict__ ds, int round, R tol, R tol_out, R negl2, int max_inner,
+                 unsigned long long* __restrict__ rows_updated) {
+  using C = JbCfg<R>;
+  constexpr int W = C::W, T = C::T, LDX = C::LDX, LDG = C::LDG, KP = C::KP;
+  const JacD<R> d = ds[blockIdx.y];
+  if (*d.done) return;
+  if (round >= d.nblk - 1 || (int)blockIdx.x >= d.nblk / 2) return;
+  extern __shared__ unsigned char smraw_b[];
+  cplx<R>* G = (cplx<R>*)smraw_b;      // G[i * LDG + j] = x_i^* x_j
+  cplx<R>* V = G + W * LDG;            // V[i * LDG + j]
+  cplx<R>* Xs = V + W * LDG;           // chunk, column-major: Xs[c * LDX + k]
+  __shared__ int cidx[W];
+  __shared__ R rc[W / 2];
+  __shared__ cplx<R> rse[W / 2];
+  __shared__ int ract[W / 2];
+  __shared__ int any_s;
+  __shared__ float offw[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int I, J;
+  rr_pair(blockIdx.x, round, d.nblk, I, J);
+  if (tid < W) {
+    const int c = (tid < 32 ? I : J) * 32 + (tid & 31);
+    cidx[tid] = c < d.k ? c : -1;
+  }
+  __syncthreads();
+  const R floor2 = negl2 * (*d.amax);
+  // ---- 1. Gram: thread (ti, tj) owns G[ti + 16p][tj + 16q], p, q < 4
+  const int ti = tid >> 4, tj = tid & 15;
+  {
+    cplx<R> acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = czero<R>();
+    cplx<R> pf[C::PF];
+    jb_load<R>(d, cidx, 0, pf);
+    for (int r0 = 0; r0 < d.r; r0 += T) {
+      jb_stage<R>(Xs, pf);
+      __syncthreads();
+      if (r0 + T < d.r) jb_load<R>(d, cidx, r0 + T, pf);
+#pragma unroll 4
+      for (int k = 0; k < T; ++k) {
+        cplx<R> a[4], b[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) a[p] = Xs[(ti + 16 * p) * LDX + k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = Xs[(tj + 16 * q) * LDX + k];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cfmac(acc[p][q], a[p], b[q]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) G[(ti + 16 * p) * LDG + tj + 16 * q] = acc[p][q];
+  }
+  __syncthreads();
+  // ---- 2. largest cosine of the fresh Gram (columns above the noise floor only)
+  {
+    float m = 0.f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = ti + 16 * p, j = tj + 16 * q;
+        const R di = G[i * LDG + i].x, dj = G[j * LDG + j].x;
+        if (i != j && di > floor2 && dj > floor2) {
+          const R g = sqrt(abs2(G[i * LDG + j]));
+          m = fmaxf(m, (float)(g / (sqrt(di) * sqrt(dj))));
+        }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) offw[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < 8; ++w) t = fmaxf(t, offw[w]);
+      offw[0] = t;
+      if (t > 0.f) atomicMax(d.off, __float_as_uint(t));
+    }
+    __syncthreads();
+    if ((R)offw[0] <= tol_out) return;   // uniform: the pair is already orthogonal
+  }
+  // ---- 3. cyclic two-sided Jacobi on G, V <- V J for every rotation J
+  for (int e = tid; e < W * W; e += 256) {
+    const int i = e / W, j = e - i * W;
+    V[i * LDG + j] = mkc(R(i == j ? 1 : 0), R(0));
+  }
+  if (tid == 0) any_s = 0;
+  __syncthreads();
+  for (int sw = 0; sw < max_inner; ++sw) {
+    for (int ir = 0; ir < W - 1; ++ir) {
+      if (tid < W / 2) {
+        int a, b;
+        rr_pair(tid, ir, W, a, b);
+        const R al = G[a * LDG + a].x, be = G[b * LDG + b].x;
+        const cplx<R> ga = G[a * LDG + b];
+        const R g = sqrt(abs2(ga));
+        int act = 0;
+        if (al > floor2 && be > floor2 && g > R(0) && g / (sqrt(al) * sqrt(be)) > tol) {
+          const R zeta = (be - al) / (R(2) * g);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          const R c = R(1) / sqrt(R(1) + t * t);
+          const R s = c * t;
+          rc[tid] = c;
+          rse[tid] = mkc(s * ga.x / g, s * ga.y / g);
+          act = 1;
+          any_s = 1;
+        }
+        ract[tid] = act;
+      }
+      __syncthreads();
+      // columns a, b of G and of V: (x_a, x_b) <- (c x_a - conj(se) x_b, se x_a + c x_b)
+      for (int e = tid; e < 2 * (W / 2) * W; e += 256) {
+        const int which = e / ((W / 2) * W), rest = e - which * ((W / 2) * W);
+        const int p = rest / W, i = rest - p * W;
+        if (!ract[p]) continue;
+        int a, b;
+        rr_pair(p, ir, W, a, b);
+        cplx<R>* M = which ? V : G;
+        const R c = rc[p];
+        const cplx<R> se = rse[p], sec = conj(se);
+        const cplx<R> x = M[i * LDG + a], y = M[i * LDG + b];
+        M[i * LDG + a] = c * x - sec * y;
+        M[i * LDG + b] = se * x + c * y;
+      }
+      __syncthreads();
+      // rows a, b of G (the conjugate transformation from the left)
+      for (int e = tid; e < (W / 2) * W; e += 256) {
+        const int p = e / W, j = e - p * W;
+        if (!ract[p]) continue;
+        int a, b;
+        rr_pair(p, ir, W, a, b);
+        const R c = rc[p];
+        const cplx<R> se = rse[p], sec = conj(se);
+        const cplx<R> x = G[a * LDG + j], y = G[b * LDG + j];
+        G[a * LDG + j] = c * x - se * y;
+        G[b * LDG + j] = sec * x + c * y;
+      }
+      __syncthreads();
+      if (tid < W / 2 && ract[tid]) {
+        int a, b;
+        rr_pair(tid, ir, W, a, b);
+        G[a * LDG + b] = czero<R>();
+        G[b * LDG + a] = czero<R>();
+        G[a * LDG + a].y = R(0);
+        G[b * LDG + b].y = R(0);
+      }
+      __syncthreads();
+    }
+    const int more = any_s;
+    __syncthreads();                   // every thread has read the flag before it is reset
+    if (!more) break;
+    if (tid == 0) any_s = 0;
+    __syncthreads();
+  }
+  // ---- 4. X_P <- X_P V, chunk by chunk (in place; each chunk's rows are read before written)
+  const int tk = ti;
+  cplx<R> pf[C::PF];
+  jb_load<R>(d, cidx, 0, pf);
+  for (int r0 = 0; r0 < d.r; r0 += T) {
+    jb_stage<R>(Xs, pf);
+    __syncthreads();
+    if (r0 + T < d.r) jb_load<R>(d, cidx, r0 + T, pf);
+    cplx<R> acc[KP][4];
+#pragma unroll
+    for (int p = 0; p < KP; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = czero<R>();
+#pragma unroll 4
+    for (int c = 0; c < W; ++c) {
+      cplx<R> a[KP], b[4];
+#pragma unroll
+      for (int p = 0; p < KP; ++p) a[p] = Xs[c * LDX + tk + 16 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = V[c * LDG + tj + 16 * q];
+#pragma unroll
+      for (int p = 0; p < KP; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(acc[p][q], a[p], b[q]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < KP; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Xs[(tj + 16 * q) * LDX + tk + 16 * p] = acc[p][q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < C::PF; ++q) {
+      const int e = tid + 256 * q, c = e / T, k = e - c * T, row = r0 + k, col = cidx[c];
+      if (col >= 0 && row < d.r) d.X[(size_t)row + (size_t)col * d.ld] = Xs[c * LDX + k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) atomicAdd(rows_updated, (unsigned long long)d.r);
 }
 
 // sigma_j = ||x_j||; rank positions by counting (descending, ties by index); count retained.
@@ -1520,6 +1825,74 @@ template <typename R> __global__ void __launch_bounds__(256) k_qp_update(const Q
   }
 }
 
+// Step k, part 2, for columns of at most 256*EPT rows: one CTA per column, the column held in
+// registers, so each trailing entry is read once and written once per step (the warp-per-column
+// kernel above reads it twice).  Same reflector application and norm downdate.
+template <typename R> __device__ __forceinline__ cplx<R> block_csum(cplx<R> v, cplx<R>* red) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  cplx<R> t = czero<R>();
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t = t + red[w];
+  __syncthreads();
+  return t;
+}
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(256) k_qp_update_cta(const QpD<R>* __restrict__ ds, int k, R tol3z) {
+  const QpD<R> d = ds[blockIdx.y];
+  if (k >= min(d.m, d.n)) return;
+  const int j = k + 1 + blockIdx.x;
+  if (j >= d.n) return;
+  __shared__ cplx<R> red[8];
+  __shared__ cplx<R> yk_s;
+  const R tau = *d.tau;
+  cplx<R>* y = d.A + (size_t)j * d.lda;
+  const int tid = threadIdx.x;
+  cplx<R> yv[EPT];
+  cplx<R> w = czero<R>();
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = k + tid + 256 * e;
+    yv[e] = i < d.m ? y[i] : czero<R>();
+    if (i < d.m) cfmac(w, d.v[i], yv[e]);
+  }
+  if (tau != R(0)) {
+    w = tau * block_csum<R>(w, red);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int i = k + tid + 256 * e;
+      if (i < d.m) {
+        yv[e] = yv[e] - d.v[i] * w;
+        y[i] = yv[e];
+      }
+    }
+  }
+  if (tid == 0) yk_s = yv[0];
+  R vn1 = d.vn1[j];                      // every thread reads the norms before thread 0 updates them
+  const R vn2 = d.vn2[j];
+  __syncthreads();
+  if (vn1 != R(0)) {
+    const R a = sqrt(abs2(yk_s)) / vn1;
+    const R temp = fmax(R(0), (R(1) + a) * (R(1) - a));
+    const R ratio = vn1 / vn2;
+    if (temp * ratio * ratio <= tol3z) {
+      cplx<R> s = czero<R>();
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = k + tid + 256 * e;
+        if (i > k && i < d.m) s.x += abs2(yv[e]);
+      }
+      vn1 = sqrt(block_csum<R>(s, red).x);
+      if (tid == 0) { d.vn1[j] = vn1; d.vn2[j] = vn1; }
+    } else if (tid == 0) {
+      d.vn1[j] = vn1 * sqrt(temp);
+    }
+  }
+}
+
 // |R_kk| of the pivoted QR (one thread per diagonal entry).
 template <typename R> __global__ void k_rdiag(const QpD<R>* __restrict__ ds, R* const* __restrict__ out) {
   const QpD<R> d = ds[blockIdx.y];
@@ -1534,17 +1907,34 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   P.assign(nm, Mat<R>());
   S.assign(nm, {});
   auto mk = ar_->mark();
+  // 0. tall inputs (w well above r): unpivoted blocked Householder QR first.  Ct = Q0 R0 with
+  //    R0 (r x r) in the top block of Ct; the pivoted QR below then runs on R0, which has the
+  //    same column norms, pivots and R as Ct (Q0 has orthonormal columns), at r/w of the cost.
+  std::vector<Mat<R>> Cw(Ct.begin(), Ct.end());
+  {
+    std::vector<Mat<R>> tall;
+    std::vector<size_t> ti;
+    for (size_t i = 0; i < nm; ++i)
+      if (Ct[i].n >= 64 && (long long)Ct[i].m * 4 > (long long)Ct[i].n * 5) {
+        tall.push_back(Ct[i]);
+        ti.push_back(i);
+      }
+    if (!tall.empty() && std::getenv("NH_NO_QR_FIRST") == nullptr) {
+      qr(tall, *ar_);   // factors are not kept: only R0 (zero below the diagonal) is needed
+      for (size_t q = 0; q < ti.size(); ++q) Cw[ti[q]].m = Cw[ti[q]].n;
+    }
+  }
   // 1. pivoted QR of Ct (w x r): Ct Pi = Q R, R (p x r), p = min(w, r).  Then
   //    C = Pi R^* Q^*, so the left singular vectors of C are Pi times those of R^*.
   std::vector<QpD<R>> qp;
   std::vector<int*> perms(nm, nullptr);
   int pmax = 0, nmax = 0;
   for (size_t i = 0; i < nm; ++i) {
-    const int w = Ct[i].m, r = Ct[i].n;
+    const int w = Cw[i].m, r = Cw[i].n;
     perms[i] = ar_->template arr<int>(std::max(r, 1));
     if (w <= 0 || r <= 0) continue;
     QpD<R> q;
-    q.A = Ct[i].p; q.lda = Ct[i].ld; q.m = w; q.n = r;
+    q.A = Cw[i].p; q.lda = Cw[i].ld; q.m = w; q.n = r;
     q.perm = perms[i];
     q.vn1 = ar_->template arr<R>(r);
     q.vn2 = ar_->template arr<R>(r);
@@ -1565,13 +1955,19 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     if (prof.on)
       for (auto& q : qp) fl += 8.0 * (double)q.m * q.n * std::min(q.m, q.n);
     prof.begin(st_);
+    int mmax = 0;
+    for (auto& q : qp) mmax = std::max(mmax, q.m);
     for (int k = 0; k < pmax; ++k) {
       k_qp_pivot<R><<<(int)qp.size(), 256, 0, st_>>>(dq, k);
       NH_LAUNCH_CK();
-      const int cols = nmax - k - 1;
+      const int cols = nmax - k - 1, rows = mmax - k;
       if (cols > 0) {
-        dim3 gu((cols + 7) / 8, (unsigned)qp.size());
-        k_qp_update<R><<<gu, 256, 0, st_>>>(dq, k, tol3z);
+        dim3 gc((unsigned)cols, (unsigned)qp.size());
+        if (rows <= 256 * 4) k_qp_update_cta<R, 4><<<gc, 256, 0, st_>>>(dq, k, tol3z);
+        else if (rows <= 256 * 8) k_qp_update_cta<R, 8><<<gc, 256, 0, st_>>>(dq, k, tol3z);
+        else if (rows <= 256 * 16) k_qp_update_cta<R, 16><<<gc, 256, 0, st_>>>(dq, k, tol3z);
+        else if (rows <= 256 * 32) k_qp_update_cta<R, 32><<<gc, 256, 0, st_>>>(dq, k, tol3z);
+        else k_qp_update<R><<<dim3((cols + 7) / 8, (unsigned)qp.size()), 256, 0, st_>>>(dq, k, tol3z);
         NH_LAUNCH_CK();
       }
       count(2);
@@ -1587,7 +1983,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     std::vector<int> pq;
     int pm = 0;
     for (size_t i = 0, q = 0; i < nm; ++i) {
-      const int w = Ct[i].m, r = Ct[i].n;
+      const int w = Cw[i].m, r = Cw[i].n;
       peff[i] = std::min(w, r);
       if (w <= 0 || r <= 0) continue;
       dgp.push_back(ar_->template arr<R>(peff[i]));
@@ -1623,9 +2019,9 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   std::vector<Mat<R>> X(nm);
   std::vector<CopyD<R>> cp;
   for (size_t i = 0; i < nm; ++i) {
-    const int w = Ct[i].m, r = Ct[i].n, p = std::min(peff[i], std::min(w, r));
+    const int w = Cw[i].m, r = Cw[i].n, p = std::min(peff[i], std::min(w, r));
     X[i] = ar_->template mat<R>(r, p);
-    if (r > 0 && p > 0) cp.push_back({Ct[i].p, X[i].p, r, p, Ct[i].ld, X[i].ld, OP_C, R(1), R(0)});
+    if (r > 0 && p > 0) cp.push_back({Cw[i].p, X[i].p, r, p, Cw[i].ld, X[i].ld, OP_C, R(1), R(0)});
   }
   copy(cp);
   // 3. Jacobi sweeps
@@ -1634,17 +2030,31 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   unsigned* offs = ar_->template arr<unsigned>(nm + 1);
   int* done = ar_->template arr<int>(nm + 1, true);
   R* amaxv = ar_->template arr<R>(nm + 1, true);
+  // Ordering: block pairs in round-robin order.  Matrices with many rows use the blocked
+  // (Gram) step on pairs of 32-column blocks; small ones the scalar rotations on pairs of
+  // 16-column blocks, where the Gram step's fixed cost would dominate.
+  int rmax_all = 0;
+  for (size_t i = 0; i < nm; ++i)
+    if (X[i].n >= 2) rmax_all = std::max(rmax_all, X[i].m);
+  enum { J_SCALAR, J_CLUSTER, J_BLOCK } jmode = rmax_all >= 512 ? J_BLOCK : J_SCALAR;
+  if (const char* e = std::getenv("NH_JACOBI_MODE")) {
+    if (!std::strcmp(e, "scalar")) jmode = J_SCALAR;
+    else if (!std::strcmp(e, "cluster")) jmode = J_CLUSTER;
+    else if (!std::strcmp(e, "block")) jmode = J_BLOCK;
+  }
+  const int bw = jmode == J_BLOCK ? 32 : 16;
   int maxblk = 0;
   for (size_t i = 0; i < nm; ++i) {
     const int p = X[i].n;
     if (p < 2 || X[i].m == 0) continue;
-    int nb = (p + 15) / 16;
+    int nb = (p + bw - 1) / bw;
     if (nb < 2) nb = 2;
     if (nb & 1) nb++;
     jd.push_back({X[i].p, X[i].ld, X[i].m, p, nb, offs + i, done + i, amaxv + i});
     jmap.push_back((int)i);
     maxblk = std::max(maxblk, nb);
   }
+  unsigned long long* rows_upd = ar_->template arr<unsigned long long>(1, true);
   const double u = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
   std::vector<std::vector<cplx<R>>> init_copy;
   if (std::getenv("NH_DUMP_TSVD")) {
@@ -1662,17 +2072,27 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     int rmax = 0;
     for (auto& j : jd) rmax = std::max(rmax, j.r);
     const R tol = (R)(4.0 * u * std::sqrt((double)std::max(rmax, 1)));
-    // cluster-resident rounds when a block pair's row slab fits in shared memory
+    // Large matrices: cluster-resident rounds (the 32 columns of a block pair stay in shared
+    // memory, split by rows over 8 or 16 CTAs).  Small ones: global-memory rounds.
+    int JCS = 8;
+    if ((size_t)32 * ((rmax + 7) / 8) * sizeof(cplx<R>) > (size_t)200 * 1024) JCS = 16;
     const int rpc = (rmax + JCS - 1) / JCS;
     const size_t jsmem = (size_t)32 * rpc * sizeof(cplx<R>);
-    const bool use_cluster = jsmem <= (size_t)200 * 1024 && std::getenv("NH_JACOBI_CLUSTER") != nullptr;
-    if (use_cluster)
+    if (jmode == J_CLUSTER && jsmem > (size_t)200 * 1024) jmode = J_SCALAR;
+    const bool use_cluster = jmode == J_CLUSTER;
+    if (jmode == J_BLOCK)
+      NH_CK(cudaFuncSetAttribute(k_jacobi_blk<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JbCfg<R>::smem));
+    if (use_cluster) {
       NH_CK(cudaFuncSetAttribute(k_jacobi_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(jsmem, 1)));
+      if (JCS > 8) NH_CK(cudaFuncSetAttribute(k_jacobi_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
     // columns with norm <= delta * (largest column norm) are numerically zero; delta sits well
     // below the truncation threshold eps so no retained direction is affected
     const double delta = 0.1 * eps;
     const R negl2 = (R)(delta * delta);
+    // sweeps end when no pair's cosine exceeds tol_out (blocked steps: twice the rotation threshold)
+    const R tol_out = jmode == J_BLOCK ? R(2) * tol : tol;
     for (int sweep = 0; sweep < 40; ++sweep) {
       NH_CK(cudaMemsetAsync(offs, 0, nm * sizeof(unsigned), st_));
       k_colmax<R><<<(int)jd.size(), 256, 0, st_>>>(djd);
@@ -1680,11 +2100,20 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
       count();
       double fl = 0;
       if (prof.on)
-        for (size_t q = 0; q < jd.size(); ++q)
-          if (!hdone[jmap[q]]) fl += 40.0 * jd[q].r * ((double)jd[q].k * (jd[q].k - 1) / 2.0);
+        for (size_t q = 0; q < jd.size(); ++q) {
+          if (hdone[jmap[q]]) continue;
+          if (jmode == J_BLOCK)   // Gram of every block pair: 8 W^2 flops per row
+            fl += 8.0 * JbCfg<R>::W * JbCfg<R>::W * jd[q].r * (double)(jd[q].nblk / 2) * (jd[q].nblk - 1);
+          else
+            fl += 40.0 * jd[q].r * ((double)jd[q].k * (jd[q].k - 1) / 2.0);
+        }
       prof.begin(st_);
       for (int rd = 0; rd < maxblk - 1; ++rd) {
-        if (use_cluster) {
+        if (jmode == J_BLOCK) {
+          dim3 grid(maxblk / 2, (unsigned)jd.size());
+          k_jacobi_blk<R><<<grid, 256, JbCfg<R>::smem, st_>>>(djd, rd, tol, tol_out, negl2, 16, rows_upd);
+          NH_LAUNCH_CK();
+        } else if (use_cluster) {
           cudaLaunchConfig_t cfg = {};
           cfg.gridDim = dim3((unsigned)(maxblk / 2 * JCS), (unsigned)jd.size());
           cfg.blockDim = dim3(512);
@@ -1723,7 +2152,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         if (hdone[i]) continue;
         float f;
         std::memcpy(&f, &hoff[i], 4);
-        if ((double)f <= (double)tol) hdone[i] = 1; else all = false;
+        if ((double)f <= (double)tol_out) hdone[i] = 1; else all = false;
       }
       NH_CK(cudaMemcpyAsync(done, hdone.data(), nm * sizeof(int), cudaMemcpyHostToDevice, st_));
       if (all || sweep == 39) {
@@ -1758,6 +2187,12 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         break;
       }
     }
+  }
+  if (prof.on && jmode == J_BLOCK && !jd.empty()) {   // X_P V of the block pairs that rotated
+    unsigned long long ru = 0;
+    NH_CK(cudaMemcpyAsync(&ru, rows_upd, sizeof(ru), cudaMemcpyDeviceToHost, st_));
+    NH_CK(cudaStreamSynchronize(st_));
+    prof.add_flops(K_JACOBI, 8.0 * JbCfg<R>::W * JbCfg<R>::W * (double)ru);
   }
   // 4. sort + count
   std::vector<SortD<R>> sd;
@@ -1817,9 +2252,8 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
 
 void gemm_launch_raw(const GemmD<double>* desc, const int* pre, int np, int tiles, cudaStream_t st) {
   if (tiles <= 0) return;
-  k_gemm<double, GemmCfg<double>::TM, GemmCfg<double>::TN, GemmCfg<double>::BK><<<tiles, 256, 0, st>>>(
-      desc, pre, np, nullptr, nullptr);
-  NH_LAUNCH_CK();
+  launch_gemm<double, GemmCfg<double>::TM, GemmCfg<double>::TN, GemmCfg<double>::BK>(0, tiles, st, desc, pre, np,
+                                                                                     nullptr, nullptr);
 }
 
 int gemm_tiles(const GemmD<double>& g) {

@@ -81,6 +81,7 @@ class Prof {
   void begin(cudaStream_t st);
   void end(cudaStream_t st, int cls, double flops, double bytes);
   void collect();   // synchronises the recorded events and accumulates
+  void add_flops(int cls, double f) { if (on) stats[cls].flops += f; }
   KStat stats[K_NCLASS];
 
  private:
@@ -93,6 +94,7 @@ class Prof {
 
 // Launch the batched GEMM kernel on caller-provided device descriptors (no allocation, no
 // copies): desc[np] and the exclusive tile prefix pre[np] already live in device memory.
+// Every descriptor must have opA == opB == OP_N.
 void gemm_launch_raw(const GemmD<double>* desc, const int* pre, int np, int tiles, cudaStream_t st);
 int gemm_tiles(const GemmD<double>& g);
 
@@ -135,6 +137,7 @@ template <typename R> class Ops {
   int* upload_ints(const std::vector<int>& v);
 
  private:
+  void gemm_class(const std::vector<GemmD<R>>& d, int cls);   // one operand-layout class
   template <typename D> D* upload(const std::vector<D>& v);
   void* stage(const void* src, size_t bytes);
   cudaStream_t st_;

@@ -2,7 +2,8 @@
 
 * Householder QR (single-CTA panels and cluster-cooperative panels for tall matrices):
   Q R = A, Q^* Q = I, |R_ii| equal to LAPACK's.
-* Truncated SVD (QR + one-sided Jacobi, cluster-resident and global-memory variants):
+* Truncated SVD (pivoted QR + one-sided Jacobi: blocked Gram steps, scalar rotations in
+  global memory, and cluster-resident scalar rotations):
   singular values equal LAPACK's, P^* P = I, and the discarded part of C is below the
   threshold -- the truncation rule of the recompression (Sec. 2.2).
 """
@@ -48,11 +49,11 @@ CASES = [(64, 200, "graded"), (300, 120, "graded"), (520, 1500, "graded"), (1577
          (400, 400, "repeated"), (256, 512, "rankdef"), (1024, 3000, "wide"), (300, 900, "wide")]
 
 
-@pytest.mark.parametrize("jacobi", ["cluster", "global"])
+@pytest.mark.parametrize("jacobi", ["auto", "block", "scalar", "cluster"])
 @pytest.mark.parametrize("r,w,kind", CASES)
 def test_tsvd_fp64(nh, monkeypatch, jacobi, r, w, kind):
-    if jacobi == "cluster":
-        monkeypatch.setenv("NH_JACOBI_CLUSTER", "1")
+    if jacobi != "auto":
+        monkeypatch.setenv("NH_JACOBI_MODE", jacobi)
     C = make_matrix(r, w, kind, r + w)
     eps = 1e-10
     P, sig = nh.la_tsvd(torch.from_numpy(C).cuda(), eps)
@@ -66,8 +67,10 @@ def test_tsvd_fp64(nh, monkeypatch, jacobi, r, w, kind):
     assert np.linalg.norm(resid, 2) <= 2 * eps * s_ref[0] + 1e-13 * s_ref[0]
 
 
-@pytest.mark.parametrize("r,w", [(300, 120), (1577, 3000)])
-def test_tsvd_fp32(nh, r, w):
+@pytest.mark.parametrize("jacobi", ["block", "scalar"])
+@pytest.mark.parametrize("r,w", [(300, 120), (1577, 3000), (2600, 2100)])
+def test_tsvd_fp32(nh, monkeypatch, jacobi, r, w):
+    monkeypatch.setenv("NH_JACOBI_MODE", jacobi)
     C = make_matrix(r, w, "graded", 5).astype(np.complex64)
     eps = 1e-5
     P, sig = nh.la_tsvd(torch.from_numpy(C).cuda(), eps)
@@ -76,10 +79,16 @@ def test_tsvd_fp32(nh, r, w):
     s_ref = np.linalg.svd(C64, compute_uv=False)
     k = P.shape[1]
     assert abs(k - int(np.sum(s_ref > eps * s_ref[0]))) <= 2
-    assert np.max(np.abs(np.array(sig[:k]) - s_ref[:k])) < 1e-5 * s_ref[0]
-    assert np.max(np.abs(P.conj().T @ P - np.eye(k))) < 1e-5
-    resid = C64 - P @ (P.conj().T @ C64)
-    assert np.linalg.norm(resid, 2) <= 5 * eps * s_ref[0]
+    # FP32 pivoted QR + Jacobi: every column takes part in ~1e4 rotations or block updates, each
+    # rounding at u * sigma_1; 5e-5 * sigma_1 was observed with both sweep kinds
+    assert np.max(np.abs(np.array(sig[:k]) - s_ref[:k])) < 2e-4 * s_ref[0]
+    # the sweeps stop once every column cosine is below 4 u sqrt(r) (about 1e-5 here), so P is
+    # orthonormal to that level; the subspace it spans is checked through an orthonormal basis
+    u32 = 2.0 ** -24
+    assert np.max(np.abs(P.conj().T @ P - np.eye(k))) < 2 * 4 * u32 * np.sqrt(r)
+    Qo, _ = np.linalg.qr(P)
+    resid = C64 - Qo @ (Qo.conj().T @ C64)
+    assert np.linalg.norm(resid, 2) <= 2 * eps * s_ref[0]
 
 
 @pytest.mark.parametrize("m,n,grouped", [(100, 60, False), (40, 100, False), (2000, 300, False), (5000, 100, False),
@@ -98,3 +107,29 @@ def test_qr(nh, m, n, grouped, dtype):
     p = min(m, n)
     Rl = np.linalg.qr(A64, mode="r")
     assert np.max(np.abs(np.abs(np.diag(R[:p, :p])) - np.abs(np.diag(Rl[:p, :p])))) < tol * 10 * np.max(np.abs(A64)) * np.sqrt(m)
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (37, 53, 29), (128, 128, 128), (300, 257, 1000), (1100, 900, 64),
+                                   (40, 33, 3000), (515, 700, 0)])
+@pytest.mark.parametrize("ops", ["NN", "CN", "NC", "TT"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_gemm(nh, m, n, k, ops, dtype):
+    """Batched GEMM (3 problems, alpha = -1.5, beta = 0.5) against complex128 matmul."""
+    dt = torch.complex128 if dtype == "fp64" else torch.complex64
+    opa, opb = ops
+    sa = (m, k) if opa == "N" else (k, m)
+    sb = (k, n) if opb == "N" else (n, k)
+    A = torch.from_numpy(_rand((3,) + sa, m + 7 * n + k)).to(dt)
+    B = torch.from_numpy(_rand((3,) + sb, m + n + 11 * k)).to(dt)
+    C = torch.from_numpy(_rand((3, m, n), 3 * m + n)).to(dt)
+
+    def op(X, o):
+        X = X.to(torch.complex128)
+        return X if o == "N" else (X.transpose(1, 2) if o == "T" else X.transpose(1, 2).conj())
+
+    ref = -1.5 * (op(A, opa) @ op(B, opb)) + 0.5 * C.to(torch.complex128)
+    out = nh.la_gemm(A.cuda(), B.cuda(), opa, opb, alpha=-1.5, beta=0.5, C=C.cuda()).cpu().to(torch.complex128)
+    u = 2.0 ** -53 if dtype == "fp64" else 2.0 ** -24
+    scale = 1.5 * torch.sqrt(torch.tensor(float(max(k, 1)))) * 4 + 1
+    err = (out - ref).abs().max().item()
+    assert err < 20 * u * float(scale) * max(1.0, float(ref.abs().max()))
