@@ -54,7 +54,9 @@ typedef enum {
   NUDFT2_EXACT_FWD = 2, /* out (M x nrhs) = A in, direct O(MN) sum of Eq. 1 in FP64              */
   NUDFT2_EXACT_ADJ = 3, /* out (N x nrhs) = A^* in, direct O(MN) sum in FP64                     */
   NUDFT2_PINV = 4,      /* out (N x nrhs) = F^{-1} G~_hss^+ in (same as nudft2_hss_solve)         */
-  NUDFT2_PINV_ADJ = 5   /* reserved */
+  NUDFT2_PINV_ADJ = 5   /* out (M x nrhs) = (F^{-1} G~_hss^+)^* in: the adjoint of PINV, for the
+                           backward pass of c = A^+ f (Sec. 4.1 uses the adjoint for LSQR); in
+                           MIXED mode refined on A^* out = in with the FP64 exact adjoint        */
 } nudft2_op;
 
 typedef struct {
@@ -112,10 +114,26 @@ nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int
                                void* stream);
 
 /* Apply one operator of nudft2_op to nrhs columns: EXACT_FWD/EXACT_ADJ need only build;
- * FAST_FWD needs build; PINV needs factor.  Shapes as documented on nudft2_op.
+ * FAST_FWD needs build; PINV and PINV_ADJ need factor.  Shapes as documented on nudft2_op.
  * Errors: EINVAL (op unknown, ld too small), ESTATE, ENOTIMPL (reserved ops). */
 nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t ldi, int nrhs, void* d_out,
                                int64_t ldo, void* stream);
+
+/* Backward pass of the least-squares solution c = A^+ f for a real loss L(c), all complex128
+ * device arrays, columns independent right-hand sides:
+ *   d_f (M x nrhs, ld ldf)  the data f;  d_c (N x nrhs, ld ldc) its solution (from solve);
+ *   d_g (N x nrhs, ld ldg)  the incoming gradient dL/dRe c + i dL/dIm c (torch convention).
+ * Outputs (each may be NULL; d_gx and d_gy together):
+ *   d_gf (M x nrhs, ld ldgf)  dL/dRe f + i dL/dIm f = lam = (A^+)^* g  (PINV_ADJ);
+ *   d_gx, d_gy (M doubles, caller point order)  dL/dx_j, dL/dy_j, summed over the columns:
+ *     dL/dx_j = sum_q Re[ -conj(lam_jq) (A_x c)_jq + conj((A_x mu)_jq) r_jq ],
+ *   with mu = A^+ lam, r = f - A c, (A_x)_jk = -2 pi i kx A_jk (Golub-Pereyra derivative of a
+ *   full-rank least-squares solution; the paper has no gradient).  Products with A are the FP64
+ *   exact apply of Eq. 1.  Synchronises the stream.
+ * Errors: ESTATE (not factored), EINVAL. */
+nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, const void* d_c, int64_t ldc,
+                              const void* d_g, int64_t ldg, int nrhs, void* d_gf, int64_t ldgf, double* d_gx,
+                              double* d_gy, void* stream);
 
 /* Statistics of the handle (ranks, stage times, memory).  Errors: EINVAL (NULL). */
 nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);

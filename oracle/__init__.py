@@ -6,5 +6,6 @@ non-GPU tests in tests/test_oracle_pins.py.  Shares no code with the CUDA path.
 """
 from .nudft_oracle import (  # noqa: F401
     nudft_1d, nudft_matrix, forward, adjoint, householder_qr, apply_qh, apply_q, back_substitute,
-    lstsq, cgls, dft_matrix, tilde_1d, tilde_2d, idft2, relres, relerr,
+    lstsq, cgls, dft_matrix, tilde_1d, tilde_2d, idft2, relres, relerr, forward_substitute_h, pinv_adjoint,
+    lstsq_grad,
 )

@@ -20,6 +20,10 @@ What it computes, each by its plain definition (Li & Liu, "A superfast direct so
 * ``idft2`` -- the 2D inverse DFT c = F^{-1} y with F = F^x (x) F^y, F(k,l) = exp(-2 pi i k l / n)
   (Sec. 2.4), by its defining sums.
 * ``relres`` / ``relerr`` -- r_s and e_s of Sec. 5.
+* ``pinv_adjoint`` / ``lstsq_grad`` -- (A^+)^* g and the gradient of a real loss of the
+  least-squares solution with respect to f and to the point coordinates (the derivative of
+  the normal equations; the paper itself states no gradient).  Pinned by central finite
+  differences of ``lstsq`` and by the minimum-norm characterisation of (A^+)^* g.
 
 Pins (tests/test_oracle_pins.py) tie every function to something other than itself: the 2D
 FFT on an unperturbed grid, A^*A = N I, brute-force normal equations in extended precision,
@@ -179,6 +183,56 @@ def lstsq(A: np.ndarray, f: np.ndarray):
     res = np.linalg.norm(G[n:], axis=0)
     rmin = float(np.min(np.abs(np.diag(R[:n, :n]))))
     return (c[:, 0] if squeeze else c), res, rmin
+
+
+def forward_substitute_h(R: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Solve R^* z = g (R square upper triangular, so R^* is lower triangular), row by row from the top."""
+    n = R.shape[0]
+    Rh = R.conj().T
+    z = np.zeros_like(g, dtype=np.complex128)
+    for i in range(n):
+        z[i] = (g[i] - Rh[i, :i] @ z[:i]) / Rh[i, i]
+    return z
+
+
+def pinv_adjoint(A: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """lam = (A^+)^* g for full column rank A (M >= N): with A = Q [R; 0], A^+ = R^{-1} Q_1^*, so
+    lam = Q [R^{-*} g; 0].  Equivalently the minimum-norm solution of A^* lam = g."""
+    A = np.asarray(A, dtype=np.complex128)
+    g = np.asarray(g, dtype=np.complex128)
+    squeeze = g.ndim == 1
+    G = g[:, None] if squeeze else g
+    m, n = A.shape
+    R, vs, taus = householder_qr(A)
+    Z = np.zeros((m, G.shape[1]), dtype=np.complex128)
+    Z[:n] = forward_substitute_h(R[:n, :n], G)
+    lam = apply_q(vs, taus, Z)
+    return lam[:, 0] if squeeze else lam
+
+
+def lstsq_grad(x, y, nx, ny, f, G):
+    """Gradient of a real loss L of the least-squares solution c = A(x, y)^+ f (Sec. 1), for the
+    incoming gradient G = dL/dRe c + i dL/dIm c (N x s).  Differentiating the normal equations
+    A^* A c = A^* f of a full-column-rank A gives
+        dc = -A^+ (dA) c + (A^* A)^{-1} (dA)^* r,   r = f - A c,
+    so with lam = (A^+)^* G and mu = (A^* A)^{-1} G = A^+ lam,
+        dL = Re[ -<lam, (dA) c> + <(dA) mu, r> ],   <u, v> = sum conj(u) v.
+    Row j of A depends on (x_j, y_j) only, with d/dx_j A(j, (kx, ky)) = -2 pi i kx A(j, (kx, ky)).
+    Returns (c, lam, grad_x, grad_y); lam is also dL/dRe f + i dL/dIm f."""
+    A = nudft_matrix(x, y, nx, ny)
+    f = np.asarray(f, dtype=np.complex128).reshape(A.shape[0], -1)
+    G = np.asarray(G, dtype=np.complex128).reshape(A.shape[1], -1)
+    c, _, _ = lstsq(A, f)
+    lam = pinv_adjoint(A, G)
+    mu, _, _ = lstsq(A, lam)
+    r = f - A @ c
+    kx = np.repeat(np.arange(nx, dtype=np.float64), ny)
+    ky = np.tile(np.arange(ny, dtype=np.float64), nx)
+    Ax = A * (-1j * TWO_PI * kx)[None, :]
+    Ay = A * (-1j * TWO_PI * ky)[None, :]
+    gx = np.sum(np.real(-np.conj(lam) * (Ax @ c) + np.conj(Ax @ mu) * r), axis=1)
+    gy = np.sum(np.real(-np.conj(lam) * (Ay @ c) + np.conj(Ay @ mu) * r), axis=1)
+    return c, lam, gx, gy
 
 
 def cgls(x, y, f, nx, ny, tol=1e-13, maxit=500):

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_solve.argtypes = [vp, vp, i64, ci, vp, i64, vp]
     L.nudft2_hss_apply.argtypes = [vp, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_hss_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.nudft2_hss_grad.argtypes = [vp, vp, i64, vp, i64, vp, i64, ci, vp, i64, vp, vp, vp]
     L.nudft2_hss_free.argtypes = [vp]
     L.nudft2_hss_free.restype = None
     L.nudft2_psi_eval.argtypes = [vp, i64, ci, vp, vp]
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
+              "nudft2_hss_grad",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc"):
         getattr(L, f).restype = ctypes.c_int
@@ -216,8 +218,9 @@ class NudftHSS:
         return c[0] if squeeze else c.t()
 
     def apply(self, op: int, v: torch.Tensor) -> torch.Tensor:
-        rows_in = self.N if op in (FAST_FWD, EXACT_FWD) else self.M
-        rows_out = self.M if op in (FAST_FWD, EXACT_FWD) else self.N
+        to_points = op in (FAST_FWD, EXACT_FWD, PINV_ADJ)
+        rows_in = self.N if to_points else self.M
+        rows_out = self.M if to_points else self.N
         squeeze = v.dim() == 1
         vc = _colmajor(v, rows_in)
         s = vc.shape[0]
@@ -225,6 +228,21 @@ class NudftHSS:
         _check(lib().nudft2_hss_apply(self._h, op, ctypes.c_void_p(vc.data_ptr()), rows_in, s,
                                       ctypes.c_void_p(out.data_ptr()), rows_out, _stream(self.stream)))
         return out[0] if squeeze else out.t()
+
+    def grad(self, f: torch.Tensor, c: torch.Tensor, g: torch.Tensor, points: bool = True):
+        """Backward of c = A^+ f for a real loss with gradient g = dL/dRe c + i dL/dIm c (N, s):
+        returns (grad_f (M, s), grad_x (M,), grad_y (M,)); grad_x/grad_y are None unless points."""
+        squeeze = f.dim() == 1
+        fc, cc, gc = _colmajor(f, self.M), _colmajor(c, self.N), _colmajor(g, self.N)
+        s = fc.shape[0]
+        gf = torch.empty((s, self.M), dtype=torch.complex128, device="cuda")
+        gx = torch.empty(self.M, dtype=torch.float64, device="cuda") if points else None
+        gy = torch.empty(self.M, dtype=torch.float64, device="cuda") if points else None
+        _check(lib().nudft2_hss_grad(self._h, ctypes.c_void_p(fc.data_ptr()), self.M, ctypes.c_void_p(cc.data_ptr()),
+                                     self.N, ctypes.c_void_p(gc.data_ptr()), self.N, s, ctypes.c_void_p(gf.data_ptr()),
+                                     self.M, ctypes.c_void_p(gx.data_ptr() if points else None),
+                                     ctypes.c_void_p(gy.data_ptr() if points else None), _stream(self.stream)))
+        return (gf[0] if squeeze else gf.t()), gx, gy
 
     def info(self) -> dict:
         i = Info()
@@ -252,3 +270,30 @@ class NudftHSS:
             self.close()
         except Exception:
             pass
+
+
+class _Lstsq(torch.autograd.Function):
+    """c = A(x, y)^+ f through the HSS factorization; backward by nudft2_hss_grad (adjoint solve,
+    one more solve and the FP64 exact applies of the point derivatives)."""
+
+    @staticmethod
+    def forward(ctx, f, x, y, nx, ny, opts):
+        h = NudftHSS(x.detach(), y.detach(), nx, ny, **opts).factor()
+        c = h.solve(f.detach())
+        ctx.h = h
+        ctx.save_for_backward(f, c)
+        return c
+
+    @staticmethod
+    def backward(ctx, gc):
+        f, c = ctx.saved_tensors
+        need_pts = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+        gf, gx, gy = ctx.h.grad(f.detach(), c, gc.contiguous(), points=need_pts)
+        return (gf if ctx.needs_input_grad[0] else None, gx if ctx.needs_input_grad[1] else None,
+                gy if ctx.needs_input_grad[2] else None, None, None, None)
+
+
+def lstsq(f: torch.Tensor, x: torch.Tensor, y: torch.Tensor, nx: int, ny: int, **opts) -> torch.Tensor:
+    """Differentiable c = argmin ||A(x, y) c - f|| (f (M,) or (M, s) complex128 on CUDA; x, y (M,)
+    float64).  opts go to NudftHSS (eps, levels, prec, ...); the handle is built per call."""
+    return _Lstsq.apply(f, x, y, nx, ny, opts)

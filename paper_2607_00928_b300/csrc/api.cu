@@ -132,7 +132,8 @@ static void exact_adj(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, dou
 }
 
 // c = F^{-1} y per column: C = Fy^{-1} Y Fx^{-1} with Y viewed ny x nx (lexicographic order)
-static void dft2(nudft2_hss_s* h, const double2* y, int64_t ldy, int s, double2* c, int64_t ldc, bool inverse) {
+static void dft2(nudft2_hss_s* h, const double2* y, int64_t ldy, int s, double2* c, int64_t ldc, bool inverse,
+                 double scale = 1.0) {
   const int nx = h->nx, ny = h->ny;
   auto mk = h->scr.mark();
   double2* T = h->scr.arr<double2>((size_t)h->N * s);
@@ -141,7 +142,7 @@ static void dft2(nudft2_hss_s* h, const double2* y, int64_t ldy, int s, double2*
   const double2* Fx = inverse ? h->Fxi : h->Fxf;
   for (int q = 0; q < s; ++q) {
     g1.push_back(g64(Fy, ny, OP_N, y + (size_t)q * ldy, ny, OP_N, T + (size_t)q * h->N, ny, ny, nx, ny));
-    g2.push_back(g64(T + (size_t)q * h->N, ny, OP_N, Fx, nx, OP_N, c + (size_t)q * ldc, ny, ny, nx, nx));
+    g2.push_back(g64(T + (size_t)q * h->N, ny, OP_N, Fx, nx, OP_N, c + (size_t)q * ldc, ny, ny, nx, nx, scale));
   }
   h->ops->gemm(g1);
   h->ops->gemm(g2);
@@ -277,6 +278,63 @@ static void la_gemm(int opa, int opb, int m, int n, int k, double alpha, const v
             m, n, k, lda, ldb, ldc, opa, opb, (R)alpha, (R)beta};
   ops.gemm(d);
   NH_CK(cudaStreamSynchronize(st));   // the descriptor staging above lives on this host frame
+}
+
+// lam (M x s, caller point order) = (G~_hss^+)^* ylex, ylex in lexicographic column order.
+template <typename R> static void hss_solve_adj_lex(nudft2_hss_s* h, Hss<R>& H, const double2* ylex, int s,
+                                                    double2* lam, int64_t ldl) {
+  const int M = h->M, N = h->N;
+  auto mk = h->scr.mark();
+  cplx<R>* yt = h->scr.arr<cplx<R>>((size_t)N * s);
+  cplx<R>* f2 = h->scr.arr<cplx<R>>((size_t)M * s);
+  convert_gather<double, R>(h->st, ylex, N, h->pl.colmap, N, s, yt, N, 1.0);
+  H.solve_adj(yt, N, s, f2, M);
+  convert_scatter<R, double>(h->st, f2, M, h->pl.perm2, M, s, lam, (int)ldl, 1.0);
+  h->scr.release(mk);
+}
+
+// lam = (A^+)^* g with A^+ = F^{-1} G~^+ (the solve); (F^{-1})^* = F / N.  In mixed precision the
+// FP32 adjoint is refined on A^* lam = g with the FP64 exact adjoint apply, like the solve.
+static void do_solve_adj(nudft2_hss_s* h, const double2* g, int64_t ldg, int s, double2* lam, int64_t ldl) {
+  const int M = h->M, N = h->N;
+  auto mk = h->scr.mark();
+  double2* ylex = h->scr.arr<double2>((size_t)N * s);
+  if (h->h64) {
+    dft2(h, g, ldg, s, ylex, N, false, 1.0 / N);
+    hss_solve_adj_lex<double>(h, *h->h64, ylex, s, lam, ldl);
+    h->iters = 0;
+    h->relres = -1;
+  } else {
+    double2* r = h->scr.arr<double2>((size_t)N * s);
+    double2* d = h->scr.arr<double2>((size_t)M * s);
+    double* gn = h->scr.arr<double>(s);
+    double* rn = h->scr.arr<double>(s);
+    NH_CK(cudaMemcpy2DAsync(r, N * sizeof(double2), g, ldg * sizeof(double2), N * sizeof(double2), s,
+                            cudaMemcpyDeviceToDevice, h->st));
+    NH_CK(cudaMemset2DAsync(lam, ldl * sizeof(double2), 0, M * sizeof(double2), s, h->st));
+    colnorm2(h->st, N, s, r, N, gn);
+    std::vector<double> hg(s), hr(s);
+    NH_CK(cudaMemcpyAsync(hg.data(), gn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    int it = 0;
+    double worst = 1.0;
+    for (it = 1; it <= std::max(1, h->opt.refine_max); ++it) {
+      dft2(h, r, N, s, ylex, N, false, 1.0 / N);
+      hss_solve_adj_lex<float>(h, *h->h32, ylex, s, d, M);
+      axpy2(h->st, M, s, 1.0, d, M, lam, (int)ldl);
+      exact_adj(h, lam, ldl, s, r, N);                // r = A^* lam (FP64)
+      axpy2(h->st, N, s, -1.0, g, (int)ldg, r, N);    // r = A^* lam - g
+      colnorm2(h->st, N, s, r, N, rn);
+      NH_CK(cudaMemcpyAsync(hr.data(), rn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      NH_CK(cudaStreamSynchronize(h->st));
+      worst = 0;
+      for (int q = 0; q < s; ++q) worst = std::max(worst, std::sqrt(hr[q] / std::max(hg[q], 1e-300)));
+      if (worst <= h->opt.refine_tol) break;
+      axpy2(h->st, N, s, -2.0, r, N, r, N);            // r = g - A^* lam
+    }
+    h->iters = std::min(it, std::max(1, h->opt.refine_max));
+    h->relres = worst;
+  }
+  h->scr.release(mk);
 }
 
 // ----------------------------------------------------------------------------- C-ABI
@@ -517,13 +575,55 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
         h->scr.release(mk);
         break;
       }
-      case NUDFT2_FAST_ADJ:
       case NUDFT2_PINV_ADJ:
+        NH_REQUIRE(h->factored, ST_ESTATE, "apply PINV_ADJ before factor");
+        NH_REQUIRE(ldi >= N && ldo >= M, ST_EINVAL, "apply: leading dimension too small");
+        do_solve_adj(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
+        break;
+      case NUDFT2_FAST_ADJ:
         throw Error(ST_ENOTIMPL, "apply: operator not available in this build");
       default:
         throw Error(ST_EINVAL, "apply: unknown operator");
     }
     NH_CK(cudaStreamSynchronize(h->st));
+  });
+}
+
+nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, const void* d_c, int64_t ldc,
+                              const void* d_g, int64_t ldg, int nrhs, void* d_gf, int64_t ldgf, double* d_gx,
+                              double* d_gy, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr, ST_ESTATE, "grad: no handle");
+    NH_REQUIRE(h->factored, ST_ESTATE, "grad before factor");
+    const int M = h->M, N = h->N, s = nrhs;
+    NH_REQUIRE(s >= 1 && d_f && d_c && d_g && ldf >= M && ldc >= N && ldg >= N && (!d_gf || ldgf >= M) &&
+                   ((d_gx == nullptr) == (d_gy == nullptr)),
+               ST_EINVAL, "grad: bad arguments");
+    enter(h, stream);
+    auto mk = h->scr.mark();
+    // lam = (A^+)^* g  (also the gradient with respect to f)
+    double2* lam = d_gf ? (double2*)d_gf : h->scr.arr<double2>((size_t)M * s);
+    const int64_t ldl = d_gf ? ldgf : M;
+    do_solve_adj(h, (const double2*)d_g, ldg, s, lam, ldl);
+    if (d_gx) {
+      // mu = A^+ lam ; W = [c, Dx c, Dy c, Dx mu, Dy mu] ; E = A W (exact, FP64)
+      double2* mu = h->scr.arr<double2>((size_t)N * s);
+      do_solve(h, lam, ldl, s, mu, N);
+      double2* W = h->scr.arr<double2>((size_t)N * 5 * s);
+      double2* E = h->scr.arr<double2>((size_t)M * 5 * s);
+      NH_CK(cudaMemcpy2DAsync(W, N * sizeof(double2), d_c, ldc * sizeof(double2), N * sizeof(double2), s,
+                              cudaMemcpyDeviceToDevice, h->st));
+      deriv_weights(h->st, h->nx, h->ny, s, (const double2*)d_c, (int)ldc, W + (size_t)N * s, W + (size_t)2 * N * s, N);
+      deriv_weights(h->st, h->nx, h->ny, s, mu, N, W + (size_t)3 * N * s, W + (size_t)4 * N * s, N);
+      exact_fwd(h, W, N, 5 * s, E, M);
+      // r = f - A c (in place over the first block)
+      axpy2(h->st, M, s, -2.0, E, M, E, M);
+      axpy2(h->st, M, s, 1.0, (const double2*)d_f, (int)ldf, E, M);
+      grad_combine(h->st, M, s, lam, (int)ldl, E + (size_t)M * s, E + (size_t)2 * M * s, E + (size_t)3 * M * s,
+                   E + (size_t)4 * M * s, E, M, d_gx, d_gy);
+    }
+    NH_CK(cudaStreamSynchronize(h->st));
+    h->scr.release(mk);
   });
 }
 

@@ -1020,6 +1020,149 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
   scr_.release(mk);   // no synchronisation here: the solve is captured into a CUDA graph
 }
 
+// ------------------------------------------------------------------------------- adjoint solve
+// f2 = (G~_hss^+)^* y: the solve above is a fixed chain of linear steps (unitary transforms,
+// copies into sub-blocks, products with the factor blocks, triangular inverses), so its adjoint
+// runs the adjoint of each step in the reverse order: first the top-down sweep backwards
+// (Q_v^* on each node, then D11^{-*}, U1^*, D12^*, V2 and the B / R couplings), then the root
+// (R^{-*}, then P_root), then the bottom-up sweep backwards (P, then Omega, each applied
+// without conjugation, level 1 down to the leaves).  Rows that the solve discards (the
+// least-squares residual rows) get zero.
+template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int s, cplx<R>* f2, int ldf) {
+  NH_REQUIRE(factored, ST_ESTATE, "adjoint solve before factor");
+  const int L = pl_->L;
+  auto mk = scr_.mark();
+  std::vector<std::vector<Mat<R>>> Yb(L + 1), Fb(L + 1), Bb(L + 2);
+  for (int l = 1; l <= L; ++l) {
+    const int nn = (int)t_[l].size();
+    Fb[l].resize(nn);
+    Yb[l].resize(nn);
+    for (int p = 0; p < nn; ++p) Fb[l][p] = scr_.mat<R>(std::max(t_[l][p].m, 1), s, true);
+  }
+  {
+    std::vector<CopyD<R>> cp;
+    for (int p = 0; p < (int)t_[L].size(); ++p) {
+      Yb[L][p] = scr_.mat<R>(std::max(t_[L][p].n, 1), s);
+      cp.push_back({ytree + pl_->c0[L][p], Yb[L][p].p, pl_->nc[L][p], s, ldy, Yb[L][p].ld, OP_N, R(1), R(0)});
+    }
+    ops_.copy(cp);
+  }
+  Mat<R> crootb = scr_.mat<R>(std::max(root_cols_, 1), s);
+  // ---- top-down sweep, backwards
+  for (int l = L; l >= 1; --l) {
+    const int nn = (int)t_[l].size();
+    {
+      std::vector<QFac<R>> qv;
+      for (int q = 0; q < nn; ++q) qv.push_back(t_[l][q].Qv);
+      ops_.apply_q_left(qv, Yb[l], true);                        // Y <- Q_v^* Y
+    }
+    // destination of the C2 adjoints: the parent's Y adjoint (or the root's c adjoint)
+    if (l >= 2) {
+      Yb[l - 1].resize(t_[l - 1].size());
+      for (int p = 0; p < (int)t_[l - 1].size(); ++p) Yb[l - 1][p] = scr_.mat<R>(std::max(t_[l - 1][p].n, 1), s);
+    }
+    std::vector<Mat<R>> F1b(nn), C2b(nn);
+    std::vector<GemmD<R>> gf, gb, gc;
+    std::vector<CopyD<R>> cp;
+    Bb[l].resize(nn);
+    for (int q = 0; q < nn; ++q) {
+      const int p = q >> 2, c = q & 3;
+      Node2<R>& nd = t_[l][q];
+      int off = 0;
+      for (int c2 = 0; c2 < c; ++c2) off += t_[l][4 * p + c2].kv;
+      const Mat<R>& dst = (l == 1) ? crootb : Yb[l - 1][p];
+      C2b[q] = dst.block(off, 0, nd.kv, s);
+      F1b[q] = Fb[l][q].block(0, 0, nd.n1, s);
+      // c1 = D11^{-1} f1  =>  f1b = D11^{-*} Yb[kv:kv+n1]
+      gf.push_back(gd<R>(nd.D11inv, OP_C, Yb[l][q].block(nd.kv, 0, nd.n1, s), OP_N, F1b[q]));
+      // Y[0:kv] = C2  =>  C2b = Yb[0:kv]
+      cp.push_back({Yb[l][q].p, C2b[q].p, nd.kv, s, Yb[l][q].ld, C2b[q].ld, OP_N, R(1), R(0)});
+      Bb[l][q] = scr_.mat<R>(std::max(nd.ku, 1), s);
+    }
+    ops_.gemm(gf);
+    ops_.copy(cp);
+    // f1 = F1 - D12 C2 - U1 b  =>  C2b -= D12^* f1b ; bb = -U1^* f1b + sum_children R_child^* bb_child
+    for (int q = 0; q < nn; ++q) {
+      Node2<R>& nd = t_[l][q];
+      gb.push_back(gd<R>(nd.Wk.block(0, nd.ku, nd.n1, nd.kv), OP_C, F1b[q], OP_N, C2b[q], R(-1), R(1)));
+      gc.push_back(gd<R>(nd.Wk.block(0, 0, nd.n1, nd.ku), OP_C, F1b[q], OP_N, Bb[l][q], R(-1), R(0)));
+    }
+    ops_.gemm(gb);
+    ops_.gemm(gc);
+    if (l < L)
+      for (int c = 0; c < 4; ++c) {
+        std::vector<GemmD<R>> g;
+        for (int q = 0; q < nn; ++q)
+          g.push_back(gd<R>(t_[l + 1][4 * q + c].R_, OP_C, Bb[l + 1][4 * q + c], OP_N, Bb[l][q], R(1), R(1)));
+        ops_.gemm(g);
+      }
+    // b_q = ... + sum_{c2 != c} B_{q,c2} z_{c2}  =>  zb_{q2} = sum_{q != q2} B_{q,c2}^* bb_q ; z = V2^* C2  =>  C2b += V2 zb
+    std::vector<Mat<R>> Zb(nn);
+    for (int q = 0; q < nn; ++q) Zb[q] = scr_.mat<R>(std::max(t_[l][q].kv, 1), s);
+    for (int j = 1; j < 4; ++j) {
+      std::vector<GemmD<R>> g;
+      for (int q2 = 0; q2 < nn; ++q2) {
+        const int p = q2 >> 2, c2 = q2 & 3, c = (c2 + j) & 3, q = 4 * p + c;
+        g.push_back(gd<R>(t_[l][q].B[c2], OP_C, Bb[l][q], OP_N, Zb[q2], R(1), j == 1 ? R(0) : R(1)));
+      }
+      ops_.gemm(g);
+    }
+    std::vector<GemmD<R>> gv;
+    for (int q = 0; q < nn; ++q) gv.push_back(gd<R>(t_[l][q].V2, OP_N, Zb[q], OP_N, C2b[q], R(1), R(1)));
+    ops_.gemm(gv);
+  }
+  // ---- root: croot = R^{-1} (P_root^* froot)[0:cols]  =>  frootb = P_root [R^{-*} crootb; 0]
+  Mat<R> frootb = scr_.mat<R>(std::max(root_rows_, 1), s, true);
+  ops_.gemm({gd<R>(Rinv_, OP_C, crootb.block(0, 0, root_cols_, s), OP_N, frootb.block(0, 0, root_cols_, s))});
+  ops_.apply_q_left({Proot_}, {frootb}, false);
+  {
+    std::vector<CopyD<R>> cp;
+    int ro = 0;
+    for (int c = 0; c < 4; ++c) {
+      Node2<R>& a = t_[1][c];
+      cp.push_back({frootb.at(ro, 0), Fb[1][c].at(a.n1, 0), a.rows2, s, frootb.ld, Fb[1][c].ld, OP_N, R(1), R(0)});
+      ro += a.rows2;
+    }
+    ops_.copy(cp);
+  }
+  // ---- bottom-up sweep, backwards: Fb <- P Fb[0:mc], then Fb <- Omega Fb, then hand rows to the children
+  for (int l = 1; l <= L; ++l) {
+    const int nn = (int)t_[l].size();
+    std::vector<QFac<R>> qo, qp;
+    std::vector<Mat<R>> co, cpm;
+    for (int p = 0; p < nn; ++p) {
+      Node2<R>& nd = t_[l][p];
+      qp.push_back(nd.P);
+      cpm.push_back(Fb[l][p].block(0, 0, nd.mc, s));
+      if (nd.omega) { qo.push_back(nd.Om); co.push_back(Fb[l][p].block(0, 0, nd.m, s)); }
+    }
+    ops_.apply_q_left(qp, cpm, false);
+    ops_.apply_q_left(qo, co, false);
+    if (l < L) {
+      std::vector<CopyD<R>> cp;
+      for (int p = 0; p < nn; ++p) {
+        int ro = 0;
+        for (int c = 0; c < 4; ++c) {
+          Node2<R>& a = t_[l + 1][4 * p + c];
+          cp.push_back({Fb[l][p].at(ro, 0), Fb[l + 1][4 * p + c].at(a.n1, 0), a.rows2, s, Fb[l][p].ld,
+                        Fb[l + 1][4 * p + c].ld, OP_N, R(1), R(0)});
+          ro += a.rows2;
+        }
+      }
+      ops_.copy(cp);
+    }
+  }
+  {
+    std::vector<CopyD<R>> cp;
+    for (int p = 0; p < (int)t_[L].size(); ++p) {
+      const int r0 = pl_->r0[L][p], m = pl_->m[L][p];
+      cp.push_back({Fb[L][p].p, f2 + r0, m, s, Fb[L][p].ld, ldf, OP_N, R(1), R(0)});
+    }
+    ops_.copy(cp);
+  }
+  scr_.release(mk);
+}
+
 // ------------------------------------------------------------------------------- HSS matvec
 template <typename R> void Hss<R>::matvec(const cplx<R>* x, int ldx, int s, cplx<R>* y, int ldy) {
   const int L = pl_->L;

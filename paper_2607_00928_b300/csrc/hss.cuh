@@ -71,6 +71,8 @@ template <typename R> class Hss {
   void factor();
   // y (N x s, tree column order) = G~_hss^+ f (f: M x s in 2D row order); both device
   void solve(const cplx<R>* f2, int ldf, int s, cplx<R>* ytree, int ldy);
+  // f2 (M x s, 2D order) = (G~_hss^+)^* y (N x s, tree column order): the adjoint of solve()
+  void solve_adj(const cplx<R>* ytree, int ldy, int s, cplx<R>* f2, int ldf);
   // y = G~_hss x (x: N x s tree order, y: M x s 2D order): the HSS matrix-vector product
   void matvec(const cplx<R>* x, int ldx, int s, cplx<R>* y, int ldy);
   int max_rank() const;

@@ -361,4 +361,52 @@ void colnorm2(cudaStream_t st, int m, int n, const double2* x, int ldx, double* 
   NH_LAUNCH_CK();
 }
 
+
+// Derivative weights of the exact map: column k = kx*ny + ky of A is exp(-2 pi i (kx x + ky y)),
+// so d/dx_j A(j,k) = -2 pi i kx A(j,k).  wx(k, q) = -2 pi i kx c(k, q), wy likewise with ky.
+__global__ void k_deriv_weights(int nx, int ny, const double2* __restrict__ c, int ldc, double2* __restrict__ wx,
+                                double2* __restrict__ wy, int ldw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+  if (k >= nx * ny) return;
+  const double2 v = c[(size_t)k + (size_t)q * ldc];
+  const double tx = 6.283185307179586 * (double)(k / ny), ty = 6.283185307179586 * (double)(k % ny);
+  // -i * t * (a + i b) = t * (b - i a)
+  wx[(size_t)k + (size_t)q * ldw] = make_double2(tx * v.y, -tx * v.x);
+  wy[(size_t)k + (size_t)q * ldw] = make_double2(ty * v.y, -ty * v.x);
+}
+void deriv_weights(cudaStream_t st, int nx, int ny, int s, const double2* c, int ldc, double2* wx, double2* wy,
+                   int ldw) {
+  if (s <= 0 || nx * ny <= 0) return;
+  dim3 grid((nx * ny + 255) / 256, s);
+  k_deriv_weights<<<grid, 256, 0, st>>>(nx, ny, c, ldc, wx, wy, ldw);
+  NH_LAUNCH_CK();
+}
+
+// gx_j = sum_q Re[ -conj(lam_jq) Dx_jq + conj(Mx_jq) r_jq ], gy likewise: the point-coordinate
+// gradient of a real loss of the least-squares solution (one thread per point).
+__global__ void k_grad_combine(int M, int s, const double2* __restrict__ lam, int ldl, const double2* __restrict__ dxc,
+                               const double2* __restrict__ dyc, const double2* __restrict__ dxm,
+                               const double2* __restrict__ dym, const double2* __restrict__ r, int lde,
+                               double* __restrict__ gx, double* __restrict__ gy) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  double ax = 0, ay = 0;
+  for (int q = 0; q < s; ++q) {
+    const double2 l = lam[(size_t)j + (size_t)q * ldl];
+    const size_t e = (size_t)j + (size_t)q * lde;
+    const double2 rr = r[e], a = dxc[e], b = dyc[e], u = dxm[e], v = dym[e];
+    // Re(conj(z) w) = z.x w.x + z.y w.y
+    ax += -(l.x * a.x + l.y * a.y) + (u.x * rr.x + u.y * rr.y);
+    ay += -(l.x * b.x + l.y * b.y) + (v.x * rr.x + v.y * rr.y);
+  }
+  gx[j] = ax;
+  gy[j] = ay;
+}
+void grad_combine(cudaStream_t st, int M, int s, const double2* lam, int ldl, const double2* dxc, const double2* dyc,
+                  const double2* dxm, const double2* dym, const double2* r, int lde, double* gx, double* gy) {
+  if (M <= 0) return;
+  k_grad_combine<<<(M + 255) / 256, 256, 0, st>>>(M, s, lam, ldl, dxc, dyc, dxm, dym, r, lde, gx, gy);
+  NH_LAUNCH_CK();
+}
+
 }  // namespace nh

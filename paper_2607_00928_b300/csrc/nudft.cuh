@@ -47,5 +47,11 @@ void convert_scatter(cudaStream_t st, const cplx<RS>* src, int lds, const int* i
 void axpy2(cudaStream_t st, int m, int n, double alpha, const double2* x, int ldx, double2* y, int ldy);
 // per-column sums of |x|^2 (double), out[q]
 void colnorm2(cudaStream_t st, int m, int n, const double2* x, int ldx, double* out);
+// wx(k, q) = -2 pi i kx c(k, q), wy(k, q) = -2 pi i ky c(k, q), k = kx * ny + ky
+void deriv_weights(cudaStream_t st, int nx, int ny, int s, const double2* c, int ldc, double2* wx, double2* wy,
+                   int ldw);
+// gx_j = sum_q Re[-conj(lam) dxc + conj(dxm) r], gy_j likewise (all M x s, ld lde except lam)
+void grad_combine(cudaStream_t st, int M, int s, const double2* lam, int ldl, const double2* dxc, const double2* dyc,
+                  const double2* dxm, const double2* dym, const double2* r, int lde, double* gx, double* gy);
 
 }  // namespace nh

@@ -261,3 +261,73 @@ def test_pin_catches_wrong_dft_normalisation():
     x, _ = jittered_grid(30, 1, -0.4, 0.4, 41)
     G = orc.nudft_1d(x, n) @ orc.dft_matrix(n).conj()      # forgot the 1/n of F^{-1}
     assert np.max(np.abs(np.linalg.norm(G, axis=1) - 1.0)) > 1.0
+
+
+# ---------------------------------------------------------------------------- gradient oracle
+def _grad_case(seed=11, nx=4, ny=3, M=30, s=2):
+    rng = np.random.default_rng(seed)
+    x, y = rng.random(M), rng.random(M)
+    f = rng.standard_normal((M, s)) + 1j * rng.standard_normal((M, s))   # inconsistent: r != 0
+    G = rng.standard_normal((nx * ny, s)) + 1j * rng.standard_normal((nx * ny, s))
+    return x, y, f, G, nx, ny
+
+
+def _loss(x, y, f, G, nx, ny):
+    """L = Re <G, c> with c = A^+ f: its gradient in the torch convention is G itself."""
+    c, _, _ = orc.lstsq(orc.nudft_matrix(x, y, nx, ny), f)
+    return float(np.sum(np.real(np.conj(G) * c)))
+
+
+def test_pinv_adjoint_min_norm():
+    """(A^+)^* g solves A^* lam = g and lies in range(A) (the minimum-norm solution)."""
+    x, y, _, G, nx, ny = _grad_case()
+    A = orc.nudft_matrix(x, y, nx, ny)
+    lam = orc.pinv_adjoint(A, G)
+    assert np.max(np.abs(A.conj().T @ lam - G)) < 1e-12 * np.max(np.abs(G)) * A.shape[0]
+    Q, _ = np.linalg.qr(A)
+    assert np.max(np.abs(lam - Q @ (Q.conj().T @ lam))) < 1e-12 * np.max(np.abs(lam))
+    # against the textbook pseudo-inverse
+    assert np.allclose(lam, np.linalg.pinv(A).conj().T @ G, atol=1e-12 * np.max(np.abs(lam)))
+
+
+def test_grad_points_finite_differences():
+    """dL/dx_j and dL/dy_j of lstsq_grad against central differences of the least-squares map."""
+    x, y, f, G, nx, ny = _grad_case()
+    _, _, gx, gy = orc.lstsq_grad(x, y, nx, ny, f, G)
+    h = 1e-6
+    for j in (0, 7, 29):
+        for arr, g in ((x, gx), (y, gy)):
+            p, m = arr.copy(), arr.copy()
+            p[j] += h
+            m[j] -= h
+            args_p = (p, y) if arr is x else (x, p)
+            args_m = (m, y) if arr is x else (x, m)
+            fd = (_loss(*args_p, f, G, nx, ny) - _loss(*args_m, f, G, nx, ny)) / (2 * h)
+            assert abs(fd - g[j]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_grad_f_finite_differences():
+    """lam = dL/dRe f + i dL/dIm f: the loss is linear in f, so differences are exact."""
+    x, y, f, G, nx, ny = _grad_case(seed=5)
+    _, lam, _, _ = orc.lstsq_grad(x, y, nx, ny, f, G)
+    h = 1e-3
+    for j, q in ((0, 0), (12, 1), (29, 1)):
+        for unit, comp in ((1.0, np.real), (1j, np.imag)):
+            fp, fm = f.copy(), f.copy()
+            fp[j, q] += h * unit
+            fm[j, q] -= h * unit
+            fd = (_loss(x, y, fp, G, nx, ny) - _loss(x, y, fm, G, nx, ny)) / (2 * h)
+            assert abs(fd - comp(lam[j, q])) < 1e-9 * max(1.0, abs(fd))
+
+
+def test_grad_points_consistent_data_drops_mu_term():
+    """With f = A c_true the residual is zero and only the -<lam, (dA) c> term remains."""
+    x, y, _, G, nx, ny = _grad_case(seed=3)
+    rng = np.random.default_rng(4)
+    ct = rng.standard_normal((nx * ny, 2)) + 1j * rng.standard_normal((nx * ny, 2))
+    f = orc.nudft_matrix(x, y, nx, ny) @ ct
+    c, lam, gx, _ = orc.lstsq_grad(x, y, nx, ny, f, G)
+    A = orc.nudft_matrix(x, y, nx, ny)
+    kx = np.repeat(np.arange(nx, dtype=np.float64), ny)
+    gx_first = np.sum(np.real(-np.conj(lam) * ((A * (-2j * np.pi * kx)[None, :]) @ c)), axis=1)
+    assert np.max(np.abs(gx - gx_first)) < 1e-9 * np.max(np.abs(gx))
