@@ -308,9 +308,9 @@ def roofline(kst, w, pk, src):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=os.environ.get("NUDFT_BENCH_WORKLOAD", "mixed_n128"))
+    ap.add_argument("--workload", default=os.environ.get("NUDFT_BENCH_WORKLOAD", "mixed_n256"))
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

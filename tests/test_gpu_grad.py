@@ -118,12 +118,16 @@ def test_autograd_matches_oracle_and_finite_differences(nh):
 def test_grad_config5_scale_properties(nh):
     """n = 128, M = 32768, 16 right-hand sides (the differentiation workload): grad_f solves
     A^* lam = g (checked with the exact adjoint), and the point gradient matches a directional
-    central difference of the GPU map along a random direction."""
+    central difference of the GPU map along a random direction.  The handles run in mixed
+    precision refined to 1e-12 with the FP64 exact applies, so the map and its gradient are the
+    FP64 least-squares ones while each build takes seconds (an FP64 build at this size takes
+    minutes)."""
     w = WORKLOADS["grad_n128"]
     x, y, c_true = make_workload(w)
     ct = complex_normal((w.N, w.nrhs), 55)
     xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    h = nh.NudftHSS(xt, yt, w.nx, w.ny, eps=w.eps, levels=w.levels).factor()
+    opts = dict(eps=1e-6, levels=w.levels, prec="mixed", refine_tol=1e-12, refine_max=30)
+    h = nh.NudftHSS(xt, yt, w.nx, w.ny, **opts).factor()
     f = h.apply(nh.EXACT_FWD, torch.from_numpy(c_true).cuda())
     c = h.solve(f)
     g = 2 * (c - torch.from_numpy(ct).cuda())
@@ -138,8 +142,7 @@ def test_grad_config5_scale_properties(nh):
     def L(sgn):
         # A is 1-periodic in each coordinate, so wrapping back into [0, 1) leaves the map unchanged
         xs, ys = np.mod(x + sgn * step * dx, 1.0), np.mod(y + sgn * step * dy, 1.0)
-        hh = nh.NudftHSS(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(),
-                         w.nx, w.ny, eps=w.eps, levels=w.levels).factor()
+        hh = nh.NudftHSS(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), w.nx, w.ny, **opts).factor()
         cc = hh.solve(f)
         hh.close()
         return float(torch.sum(torch.abs(cc - torch.from_numpy(ct).cuda()) ** 2))
