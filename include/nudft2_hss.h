@@ -135,6 +135,26 @@ nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, cons
                               const void* d_g, int64_t ldg, int nrhs, void* d_gf, int64_t ldgf, double* d_gx,
                               double* d_gy, void* stream);
 
+/* Many independent problems of uneven sizes (each its own point set, grid, tolerance and
+ * precision): build (and, if factor != 0, factor) problem i from d_x[i], d_y[i] (M[i] points),
+ * nx[i] x ny[i] frequencies and opts[i] (opts may be NULL: defaults) into out[i].  The problems
+ * run concurrently, each on its own handle-owned stream, driven by up to `threads` host threads
+ * (<= 0: 8); the kernels of different problems overlap on the GPU.  The paper treats one problem
+ * at a time; this is the batched use of the same offline stage (Sec. 4.1).  out[i] is NULL for a
+ * problem that failed; status[i] (may be NULL) receives each problem's code.  Returns OK or the
+ * first failing problem's code (nudft2_last_error names it).  Synchronises every problem. */
+nudft2_status nudft2_hss_build_batched(int count, const double* const* d_x, const double* const* d_y,
+                                       const int64_t* M, const int* nx, const int* ny, const nudft2_opts* opts,
+                                       int factor, int threads, void* stream, nudft2_hss_t* out,
+                                       nudft2_status* status);
+
+/* nudft2_hss_solve for problem i of a batch: d_c[i] (ld ldc[i]) = solution for d_f[i] (ld ldf[i],
+ * nrhs[i] columns) with handle h[i], the problems solved concurrently as in build_batched.
+ * Distinct entries of h must be distinct handles.  Errors: as nudft2_hss_solve, per problem. */
+nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const void* const* d_f, const int64_t* ldf,
+                                       const int* nrhs, void* const* d_c, const int64_t* ldc, int threads,
+                                       void* stream, nudft2_status* status);
+
 /* Statistics of the handle (ranks, stage times, memory).  Errors: EINVAL (NULL). */
 nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);
 

@@ -1,10 +1,10 @@
 """B300-native direct solver for the 2D type-II inverse NUDFT (HSS face-splitting + URV).
 
 Public API: NudftHSS (build / factor / solve / apply / grad / info), lstsq (differentiable
-solve), psi_eval, and the operator
+solve), build_batched / solve_batched (many uneven problems), psi_eval, and the operator
 constants of include/nudft2_hss.h.  All arithmetic runs in the CUDA library libnudft2_hss.so.
 """
 from .binding import (  # noqa: F401
     EXACT_ADJ, EXACT_FWD, FAST_ADJ, FAST_FWD, FP64, MIXED, PINV, PINV_ADJ, LIB_PATH, NudftError, NudftHSS, lib,
-    exact_apply, la_gemm, la_qr, la_tsvd, lstsq, psi_eval,
+    build_batched, exact_apply, la_gemm, la_qr, la_tsvd, lstsq, psi_eval, solve_batched,
 )

@@ -66,6 +66,11 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_apply.argtypes = [vp, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_hss_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.nudft2_hss_grad.argtypes = [vp, vp, i64, vp, i64, vp, i64, ci, vp, i64, vp, vp, vp]
+    pp = ctypes.POINTER(vp)
+    L.nudft2_hss_build_batched.argtypes = [ci, pp, pp, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                           ctypes.POINTER(Opts), ci, ci, vp, pp, ctypes.POINTER(ci)]
+    L.nudft2_hss_solve_batched.argtypes = [ci, pp, pp, ctypes.POINTER(i64), ctypes.POINTER(ci), pp,
+                                           ctypes.POINTER(i64), ci, vp, ctypes.POINTER(ci)]
     L.nudft2_hss_free.argtypes = [vp]
     L.nudft2_hss_free.restype = None
     L.nudft2_psi_eval.argtypes = [vp, i64, ci, vp, vp]
@@ -79,7 +84,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_hss_grad",
+              "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc"):
         getattr(L, f).restype = ctypes.c_int
@@ -270,6 +275,61 @@ class NudftHSS:
             self.close()
         except Exception:
             pass
+
+
+def _opts(eps=1e-10, levels=0, leaf=64, prec="fp64", refine_tol=1e-8, refine_max=8, profile=False) -> Opts:
+    return Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
+                FLAG_PROFILE if profile else 0)
+
+
+def build_batched(problems, factor: bool = True, threads: int = 8, stream=None):
+    """Build (and factor) many independent problems at once.  problems: list of dicts with x, y
+    (M,), nx, ny and optional NudftHSS options (eps, levels, leaf, prec, refine_tol, refine_max).
+    The problems run concurrently on their own streams.  Returns a list of NudftHSS handles."""
+    n = len(problems)
+    xs = [torch.as_tensor(p["x"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
+    ys = [torch.as_tensor(p["y"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
+    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max")
+    opts = (Opts * n)(*[_opts(**{k: p[k] for k in keys if k in p}) for p in problems])
+    px = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
+    py = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ys])
+    Ms = (ctypes.c_int64 * n)(*[t.numel() for t in xs])
+    nxs = (ctypes.c_int * n)(*[int(p["nx"]) for p in problems])
+    nys = (ctypes.c_int * n)(*[int(p["ny"]) for p in problems])
+    out = (ctypes.c_void_p * n)()
+    st = (ctypes.c_int * n)()
+    code = lib().nudft2_hss_build_batched(n, px, py, Ms, nxs, nys, opts, int(factor), threads, _stream(stream),
+                                          out, st)
+    if code != OK:
+        for hp in out:
+            if hp:
+                lib().nudft2_hss_free(ctypes.c_void_p(hp))
+        _check(code)
+    hs = []
+    for i, p in enumerate(problems):
+        h = NudftHSS.__new__(NudftHSS)
+        h._h = ctypes.c_void_p(out[i])
+        h.x, h.y = xs[i], ys[i]
+        h.M = xs[i].numel()
+        h.nx, h.ny, h.N = int(p["nx"]), int(p["ny"]), int(p["nx"]) * int(p["ny"])
+        h.stream = stream
+        hs.append(h)
+    return hs
+
+
+def solve_batched(handles, fs, threads: int = 8, stream=None):
+    """Solve problem i of a batch for fs[i] ((M_i,) or (M_i, s_i) complex128 CUDA); returns the list of c."""
+    n = len(handles)
+    fcs = [_colmajor(f, h.M) for f, h in zip(fs, handles)]
+    cs = [torch.empty((fc.shape[0], h.N), dtype=torch.complex128, device="cuda") for fc, h in zip(fcs, handles)]
+    hp = (ctypes.c_void_p * n)(*[h._h.value for h in handles])
+    pf = (ctypes.c_void_p * n)(*[fc.data_ptr() for fc in fcs])
+    pc = (ctypes.c_void_p * n)(*[c.data_ptr() for c in cs])
+    ldf = (ctypes.c_int64 * n)(*[h.M for h in handles])
+    ldc = (ctypes.c_int64 * n)(*[h.N for h in handles])
+    nr = (ctypes.c_int * n)(*[fc.shape[0] for fc in fcs])
+    _check(lib().nudft2_hss_solve_batched(n, hp, pf, ldf, nr, pc, ldc, threads, _stream(stream), None))
+    return [c[0] if f.dim() == 1 else c.t() for c, f in zip(cs, fs)]
 
 
 class _Lstsq(torch.autograd.Function):

@@ -1,12 +1,14 @@
 // C-ABI of the solver (include/nudft2_hss.h): argument checking, the exact FP64 apply,
 // the 2D inverse DFT, mixed-precision iterative refinement, and dispatch to Hss<R>.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/nudft2_hss.h"
@@ -335,6 +337,36 @@ static void do_solve_adj(nudft2_hss_s* h, const double2* g, int64_t ldg, int s, 
     h->relres = worst;
   }
   h->scr.release(mk);
+}
+
+// Runs fn(i) for every i < count on up to `threads` host threads (the caller's thread included),
+// each with the caller's device current.  Every problem owns its handle and its stream, so the
+// problems' kernels overlap on the GPU while each thread drives its own problem's host-side steps
+// (rank readbacks, descriptor uploads).  fn must not throw.
+template <typename F> static void run_pool(int count, int threads, F&& fn) {
+  int dev = 0;
+  NH_CK(cudaGetDevice(&dev));
+  const int T = std::max(1, std::min(threads > 0 ? threads : 8, count));
+  std::atomic<int> next{0};
+  auto work = [&] {
+    cudaSetDevice(dev);
+    for (int i = next++; i < count; i = next++) fn(i);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+}
+
+// First failing problem of a batch (status and message), or OK.
+static nudft2_status batch_result(const std::vector<nudft2_status>& st, const std::vector<std::string>& msg) {
+  for (size_t i = 0; i < st.size(); ++i)
+    if (st[i] != NUDFT2_OK) {
+      g_err = "problem " + std::to_string(i) + ": " + msg[i];
+      return st[i];
+    }
+  g_err.clear();
+  return NUDFT2_OK;
 }
 
 // ----------------------------------------------------------------------------- C-ABI
@@ -716,6 +748,57 @@ nudft2_status nudft2_la_gemm(int prec, int opa, int opb, int64_t m, int64_t n, i
       la_gemm<float>(opa, opb, (int)m, (int)n, (int)k, alpha, d_a, (int)lda, stride_a, d_b, (int)ldb, stride_b,
                      beta, d_c, (int)ldc, stride_c, batch, (cudaStream_t)stream);
   });
+}
+
+nudft2_status nudft2_hss_build_batched(int count, const double* const* d_x, const double* const* d_y,
+                                       const int64_t* M, const int* nx, const int* ny, const nudft2_opts* opts,
+                                       int factor, int threads, void* stream, nudft2_hss_t* out,
+                                       nudft2_status* status) {
+  if (count < 1 || !d_x || !d_y || !M || !nx || !ny || !out) {
+    g_err = "build_batched: bad arguments";
+    return NUDFT2_EINVAL;
+  }
+  std::vector<nudft2_status> st((size_t)count, NUDFT2_OK);
+  std::vector<std::string> msg((size_t)count);
+  auto r = guard([&] {
+    run_pool(count, threads, [&](int i) {
+      nudft2_hss_t h = nullptr;
+      nudft2_status s = nudft2_hss_build(d_x[i], d_y[i], M[i], nx[i], ny[i], opts ? &opts[i] : nullptr, stream, &h);
+      if (s == NUDFT2_OK && factor) s = nudft2_hss_factor(h, stream);
+      if (s != NUDFT2_OK) {
+        msg[i] = nudft2_last_error();
+        if (h) nudft2_hss_free(h);
+        h = nullptr;
+      }
+      st[i] = s;
+      out[i] = h;
+    });
+  });
+  if (r != NUDFT2_OK) return r;
+  if (status)
+    for (int i = 0; i < count; ++i) status[i] = st[i];
+  return batch_result(st, msg);
+}
+
+nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const void* const* d_f, const int64_t* ldf,
+                                       const int* nrhs, void* const* d_c, const int64_t* ldc, int threads,
+                                       void* stream, nudft2_status* status) {
+  if (count < 1 || !h || !d_f || !ldf || !nrhs || !d_c || !ldc) {
+    g_err = "solve_batched: bad arguments";
+    return NUDFT2_EINVAL;
+  }
+  std::vector<nudft2_status> st((size_t)count, NUDFT2_OK);
+  std::vector<std::string> msg((size_t)count);
+  auto r = guard([&] {
+    run_pool(count, threads, [&](int i) {
+      st[i] = nudft2_hss_solve(h[i], d_f[i], ldf[i], nrhs[i], d_c[i], ldc[i], stream);
+      if (st[i] != NUDFT2_OK) msg[i] = nudft2_last_error();
+    });
+  });
+  if (r != NUDFT2_OK) return r;
+  if (status)
+    for (int i = 0; i < count; ++i) status[i] = st[i];
+  return batch_result(st, msg);
 }
 
 void nudft2_hss_free(nudft2_hss_t h) {

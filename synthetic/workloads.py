@@ -101,3 +101,27 @@ def make_workload(w: Workload):
     x, y = jittered_grid(w.mx, w.my, w.theta[0], w.theta[1], w.seed)
     c = complex_normal((w.N, w.nrhs), w.seed + 1000)
     return x, y, c
+
+
+BATCH_SIZES = (32, 48, 64, 96, 128, 192, 256)
+
+
+def batched_uneven(count: int = 64, seed: int = 100, sizes=BATCH_SIZES, nrhs: int = 8,
+                   ratio=(1.5, 4.0), theta=(-0.25, 0.35)):
+    """Independent problems of uneven size (the batched workload): problem p draws n_x, n_y
+    uniformly from `sizes` and an oversampling rho ~ U[ratio] from seed + p, then takes a
+    jittered m_x x m_y grid with m_x = ceil(n_x sqrt(rho)), m_y = ceil(n_y sqrt(rho)) (so
+    M ~ rho N >= N) and theta ~ U[theta], plus nrhs iid complex normal coefficient columns.
+    Returns a list of dicts with nx, ny, x, y, c_true (N x nrhs, lexicographic ky + kx*ny)."""
+    out = []
+    for p in range(count):
+        rng = _rng(seed + p)
+        nx = int(rng.choice(sizes))
+        ny = int(rng.choice(sizes))
+        rho = float(rng.uniform(*ratio))
+        mx = int(np.ceil(nx * np.sqrt(rho)))
+        my = int(np.ceil(ny * np.sqrt(rho)))
+        x, y = jittered_grid(mx, my, theta[0], theta[1], seed + p + 10_000)
+        c = complex_normal((nx * ny, nrhs), seed + p + 20_000)
+        out.append({"nx": nx, "ny": ny, "x": x, "y": y, "c_true": c, "rho": rho})
+    return out

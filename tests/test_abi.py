@@ -52,3 +52,14 @@ def test_invalid_arguments_are_rejected_on_the_host(cdll):
                                  ctypes.byref(h)) == EINVAL
     # factor on a NULL handle is an ordering error
     assert cdll.nudft2_hss_factor(None, None) == ESTATE
+
+
+def test_batched_entry_points_reject_bad_arguments_on_the_host(cdll):
+    from paper_2607_00928_b300.binding import EINVAL
+    cdll.nudft2_hss_build_batched.restype = ctypes.c_int
+    cdll.nudft2_hss_solve_batched.restype = ctypes.c_int
+    cdll.nudft2_last_error.restype = ctypes.c_char_p
+    assert cdll.nudft2_hss_build_batched(0, None, None, None, None, None, None, 1, 4, None, None, None) == EINVAL
+    assert b"build_batched" in cdll.nudft2_last_error()
+    assert cdll.nudft2_hss_solve_batched(3, None, None, None, None, None, None, 4, None, None) == EINVAL
+    assert b"solve_batched" in cdll.nudft2_last_error()
