@@ -194,18 +194,34 @@ def run_ours(args, w):
         f = f + torch.from_numpy(noise_like(f.cpu().numpy(), w.noise, w.seed + 7)).to(dev)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(extra=None):
         h = nh.NudftHSS(xt, yt, w.nx, w.ny, eps=eps, levels=w.levels, prec=prec, refine_tol=1e-8, refine_max=10,
                         profile=True)
         h.factor()
         c = h.solve(f)
         inf = h.info()
         inf["kstats"] = h.kstats()
+        if extra is not None:
+            extra(h)
         h.close()
         return c, inf
 
-    for _ in range(args.warmup):
-        c, inf = step()
+    # online solve with one right-hand side, on the last warm-up step's handle (outside the timed region)
+    s1 = {}
+
+    def time_one_rhs(h):
+        f1 = f[:, :1].contiguous()
+        for _ in range(2):              # the first call also captures the one-column sweeps
+            h.solve(f1)
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            h.solve(f1)                 # each call synchronises its stream before returning
+        s1["ms"] = (time.perf_counter() - t0) * 1e3 / reps
+
+    for i in range(args.warmup):
+        c, inf = step(time_one_rhs if i == args.warmup - 1 else None)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -276,6 +292,7 @@ def run_ours(args, w):
                 "config": config_of(w, args),
                 "t_build_ms": t_c, "t_factor_ms": t_f, "t_solve_ms": t_s,
                 "online_solves_per_s": w.nrhs / (t_s / 1e3) if t_s > 0 else None,
+                "online_solves_per_s_one_rhs": (1e3 / s1["ms"]) if s1.get("ms") else None,
                 "rel_err_vs_c_true": rel, "max_rank": infos[-1]["max_rank"],
                 "level_rank": infos[-1]["level_rank"], "refine_iters": infos[-1]["refine_iters"],
                 "refine_relres": infos[-1]["refine_relres"],
