@@ -159,7 +159,9 @@ nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const v
 nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);
 
 /* Per-class kernel statistics recorded since build (needs NUDFT2_FLAG_PROFILE; synchronises
- * the recorded events).  Writes at most max entries to out and their count to *n.
+ * the recorded events).  Writes at most max entries to out and their count to *n.  Classes:
+ * gemm, qr_panel, jacobi, other, qrcp; in MIXED mode the handle's FP64 work (exact applies of the
+ * refinement, DFTs) is listed apart with the suffix "_fp64".
  * Errors: EINVAL (NULL arguments). */
 nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int* n);
 

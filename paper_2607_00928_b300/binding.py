@@ -259,9 +259,9 @@ class NudftHSS:
 
     def kstats(self) -> dict:
         """Per kernel class: device ms, algorithmic flops and bytes, launches (profile=True)."""
-        arr = (KStat * 8)()
+        arr = (KStat * 16)()
         n = ctypes.c_int()
-        _check(lib().nudft2_hss_kstats(self._h, arr, 8, ctypes.byref(n)))
+        _check(lib().nudft2_hss_kstats(self._h, arr, 16, ctypes.byref(n)))
         return {arr[i].name.decode(): {"ms": arr[i].ms, "flops": arr[i].flops, "bytes": arr[i].bytes,
                                        "launches": arr[i].launches} for i in range(n.value)}
 

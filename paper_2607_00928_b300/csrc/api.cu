@@ -680,28 +680,36 @@ nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info) {
 nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int* n) {
   return guard([&] {
     NH_REQUIRE(h && out && n && max >= 0, ST_EINVAL, "kstats: NULL argument");
-    Prof* ps[2] = {&h->ops->prof, h->h64 ? &h->h64->ops().prof : &h->h32->ops().prof};
-    KStat acc[K_NCLASS];
-    for (Prof* p : ps) {
-      p->collect();
+    // The handle's own FP64 operations (exact applies, DFTs) and the HSS operations.  In MIXED
+    // mode the HSS runs in FP32, so the FP64 classes are reported apart, with a "_fp64" suffix:
+    // they run on a different pipe.
+    Prof* ps[2] = {h->h64 ? &h->h64->ops().prof : &h->h32->ops().prof, &h->ops->prof};
+    const bool split = !h->h64;
+    KStat acc[2][K_NCLASS];
+    for (int q = 0; q < 2; ++q) {
+      ps[q]->collect();
+      KStat* a = acc[split ? q : 0];
       for (int c = 0; c < K_NCLASS; ++c) {
-        acc[c].ms += p->stats[c].ms;
-        acc[c].flops += p->stats[c].flops;
-        acc[c].bytes += p->stats[c].bytes;
-        acc[c].launches += p->stats[c].launches;
+        a[c].ms += ps[q]->stats[c].ms;
+        a[c].flops += ps[q]->stats[c].flops;
+        a[c].bytes += ps[q]->stats[c].bytes;
+        a[c].launches += ps[q]->stats[c].launches;
       }
     }
     int k = 0;
-    for (int c = 0; c < K_NCLASS && k < max; ++c) {
-      if (acc[c].launches == 0) continue;
-      std::memset(&out[k], 0, sizeof(out[k]));
-      std::strncpy(out[k].name, kclass_name(c), sizeof(out[k].name) - 1);
-      out[k].ms = acc[c].ms;
-      out[k].flops = acc[c].flops;
-      out[k].bytes = acc[c].bytes;
-      out[k].launches = acc[c].launches;
-      ++k;
-    }
+    for (int q = 0; q < (split ? 2 : 1); ++q)
+      for (int c = 0; c < K_NCLASS && k < max; ++c) {
+        if (acc[q][c].launches == 0) continue;
+        std::memset(&out[k], 0, sizeof(out[k]));
+        std::string name = kclass_name(c);
+        if (q == 1) name += "_fp64";
+        std::strncpy(out[k].name, name.c_str(), sizeof(out[k].name) - 1);
+        out[k].ms = acc[q][c].ms;
+        out[k].flops = acc[q][c].flops;
+        out[k].bytes = acc[q][c].bytes;
+        out[k].launches = acc[q][c].launches;
+        ++k;
+      }
     *n = k;
   });
 }
