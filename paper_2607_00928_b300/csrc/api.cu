@@ -280,6 +280,8 @@ static void la_gemm(int opa, int opb, int m, int n, int k, double alpha, const v
             m, n, k, lda, ldb, ldc, opa, opb, (R)alpha, (R)beta};
   ops.gemm(d);
   NH_CK(cudaStreamSynchronize(st));   // the descriptor staging above lives on this host frame
+  if (sizeof(R) == 4 && gemm_tc_enabled() && gemm_tc_error(true))
+    throw Error(ST_ETIMEOUT, "la_gemm: a bounded wait of the tensor-core GEMM ran out");
 }
 
 // lam (M x s, caller point order) = (G~_hss^+)^* ylex, ylex in lexicographic column order.

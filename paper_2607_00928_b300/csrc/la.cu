@@ -344,8 +344,15 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
     if (prof.on)
       for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
     prof.begin(st_);
-    launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
-    glog.path = "tiles128";
+    bool tc = false;
+    if constexpr (sizeof(R) == 4) tc = gemm_tc_enabled();
+    if (tc) {
+      if constexpr (sizeof(R) == 4) gemm_tc_launch(cls, dd, dp, (int)d.size(), t, st_);
+      glog.path = "tcgen05";
+    } else {
+      launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
+      glog.path = "tiles128";
+    }
     prof.end(st_, K_GEMM, fl, 0);
     count();
     return;

@@ -98,6 +98,15 @@ class Prof {
 void gemm_launch_raw(const GemmD<double>* desc, const int* pre, int np, int tiles, cudaStream_t st);
 int gemm_tiles(const GemmD<double>& g);
 
+// Tensor-core (tcgen05, 3xTF32) complex FP32 GEMM on 128 x 128 tiles, opt-in through the
+// environment (NH_GEMM_TC=1): used in place of the CUDA-core kernel for batches of large FP32
+// products.  cls is the operand-layout class (2 * (opA != N) + (opB != N)); desc / pre as for
+// gemm_launch_raw with 128 x 128 tiles.  gemm_tc_error reads (and optionally clears) the flag set
+// when one of the kernel's bounded waits ran out.
+bool gemm_tc_enabled();
+void gemm_tc_launch(int cls, const GemmD<float>* desc, const int* pre, int np, int tiles, cudaStream_t st);
+int gemm_tc_error(bool reset);
+
 template <typename R> class Ops {
  public:
   explicit Ops(cudaStream_t s, Arena* scratch) : st_(s), ar_(scratch) {}

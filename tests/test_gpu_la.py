@@ -7,6 +7,8 @@
   singular values equal LAPACK's, P^* P = I, and the discarded part of C is below the
   threshold -- the truncation rule of the recompression (Sec. 2.2).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -133,3 +135,27 @@ def test_gemm(nh, m, n, k, ops, dtype):
     scale = 1.5 * torch.sqrt(torch.tensor(float(max(k, 1)))) * 4 + 1
     err = (out - ref).abs().max().item()
     assert err < 20 * u * float(scale) * max(1.0, float(ref.abs().max()))
+
+
+@pytest.mark.skipif(os.environ.get("NH_GEMM_TC") != "1",
+                    reason="tensor-core GEMM path is opt-in (NH_GEMM_TC=1)")
+@pytest.mark.parametrize("m,n,k,batch", [(2048, 2048, 300, 2), (1030, 2100, 517, 4), (4100, 700, 64, 2)])
+@pytest.mark.parametrize("ops", ["NN", "CN", "NC", "TT"])
+def test_gemm_tensor_cores_3xtf32(nh, m, n, k, batch, ops):
+    """The tcgen05 3xTF32 complex GEMM (large FP32 batches when NH_GEMM_TC=1) against complex128
+    matmul: FP32-level accuracy, ragged tile edges, all layout classes."""
+    opa, opb = ops
+    sa = (m, k) if opa == "N" else (k, m)
+    sb = (k, n) if opb == "N" else (n, k)
+    A = torch.from_numpy(_rand((batch,) + sa, m + k)).to(torch.complex64)
+    B = torch.from_numpy(_rand((batch,) + sb, n + k)).to(torch.complex64)
+    C = torch.from_numpy(_rand((batch, m, n), m * n % 97)).to(torch.complex64)
+
+    def op(X, o):
+        X = X.to(torch.complex128)
+        return X if o == "N" else (X.transpose(1, 2) if o == "T" else X.transpose(1, 2).conj())
+
+    ref = -1.5 * (op(A, opa) @ op(B, opb)) + 0.5 * C.to(torch.complex128)
+    out = nh.la_gemm(A.cuda(), B.cuda(), opa, opb, alpha=-1.5, beta=0.5, C=C.cuda()).cpu().to(torch.complex128)
+    err = (out - ref).abs().max().item()
+    assert err < 20 * 2.0 ** -24 * (1.5 * 4 * np.sqrt(k) + 1) * max(1.0, float(ref.abs().max()))
