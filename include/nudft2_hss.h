@@ -155,6 +155,19 @@ nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const v
                                        const int* nrhs, void* const* d_c, const int64_t* ldc, int threads,
                                        void* stream, nudft2_status* status);
 
+/* plsqr: the direct solver as a preconditioner for LSQR (Sec. 4.1, Sec. 5): LSQR (Paige &
+ * Saunders) on B c = P f with B = P A and P = F^{-1} G~_hss^+ (one URV solve + 2D inverse DFT, no
+ * refinement), B^* = A^* P^* (2D DFT + adjoint URV solve).  A and A^* are the exact FP64 apply of
+ * Eq. 1 (this library has no NUFFT).  d_f: M x nrhs, d_c: N x nrhs, complex128, as for solve.
+ * Each column stops when its estimated ||P f - B c|| / ||P f|| <= tol, or after maxit
+ * iterations.  *iters (may be NULL): iterations of the slowest column; *relres (may be NULL): the
+ * largest ||f - A c|| / ||f|| over the columns (exact apply).  For data in the range of A the
+ * result is the least-squares solution; otherwise it differs from it by O(eps) times the
+ * least-squares residual (left preconditioning).  Synchronises the stream.
+ * Errors: ESTATE (not factored), EINVAL. */
+nudft2_status nudft2_hss_plsqr(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
+                               double tol, int maxit, int* iters, double* relres, void* stream);
+
 /* Statistics of the handle (ranks, stage times, memory).  Errors: EINVAL (NULL). */
 nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);
 

@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_apply.argtypes = [vp, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_hss_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.nudft2_hss_grad.argtypes = [vp, vp, i64, vp, i64, vp, i64, ci, vp, i64, vp, vp, vp]
+    L.nudft2_hss_plsqr.argtypes = [vp, vp, i64, ci, vp, i64, ctypes.c_double, ci, ctypes.POINTER(ci),
+                                   ctypes.POINTER(ctypes.c_double), vp]
     pp = ctypes.POINTER(vp)
     L.nudft2_hss_build_batched.argtypes = [ci, pp, pp, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(ci),
                                            ctypes.POINTER(Opts), ci, ci, vp, pp, ctypes.POINTER(ci)]
@@ -84,7 +86,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched",
+              "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_plsqr",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc"):
         getattr(L, f).restype = ctypes.c_int
@@ -248,6 +250,20 @@ class NudftHSS:
                                      self.M, ctypes.c_void_p(gx.data_ptr() if points else None),
                                      ctypes.c_void_p(gy.data_ptr() if points else None), _stream(self.stream)))
         return (gf[0] if squeeze else gf.t()), gx, gy
+
+    def plsqr(self, f: torch.Tensor, tol: float = 1e-12, maxit: int = 500):
+        """LSQR preconditioned by this factorization (exact FP64 applies of A, A^*): returns
+        (c, iterations, relative residual ||f - A c|| / ||f||)."""
+        squeeze = f.dim() == 1
+        fc = _colmajor(f, self.M)
+        s = fc.shape[0]
+        c = torch.empty((s, self.N), dtype=torch.complex128, device="cuda")
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        _check(lib().nudft2_hss_plsqr(self._h, ctypes.c_void_p(fc.data_ptr()), self.M, s, ctypes.c_void_p(c.data_ptr()),
+                                      self.N, float(tol), int(maxit), ctypes.byref(it), ctypes.byref(rr),
+                                      _stream(self.stream)))
+        return (c[0] if squeeze else c.t()), it.value, rr.value
 
     def info(self) -> dict:
         i = Info()

@@ -341,6 +341,137 @@ static void do_solve_adj(nudft2_hss_s* h, const double2* g, int64_t ldg, int s, 
   h->scr.release(mk);
 }
 
+// The direct solver as a preconditioner (Sec. 4.1): P = F^{-1} G~_hss^+ applied once (no
+// refinement), and its adjoint P^* = G~_hss^{+*} F / N.
+static void precond_apply(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* c, int64_t ldc) {
+  auto mk = h->scr.mark();
+  double2* ylex = h->scr.arr<double2>((size_t)h->N * s);
+  if (h->h64) hss_solve_lex<double>(h, *h->h64, f, ldf, s, ylex);
+  else hss_solve_lex<float>(h, *h->h32, f, ldf, s, ylex);
+  dft2(h, ylex, h->N, s, c, ldc, true);
+  h->scr.release(mk);
+}
+static void precond_adjoint(nudft2_hss_s* h, const double2* g, int64_t ldg, int s, double2* lam, int64_t ldl) {
+  auto mk = h->scr.mark();
+  double2* ylex = h->scr.arr<double2>((size_t)h->N * s);
+  dft2(h, g, ldg, s, ylex, h->N, false, 1.0 / h->N);
+  if (h->h64) hss_solve_adj_lex<double>(h, *h->h64, ylex, s, lam, ldl);
+  else hss_solve_adj_lex<float>(h, *h->h32, ylex, s, lam, ldl);
+  h->scr.release(mk);
+}
+
+// plsqr: LSQR (Paige & Saunders) on the preconditioned system B c = P f with B = P A, N x N and
+// close to the identity; B v = P (A v) and B^* u = A^* (P^* u), A and A^* by the exact FP64 apply.
+// Columns iterate together, each with its own scalars; a column stops when its estimated
+// ||P f - B c|| / ||P f|| drops to tol (or its Lanczos vectors vanish).  Returns the iterations
+// of the slowest column and the largest ||f - A c|| / ||f|| (exact apply) over the columns.
+static void do_plsqr(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* x, int64_t ldx, double tol,
+                     int maxit, int* iters_out, double* relres_out) {
+  const int M = h->M, N = h->N;
+  auto mk = h->scr.mark();
+  double2* u = h->scr.arr<double2>((size_t)N * s);
+  double2* v = h->scr.arr<double2>((size_t)N * s);
+  double2* w = h->scr.arr<double2>((size_t)N * s);
+  double2* tn = h->scr.arr<double2>((size_t)N * s);
+  double2* tm = h->scr.arr<double2>((size_t)M * s);
+  double* dn = h->scr.arr<double>(s);
+  double* ca = h->scr.arr<double>(s);
+  double* cb = h->scr.arr<double>(s);
+  std::vector<double> hn(s), ha(s), hb(s);
+  auto norms = [&](const double2* z, int m) {
+    colnorm2(h->st, m, s, z, m, dn);
+    NH_CK(cudaMemcpyAsync(hn.data(), dn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    NH_CK(cudaStreamSynchronize(h->st));
+    for (int q = 0; q < s; ++q) hn[q] = std::sqrt(hn[q]);
+    return hn;
+  };
+  auto axpby = [&](const double2* xs, int ldxs, double2* y, int ldy, int m) {   // y = ha x + hb y
+    NH_CK(cudaMemcpyAsync(ca, ha.data(), s * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    NH_CK(cudaMemcpyAsync(cb, hb.data(), s * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    axpby_cols(h->st, m, s, ca, xs, ldxs, cb, y, ldy);
+    NH_CK(cudaStreamSynchronize(h->st));   // the host coefficient vectors are reused next
+  };
+  auto applyB = [&](const double2* in, double2* out) {     // out = P (A in)
+    exact_fwd(h, in, N, s, tm, M);
+    precond_apply(h, tm, M, s, out, N);
+  };
+  auto applyBh = [&](const double2* in, double2* out) {    // out = A^* (P^* in)
+    precond_adjoint(h, in, N, s, tm, M);
+    exact_adj(h, tm, M, s, out, N);
+  };
+  std::vector<double> alpha(s), beta(s), rhobar(s), phibar(s), beta1(s);
+  std::vector<char> active(s, 1);
+  // beta1 u = P f ; alpha v = B^* u ; w = v ; x = 0
+  precond_apply(h, f, ldf, s, u, N);
+  beta1 = norms(u, N);
+  for (int q = 0; q < s; ++q) { ha[q] = 0; hb[q] = beta1[q] > 0 ? 1.0 / beta1[q] : 0.0; if (!(beta1[q] > 0)) active[q] = 0; }
+  axpby(nullptr, N, u, N, N);
+  applyBh(u, v);
+  alpha = norms(v, N);
+  for (int q = 0; q < s; ++q) { ha[q] = 0; hb[q] = alpha[q] > 0 ? 1.0 / alpha[q] : 0.0; if (!(alpha[q] > 0)) active[q] = 0; }
+  axpby(nullptr, N, v, N, N);
+  NH_CK(cudaMemcpy2DAsync(w, N * sizeof(double2), v, N * sizeof(double2), N * sizeof(double2), s,
+                          cudaMemcpyDeviceToDevice, h->st));
+  NH_CK(cudaMemset2DAsync(x, ldx * sizeof(double2), 0, N * sizeof(double2), s, h->st));
+  for (int q = 0; q < s; ++q) { phibar[q] = beta1[q]; rhobar[q] = alpha[q]; }
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    bool any = false;
+    for (int q = 0; q < s; ++q) any = any || active[q];
+    if (!any) { --it; break; }
+    // beta u = B v - alpha u
+    applyB(v, tn);
+    for (int q = 0; q < s; ++q) { ha[q] = active[q] ? 1.0 : 0.0; hb[q] = active[q] ? -alpha[q] : 1.0; }
+    axpby(tn, N, u, N, N);
+    beta = norms(u, N);
+    for (int q = 0; q < s; ++q) { ha[q] = 0; hb[q] = (active[q] && beta[q] > 0) ? 1.0 / beta[q] : 1.0; }
+    axpby(nullptr, N, u, N, N);
+    // alpha v = B^* u - beta v
+    applyBh(u, tn);
+    std::vector<double> anew(s);
+    for (int q = 0; q < s; ++q) { ha[q] = active[q] ? 1.0 : 0.0; hb[q] = active[q] ? -beta[q] : 1.0; }
+    axpby(tn, N, v, N, N);
+    anew = norms(v, N);
+    for (int q = 0; q < s; ++q) { ha[q] = 0; hb[q] = (active[q] && anew[q] > 0) ? 1.0 / anew[q] : 1.0; }
+    axpby(nullptr, N, v, N, N);
+    // plane rotation, then x += (phi / rho) w ; w = v - (theta / rho) w
+    std::vector<double> cx(s, 0.0), cw(s, 1.0), ccw(s, 0.0);
+    for (int q = 0; q < s; ++q) {
+      if (!active[q]) continue;
+      const double rho = std::hypot(rhobar[q], beta[q]);
+      const double c = rhobar[q] / rho, sn = beta[q] / rho;
+      const double theta = sn * anew[q];
+      rhobar[q] = -c * anew[q];
+      const double phi = c * phibar[q];
+      phibar[q] = sn * phibar[q];
+      cx[q] = phi / rho;
+      cw[q] = -theta / rho;
+      ccw[q] = 1.0;
+      alpha[q] = anew[q];
+      if (!(phibar[q] > tol * beta1[q]) || !(beta[q] > 0) || !(anew[q] > 0)) active[q] = 0;
+    }
+    for (int q = 0; q < s; ++q) { ha[q] = cx[q]; hb[q] = 1.0; }
+    axpby(w, N, x, (int)ldx, N);
+    for (int q = 0; q < s; ++q) { ha[q] = ccw[q]; hb[q] = ccw[q] > 0 ? cw[q] : 1.0; }
+    axpby(v, N, w, N, N);
+  }
+  *iters_out = std::min(it, maxit);
+  // true residual of the original problem
+  exact_fwd(h, x, ldx, s, tm, M);
+  for (int q = 0; q < s; ++q) { ha[q] = 1.0; hb[q] = -1.0; }
+  NH_CK(cudaMemcpyAsync(ca, ha.data(), s * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  NH_CK(cudaMemcpyAsync(cb, hb.data(), s * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  axpby_cols(h->st, M, s, ca, f, (int)ldf, cb, tm, M);          // tm = f - A x
+  std::vector<double> rn = norms(tm, M);
+  NH_CK(cudaMemcpy2DAsync(tm, M * sizeof(double2), f, ldf * sizeof(double2), M * sizeof(double2), s,
+                          cudaMemcpyDeviceToDevice, h->st));
+  std::vector<double> fn = norms(tm, M);
+  double worst = 0;
+  for (int q = 0; q < s; ++q) worst = std::max(worst, rn[q] / std::max(fn[q], 1e-300));
+  *relres_out = worst;
+  h->scr.release(mk);
+}
+
 // Runs fn(i) for every i < count on up to `threads` host threads (the caller's thread included),
 // each with the caller's device current.  Every problem owns its handle and its stream, so the
 // problems' kernels overlap on the GPU while each thread drives its own problem's host-side steps
@@ -658,6 +789,23 @@ nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, cons
     }
     NH_CK(cudaStreamSynchronize(h->st));
     h->scr.release(mk);
+  });
+}
+
+nudft2_status nudft2_hss_plsqr(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
+                               double tol, int maxit, int* iters, double* relres, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr, ST_ESTATE, "plsqr: no handle");
+    NH_REQUIRE(h->factored, ST_ESTATE, "plsqr before factor");
+    NH_REQUIRE(nrhs >= 1 && d_f && d_c && ldf >= h->M && ldc >= h->N && tol > 0 && maxit >= 1, ST_EINVAL,
+               "plsqr: bad arguments");
+    enter(h, stream);
+    int it = 0;
+    double rr = -1;
+    do_plsqr(h, (const double2*)d_f, ldf, nrhs, (double2*)d_c, ldc, tol, maxit, &it, &rr);
+    NH_CK(cudaStreamSynchronize(h->st));
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
   });
 }
 

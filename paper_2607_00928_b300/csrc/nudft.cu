@@ -409,4 +409,27 @@ void grad_combine(cudaStream_t st, int M, int s, const double2* lam, int ldl, co
   NH_LAUNCH_CK();
 }
 
+
+// y(:, q) = a[q] * x(:, q) + b[q] * y(:, q) (x may be NULL: y = b y), per-column coefficients.
+__global__ void k_axpby_cols(int m, const double* __restrict__ a, const double2* __restrict__ x, int ldx,
+                             const double* __restrict__ b, double2* __restrict__ y, int ldy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+  if (i >= m) return;
+  double2* yp = y + (size_t)i + (size_t)q * ldy;
+  double2 v = make_double2(b[q] * yp->x, b[q] * yp->y);
+  if (x) {
+    const double2 xv = x[(size_t)i + (size_t)q * ldx];
+    v.x += a[q] * xv.x;
+    v.y += a[q] * xv.y;
+  }
+  *yp = v;
+}
+void axpby_cols(cudaStream_t st, int m, int n, const double* a, const double2* x, int ldx, const double* b, double2* y,
+                int ldy) {
+  if (m <= 0 || n <= 0) return;
+  dim3 grid((m + 255) / 256, n);
+  k_axpby_cols<<<grid, 256, 0, st>>>(m, a, x, ldx, b, y, ldy);
+  NH_LAUNCH_CK();
+}
+
 }  // namespace nh

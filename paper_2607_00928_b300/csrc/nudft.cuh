@@ -47,6 +47,9 @@ void convert_scatter(cudaStream_t st, const cplx<RS>* src, int lds, const int* i
 void axpy2(cudaStream_t st, int m, int n, double alpha, const double2* x, int ldx, double2* y, int ldy);
 // per-column sums of |x|^2 (double), out[q]
 void colnorm2(cudaStream_t st, int m, int n, const double2* x, int ldx, double* out);
+// y(:, q) = a[q] x(:, q) + b[q] y(:, q) with device coefficient arrays a, b (x may be NULL)
+void axpby_cols(cudaStream_t st, int m, int n, const double* a, const double2* x, int ldx, const double* b, double2* y,
+                int ldy);
 // wx(k, q) = -2 pi i kx c(k, q), wy(k, q) = -2 pi i ky c(k, q), k = kx * ny + ky
 void deriv_weights(cudaStream_t st, int nx, int ny, int s, const double2* c, int ldc, double2* wx, double2* wy,
                    int ldw);
