@@ -5,6 +5,6 @@ It performs none of the solver's arithmetic, so neither the CUDA path nor the CP
 oracle depends on the other through it.
 """
 from .workloads import (  # noqa: F401
-    BATCH_SIZES, batched_uneven,
+    BATCH_SIZES, batched_uneven, polar_grid, random_grid,
     Workload, WORKLOADS, jittered_grid, uniform_grid, complex_normal, noise_like, make_workload,
 )

@@ -125,3 +125,25 @@ def batched_uneven(count: int = 64, seed: int = 100, sizes=BATCH_SIZES, nrhs: in
         c = complex_normal((nx * ny, nrhs), seed + p + 20_000)
         out.append({"nx": nx, "ny": ny, "x": x, "y": y, "c_true": c, "rho": rho})
     return out
+
+
+def polar_grid(n: int, beta: float = 0.6):
+    """The modified polar grid of the paper's experiments: the centre (1/2, 1/2) and the points
+    x = 1/2 + r_p cos(2 pi t_q), y = 1/2 + r_p sin(2 pi t_q), r_p = (sqrt(2)/2) p / n_r,
+    t_q = q / n_t, p = 1..n_r-1, q = 0..n_t-1, with n_r = n and n_t = ceil(beta n log2 n);
+    points outside [0, 1)^2 are dropped.  Deterministic (no seed)."""
+    nr = n
+    nt = int(np.ceil(beta * n * np.log2(n)))
+    r = (np.sqrt(2.0) / 2.0) * np.arange(1, nr, dtype=np.float64) / nr
+    t = np.arange(nt, dtype=np.float64) / nt
+    R, T = np.meshgrid(r, t, indexing="ij")
+    x = np.concatenate([[0.5], (0.5 + R * np.cos(2 * np.pi * T)).ravel()])
+    y = np.concatenate([[0.5], (0.5 + R * np.sin(2 * np.pi * T)).ravel()])
+    keep = (x >= 0) & (x < 1) & (y >= 0) & (y < 1)
+    return x[keep], y[keep]
+
+
+def random_grid(M: int, seed: int):
+    """M points drawn independently and uniformly from [0, 1)^2 (the paper's random grid)."""
+    rng = _rng(seed)
+    return rng.random(M), rng.random(M)
