@@ -27,23 +27,33 @@ def main() -> None:
     a = ap.parse_args()
     if a.tensor_cores:
         os.environ["NH_GEMM_TC"] = "1"
+    import ctypes
+
     import torch
 
-    from .binding import la_gemm
+    from .binding import FP64, MIXED, _check, _stream, lib
     dt = torch.complex64 if a.prec == "fp32" else torch.complex128
     opa, opb = a.ops
-    sa = (a.m, a.k) if opa == "N" else (a.k, a.m)
-    sb = (a.k, a.n) if opb == "N" else (a.n, a.k)
-    A = torch.randn((a.batch,) + sa, dtype=dt, device="cuda")
-    B = torch.randn((a.batch,) + sb, dtype=dt, device="cuda")
-    la_gemm(A, B, opa, opb)
+    ra, ca = (a.m, a.k) if opa == "N" else (a.k, a.m)     # stored shapes (column major)
+    rb, cb = (a.k, a.n) if opb == "N" else (a.n, a.k)
+    A = torch.randn((a.batch, ca, ra), dtype=dt, device="cuda")   # (batch, cols, rows) = column major
+    B = torch.randn((a.batch, cb, rb), dtype=dt, device="cuda")
+    C = torch.zeros((a.batch, a.n, a.m), dtype=dt, device="cuda")
+    ops = {"N": 0, "T": 1, "C": 2}
+
+    def call():
+        _check(lib().nudft2_la_gemm(FP64 if a.prec == "fp64" else MIXED, ops[opa], ops[opb], a.m, a.n, a.k, 1.0,
+                                    ctypes.c_void_p(A.data_ptr()), ra, ra * ca, ctypes.c_void_p(B.data_ptr()), rb,
+                                    rb * cb, 0.0, ctypes.c_void_p(C.data_ptr()), a.m, a.m * a.n, a.batch, _stream()))
+
+    call()
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     ts = []
     for _ in range(a.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        la_gemm(A, B, opa, opb)
+        call()
         e1.record(st)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
