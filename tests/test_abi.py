@@ -63,3 +63,18 @@ def test_batched_entry_points_reject_bad_arguments_on_the_host(cdll):
     assert b"build_batched" in cdll.nudft2_last_error()
     assert cdll.nudft2_hss_solve_batched(3, None, None, None, None, None, None, 4, None, None) == EINVAL
     assert b"solve_batched" in cdll.nudft2_last_error()
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as C99 on its own (no C++ or torch types leak into it)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "nudft2_hss.h"\nint main(void) { return 0; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
