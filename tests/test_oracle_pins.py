@@ -331,3 +331,37 @@ def test_grad_points_consistent_data_drops_mu_term():
     kx = np.repeat(np.arange(nx, dtype=np.float64), ny)
     gx_first = np.sum(np.real(-np.conj(lam) * ((A * (-2j * np.pi * kx)[None, :]) @ c)), axis=1)
     assert np.max(np.abs(gx - gx_first)) < 1e-9 * np.max(np.abs(gx))
+
+
+# ---------------------------------------------------------------- planted mistakes in the gradient
+def _grad_x_variant(x, y, nx, ny, f, G, mu_sign=1.0, deriv_sign=-1.0):
+    """lstsq_grad's x-gradient with the two signs exposed, to plant plausible slips."""
+    A = orc.nudft_matrix(x, y, nx, ny)
+    c, _, _ = orc.lstsq(A, f)
+    lam = orc.pinv_adjoint(A, G)
+    mu, _, _ = orc.lstsq(A, lam)
+    r = f - A @ c
+    kx = np.repeat(np.arange(nx, dtype=np.float64), ny)
+    Ax = A * (deriv_sign * 2j * np.pi * kx)[None, :]
+    return np.sum(np.real(-np.conj(lam) * (Ax @ c) + mu_sign * np.conj(Ax @ mu) * r), axis=1)
+
+
+def _grad_fd_error(gx_fn):
+    x, y, f, G, nx, ny = _grad_case()
+    gx = gx_fn(x, y, nx, ny, f, G)
+    h, worst = 1e-6, 0.0
+    for j in (0, 7, 29):
+        p, m = x.copy(), x.copy()
+        p[j] += h
+        m[j] -= h
+        fd = (_loss(p, y, f, G, nx, ny) - _loss(m, y, f, G, nx, ny)) / (2 * h)
+        worst = max(worst, abs(fd - gx[j]) / max(1.0, abs(fd)))
+    return worst
+
+
+def test_gradient_pin_accepts_the_oracle_and_catches_planted_slips():
+    assert _grad_fd_error(lambda *a: orc.lstsq_grad(*a)[2]) < 1e-6
+    assert _grad_fd_error(lambda *a: _grad_x_variant(*a)) < 1e-6                     # the variant itself is right
+    assert _grad_fd_error(lambda *a: _grad_x_variant(*a, mu_sign=-1.0)) > 1e-3       # residual term sign
+    assert _grad_fd_error(lambda *a: _grad_x_variant(*a, mu_sign=0.0)) > 1e-3        # residual term dropped
+    assert _grad_fd_error(lambda *a: _grad_x_variant(*a, deriv_sign=1.0)) > 1e-3     # d/dx of exp(+2 pi i ...)
