@@ -9,8 +9,12 @@
   is the identity on the unperturbed square grid (Psi = 1 at coincidence, Sec. 2.4);
 * the face-splitting identity A F^{-1} = (A^x F_x^{-1}) . (A^y F_y^{-1}) (Sec. 3.1).
 
-The mutation tests at the end plant plausible mistakes in copies of oracle routines (sign of
-the exponent, transposed column order, dropped reflector factor) and assert a pin catches each.
+The mutation tests plant plausible mistakes in copies of oracle routines (sign of the
+exponent, transposed column order, dropped reflector factor, DFT normalisation; in the gradient:
+residual-term sign, dropped residual term, derivative sign) and assert a pin catches each.
+
+The gradient oracle (pinv_adjoint, lstsq_grad) is pinned by the minimum-norm property of
+(A^+)^* g and by central differences of the least-squares map in the point coordinates and in f.
 """
 import numpy as np
 import pytest
