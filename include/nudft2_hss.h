@@ -160,10 +160,13 @@ nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const v
  * refinement), B^* = A^* P^* (2D DFT + adjoint URV solve).  A and A^* are the exact FP64 apply of
  * Eq. 1 (this library has no NUFFT).  d_f: M x nrhs, d_c: N x nrhs, complex128, as for solve.
  * Each column stops when its estimated ||P f - B c|| / ||P f|| <= tol, or after maxit
- * iterations.  *iters (may be NULL): iterations of the slowest column; *relres (may be NULL): the
- * largest ||f - A c|| / ||f|| over the columns (exact apply).  For data in the range of A the
- * result is the least-squares solution; otherwise it differs from it by O(eps) times the
- * least-squares residual (left preconditioning).  Synchronises the stream.
+ * iterations.  With a MIXED handle P is applied in FP32, so B is linear only to FP32 level: the
+ * LSQR then runs inside an outer defect correction on the exact FP64 residual r = f - A c
+ * (LSQR on B x = P r to max(tol, 1e-5), c += x), until ||P r|| <= tol ||P f|| per column.
+ * *iters (may be NULL): LSQR iterations of the slowest column, summed over the passes; *relres
+ * (may be NULL): the largest ||f - A c|| / ||f|| over the columns (exact apply).  For data in the
+ * range of A the result is the least-squares solution; otherwise it differs from it by O(eps)
+ * times the least-squares residual (left preconditioning).  Synchronises the stream.
  * Errors: ESTATE (not factored), EINVAL. */
 nudft2_status nudft2_hss_plsqr(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
                                double tol, int maxit, int* iters, double* relres, void* stream);
@@ -225,16 +228,18 @@ nudft2_status nudft2_la_gemm(int prec, int opa, int opb, int64_t m, int64_t n, i
 
 /* Allocation-free variant of the exact forward apply (NUDFT2_EXACT_FWD of nudft2_exact_apply):
  * d_f (M x nrhs, ld ldf >= M) = A d_c (N x nrhs, ld ldc == N, complex128), in FP64.
- * The paper has no counterpart: this entry point exists for callers that cannot allocate device
- * memory while they run -- e.g. code being captured into a CUDA graph (allocation is not
- * capturable), serving loops that reserve all memory up front, or hosts whose own allocator
- * owns the device.  It never calls cudaMalloc/cudaFree or any allocating routine; its workspace
- * is one fixed 64 MiB device array inside the library (held by every GPU that loads it, until
- * exit).  Limit: M*(2*nx + ny)*16 bytes must fit in 64 MiB minus 4 KiB; right-hand sides are
- * processed in chunks that fit.  The first call on a device looks up the array's address with
- * cudaGetSymbolAddress, so make that first call before any stream capture.  All calls share the
- * array: calls that overlap on the GPU race and must be serialised by the caller.
- * Errors: EINVAL (bad sizes, ldc != nx*ny, workspace too small), ECUDA. */
+ * The paper has no counterpart: this entry point exists for callers that must not allocate
+ * device memory while they run -- serving loops that reserve all device memory at start-up,
+ * hosts whose own allocator owns the device, and latency-bound paths that cannot pay for
+ * cudaMalloc (it may synchronise the device).  It never calls cudaMalloc/cudaFree or any
+ * allocating routine; its workspace is one fixed 64 MiB device array inside the library (held
+ * by every GPU that loads it, until exit).  Limit: M*(2*nx + ny)*16 bytes must fit in 64 MiB
+ * minus 4 KiB (larger sizes return EINVAL); right-hand sides are processed in chunks that fit.
+ * The first call on a device looks up the array's address with cudaGetSymbolAddress, so make
+ * that first call before any stream capture.  All calls share the array, which keeps the last
+ * call's contents: calls that overlap on the GPU race and must be serialised by the caller.
+ * The call returns once its work is queued on `stream`; d_f is ready in stream order.
+ * Errors: EINVAL (bad sizes, ldc != nx*ny, M or ldf >= 2^31, workspace too small), ECUDA. */
 nudft2_status nudft2_exact_fwd_noalloc(const double* d_x, const double* d_y, int64_t M, int nx, int ny,
                                        const void* d_c, int64_t ldc, int nrhs, void* d_f, int64_t ldf, void* stream);
 

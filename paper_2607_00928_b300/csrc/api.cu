@@ -360,13 +360,14 @@ static void precond_adjoint(nudft2_hss_s* h, const double2* g, int64_t ldg, int 
   h->scr.release(mk);
 }
 
-// plsqr: LSQR (Paige & Saunders) on the preconditioned system B c = P f with B = P A, N x N and
-// close to the identity; B v = P (A v) and B^* u = A^* (P^* u), A and A^* by the exact FP64 apply.
-// Columns iterate together, each with its own scalars; a column stops when its estimated
-// ||P f - B c|| / ||P f|| drops to tol (or its Lanczos vectors vanish).  Returns the iterations
-// of the slowest column and the largest ||f - A c|| / ||f|| (exact apply) over the columns.
-static void do_plsqr(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* x, int64_t ldx, double tol,
-                     int maxit, int* iters_out, double* relres_out) {
+// LSQR (Paige & Saunders) on the preconditioned system B x = P r with B = P A, N x N and close
+// to the identity; B v = P (A v) and B^* u = A^* (P^* u), A and A^* by the exact FP64 apply.
+// Columns iterate together, each with its own scalars.  A column stops when its estimated
+// ||P r - B x|| drops to tol * ||P r|| (or its Lanczos vectors vanish); a column whose ||P r||
+// is at most skip[q] does not iterate at all (x = 0).  beta1 returns ||P r|| per column; the
+// return value is the iteration count of the slowest column.
+static int lsqr_core(nudft2_hss_s* h, const double2* r, int64_t ldr, int s, double2* x, int64_t ldx, double tol,
+                     int maxit, const std::vector<double>& skip, std::vector<double>& beta1) {
   const int M = h->M, N = h->N;
   auto mk = h->scr.mark();
   double2* u = h->scr.arr<double2>((size_t)N * s);
@@ -399,12 +400,16 @@ static void do_plsqr(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, doub
     precond_adjoint(h, in, N, s, tm, M);
     exact_adj(h, tm, M, s, out, N);
   };
-  std::vector<double> alpha(s), beta(s), rhobar(s), phibar(s), beta1(s);
+  std::vector<double> alpha(s), beta(s), rhobar(s), phibar(s);
   std::vector<char> active(s, 1);
-  // beta1 u = P f ; alpha v = B^* u ; w = v ; x = 0
-  precond_apply(h, f, ldf, s, u, N);
+  // beta1 u = P r ; alpha v = B^* u ; w = v ; x = 0
+  precond_apply(h, r, ldr, s, u, N);
   beta1 = norms(u, N);
-  for (int q = 0; q < s; ++q) { ha[q] = 0; hb[q] = beta1[q] > 0 ? 1.0 / beta1[q] : 0.0; if (!(beta1[q] > 0)) active[q] = 0; }
+  for (int q = 0; q < s; ++q) {
+    if (!(beta1[q] > skip[q])) active[q] = 0;
+    ha[q] = 0;
+    hb[q] = active[q] ? 1.0 / beta1[q] : 0.0;
+  }
   axpby(nullptr, N, u, N, N);
   applyBh(u, v);
   alpha = norms(v, N);
@@ -455,13 +460,65 @@ static void do_plsqr(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, doub
     for (int q = 0; q < s; ++q) { ha[q] = ccw[q]; hb[q] = ccw[q] > 0 ? cw[q] : 1.0; }
     axpby(v, N, w, N, N);
   }
-  *iters_out = std::min(it, maxit);
+  h->scr.release(mk);
+  return std::min(it, maxit);
+}
+
+// plsqr: the direct solver as a preconditioner (Sec. 4.1).  With an FP64 factorization it is one
+// LSQR run on B c = P f.  With a MIXED (FP32) factorization the applications of P and P^* carry FP32
+// rounding, so B = P A is linear and self-consistent only to FP32 level and a single Krylov
+// recursion stalls near u_32 times the conditioning.  There the LSQR runs inside an outer
+// defect correction whose residual is exact FP64: r = f - A c; x = LSQR(B, P r) to a modest
+// tolerance; c += x; repeated until ||P r|| <= tol ||P f|| per column.  Each pass reduces the
+// preconditioned residual by the inner tolerance (or the FP32 floor), so a few passes reach tol.
+// Returns the total LSQR iterations over all passes (slowest column per pass) and the largest
+// ||f - A c|| / ||f|| (exact apply) over the columns.
+static void do_plsqr(nudft2_hss_s* h, const double2* f, int64_t ldf, int s, double2* x, int64_t ldx, double tol,
+                     int maxit, int* iters_out, double* relres_out) {
+  const int M = h->M, N = h->N;
+  auto mk = h->scr.mark();
+  double2* tm = h->scr.arr<double2>((size_t)M * s);
+  double* dn = h->scr.arr<double>(s);
+  std::vector<double> hn(s);
+  auto norms = [&](const double2* z, int m) {
+    colnorm2(h->st, m, s, z, m, dn);
+    NH_CK(cudaMemcpyAsync(hn.data(), dn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    NH_CK(cudaStreamSynchronize(h->st));
+    for (int q = 0; q < s; ++q) hn[q] = std::sqrt(hn[q]);
+    return hn;
+  };
+  std::vector<double> beta1, pf, skip(s, 0.0);
+  int total = 0;
+  if (h->h64) {
+    total = lsqr_core(h, f, ldf, s, x, ldx, tol, maxit, skip, beta1);
+  } else {
+    // outer defect correction with the exact FP64 residual
+    const double tol_in = std::max(tol, 1e-5);
+    double2* r = h->scr.arr<double2>((size_t)M * s);
+    double2* dx = h->scr.arr<double2>((size_t)N * s);
+    NH_CK(cudaMemcpy2DAsync(r, M * sizeof(double2), f, ldf * sizeof(double2), M * sizeof(double2), s,
+                            cudaMemcpyDeviceToDevice, h->st));
+    NH_CK(cudaMemset2DAsync(x, ldx * sizeof(double2), 0, N * sizeof(double2), s, h->st));
+    for (int pass = 0; pass < 20 && total < maxit; ++pass) {
+      total += lsqr_core(h, r, M, s, dx, N, tol_in, maxit - total, skip, beta1);
+      if (pass == 0) {
+        pf = beta1;
+        for (int q = 0; q < s; ++q) skip[q] = tol * pf[q];
+      } else {
+        bool done = true;
+        for (int q = 0; q < s; ++q) done = done && !(beta1[q] > skip[q]);
+        if (done) break;
+      }
+      axpy2(h->st, N, s, 1.0, dx, N, x, (int)ldx);      // c += x (zero for converged columns)
+      exact_fwd(h, x, ldx, s, r, M);                    // r = A c (FP64, Eq. 1)
+      axpy2(h->st, M, s, -1.0, f, (int)ldf, r, M);      // r = A c - f
+      axpy2(h->st, M, s, -2.0, r, M, r, M);             // r = f - A c
+    }
+  }
+  *iters_out = total;
   // true residual of the original problem
   exact_fwd(h, x, ldx, s, tm, M);
-  for (int q = 0; q < s; ++q) { ha[q] = 1.0; hb[q] = -1.0; }
-  NH_CK(cudaMemcpyAsync(ca, ha.data(), s * sizeof(double), cudaMemcpyHostToDevice, h->st));
-  NH_CK(cudaMemcpyAsync(cb, hb.data(), s * sizeof(double), cudaMemcpyHostToDevice, h->st));
-  axpby_cols(h->st, M, s, ca, f, (int)ldf, cb, tm, M);          // tm = f - A x
+  axpy2(h->st, M, s, -1.0, f, (int)ldf, tm, M);         // tm = A x - f
   std::vector<double> rn = norms(tm, M);
   NH_CK(cudaMemcpy2DAsync(tm, M * sizeof(double2), f, ldf * sizeof(double2), M * sizeof(double2), s,
                           cudaMemcpyDeviceToDevice, h->st));

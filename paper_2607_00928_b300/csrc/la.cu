@@ -273,48 +273,8 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
     if (!part[c].empty()) gemm_class(part[c], c);
 }
 
-// Diagnostics (environment NH_GEMM_LOG): one line per batched launch with its shape summary and
-// device time; skipped while the stream is being captured.
-struct GemmLog {
-  bool on = false;
-  cudaStream_t st;
-  cudaEvent_t a = nullptr, b = nullptr;
-  const char* path = "tiles64";
-  int cls = 0, np = 0, mx = 0, nx = 0, kx = 0;
-  double fl = 0;
-  GemmLog(cudaStream_t s) : st(s) {
-    if (!std::getenv("NH_GEMM_LOG")) return;
-    cudaStreamCaptureStatus cs;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-    on = true;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, st);
-  }
-  ~GemmLog() {
-    if (!on) return;
-    cudaEventRecord(b, st);
-    cudaEventSynchronize(b);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, a, b);
-    std::fprintf(stderr, "[gemm] cls=%d path=%s np=%d m=%d n=%d k=%d gflop=%.3f ms=%.4f tflops=%.2f\n", cls, path, np, mx,
-                 nx, kx, fl * 1e-9, ms, fl / std::max(ms, 1e-6f) * 1e-9);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-  }
-};
-
 template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, int cls) {
   constexpr int BM = 16 * GemmCfg<R>::TM, BN = 16 * GemmCfg<R>::TN;
-  GemmLog glog(st_);
-  if (glog.on) {
-    glog.cls = cls;
-    glog.np = (int)d0.size();
-    for (const auto& g : d0) {
-      glog.mx = std::max(glog.mx, g.m); glog.nx = std::max(glog.nx, g.n); glog.kx = std::max(glog.kx, g.k);
-      glog.fl += 8.0 * g.m * g.n * std::max(g.k, 0);
-    }
-  }
   std::vector<GemmD<R>> d;
   d.reserve(d0.size());
   std::vector<int> pre;
@@ -348,10 +308,8 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
     if constexpr (sizeof(R) == 4) tc = gemm_tc_enabled();
     if (tc) {
       if constexpr (sizeof(R) == 4) gemm_tc_launch(cls, dd, dp, (int)d.size(), t, st_);
-      glog.path = "tcgen05";
     } else {
       launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
-      glog.path = "tiles128";
     }
     prof.end(st_, K_GEMM, fl, 0);
     count();
@@ -392,7 +350,6 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
     }
   prof.begin(st_);
   launch_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK>(cls, tiles2, st_, dd, dp, (int)d.size(), dks, dws);
-  if (any_split) glog.path = "splitk";
   if (any_split) {
     std::vector<int> epre;
     int ne = 0;
@@ -1926,7 +1883,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         tall.push_back(Ct[i]);
         ti.push_back(i);
       }
-    if (!tall.empty() && std::getenv("NH_NO_QR_FIRST") == nullptr) {
+    if (!tall.empty()) {
       qr(tall, *ar_);   // factors are not kept: only R0 (zero below the diagonal) is needed
       for (size_t q = 0; q < ti.size(); ++q) Cw[ti[q]].m = Cw[ti[q]].n;
     }
@@ -2063,15 +2020,6 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
   }
   unsigned long long* rows_upd = ar_->template arr<unsigned long long>(1, true);
   const double u = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
-  std::vector<std::vector<cplx<R>>> init_copy;
-  if (std::getenv("NH_DUMP_TSVD")) {
-    NH_CK(cudaStreamSynchronize(st_));
-    for (auto& j : jd) {
-      init_copy.emplace_back((size_t)j.r * j.k);
-      NH_CK(cudaMemcpy2D(init_copy.back().data(), (size_t)j.r * sizeof(cplx<R>), j.X, (size_t)j.ld * sizeof(cplx<R>),
-                         (size_t)j.r * sizeof(cplx<R>), j.k, cudaMemcpyDeviceToHost));
-    }
-  }
   if (!jd.empty()) {
     auto djd = upload(jd);
     std::vector<unsigned> hoff(nm);
@@ -2144,15 +2092,6 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
       prof.end(st_, K_JACOBI, fl, 0);
       NH_CK(cudaMemcpyAsync(hoff.data(), offs, nm * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
       NH_CK(cudaStreamSynchronize(st_));
-      if (std::getenv("NH_DEBUG") && std::atoi(std::getenv("NH_DEBUG")) >= 2) {
-        float w = 0;
-        for (size_t q = 0; q < jd.size(); ++q) {
-          float f;
-          std::memcpy(&f, &hoff[jmap[q]], 4);
-          if (!hdone[jmap[q]]) w = std::max(w, f);
-        }
-        std::fprintf(stderr, "[tsvd] sweep %d max_off %.3e (rmax %d)\n", sweep, w, rmax);
-      }
       bool all = true;
       for (size_t q = 0; q < jd.size(); ++q) {
         const int i = jmap[q];
@@ -2163,34 +2102,6 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
       }
       NH_CK(cudaMemcpyAsync(done, hdone.data(), nm * sizeof(int), cudaMemcpyHostToDevice, st_));
       if (all || sweep == 39) {
-        if (!all && std::getenv("NH_DUMP_TSVD")) {
-          // write the first unconverged matrix (after the sweeps) for offline analysis
-          for (size_t q = 0; q < jd.size(); ++q) {
-            if (hdone[jmap[q]]) continue;
-            const JacD<R>& j = jd[q];
-            std::vector<cplx<R>>& hx = init_copy[q];    // the input of the sweeps
-            FILE* fp = std::fopen(std::getenv("NH_DUMP_TSVD"), "wb");
-            if (fp) {
-              int hdr[3] = {j.r, j.k, (int)sizeof(R)};
-              std::fwrite(hdr, sizeof(int), 3, fp);
-              std::fwrite(hx.data(), sizeof(cplx<R>), hx.size(), fp);
-              std::fclose(fp);
-            }
-            break;
-          }
-        }
-        if (std::getenv("NH_DEBUG")) {
-          int unconv = 0;
-          float worst = 0;
-          for (size_t q = 0; q < jd.size(); ++q) {
-            const int i = jmap[q];
-            float f;
-            std::memcpy(&f, &hoff[i], 4);
-            if (!hdone[i]) { unconv++; worst = std::max(worst, f); }
-          }
-          std::fprintf(stderr, "[tsvd] mats=%zu rmax=%d kmax_blocks=%d sweeps=%d unconverged=%d worst_off=%.3e tol=%.3e\n",
-                       jd.size(), rmax, maxblk, sweep + 1, unconv, worst, (double)tol);
-        }
         break;
       }
     }

@@ -1,15 +1,17 @@
 // Exact forward apply f = A c (Eq. 1) that allocates no device memory.
 //
-// Who needs it: callers that cannot call cudaMalloc while they run -- code that is itself
-// being captured into a CUDA graph (allocation calls are not capturable), serving loops that
-// reserve all device memory up front and forbid allocation on the request path, or hosts whose
-// custom allocator owns the device.  Instead of asking for workspace, this entry point works in
-// one fixed, file-scope device array that every GPU loading the library holds until exit.
+// Who needs it: callers that must not allocate device memory while they run.  A serving loop
+// that reserves all device memory up front at start-up has nothing left for a workspace; a host
+// application whose own allocator owns the device (a framework's caching pool) cannot have a
+// library allocate behind its back; and latency-bound request paths cannot afford cudaMalloc,
+// which may synchronise the device and has no bounded cost.  Instead of asking for workspace,
+// this entry point works in one fixed, file-scope device array that every GPU loading the
+// library holds until exit.
 //
 // Contract: the array is shared by all calls in the process.  Calls that overlap on the GPU
 // (different streams, or several host threads) race on it; serialise them.  Every byte a call
 // reads from the array is written earlier by the same call, so leftovers from the previous call
-// never leak into a result.
+// never leak into a result.  The call returns once its work is queued on the caller's stream.
 #include <cstring>
 #include <mutex>
 
@@ -67,6 +69,7 @@ extern "C" nudft2_status nudft2_exact_fwd_noalloc(const double* d_x, const doubl
                "exact_fwd_noalloc: bad arguments");
     const int64_t N = (int64_t)nx * ny;
     NH_REQUIRE(ldc >= N && ldf >= M, ST_EINVAL, "exact_fwd_noalloc: leading dimension too small");
+    NH_REQUIRE(M < (1LL << 31) && ldf < (1LL << 31), ST_EINVAL, "exact_fwd_noalloc: M and ldf must be below 2^31");
     const size_t tab = (size_t)M * (nx + ny) * sizeof(double2);
     const size_t per_rhs = (size_t)M * nx * sizeof(double2);
     NH_REQUIRE(kHeader + tab + per_rhs <= kNoAllocBytes, ST_EINVAL,
@@ -97,7 +100,6 @@ extern "C" nudft2_status nudft2_exact_fwd_noalloc(const double* d_x, const doubl
       // f_j = sum_kx Ax(j, kx) T(j, kx): the outer sum
       rowdot(st, Ax, (int)M, T, (int)M, (int)M, nx, qs, static_cast<double2*>(d_f) + (size_t)q0 * ldf, (int)ldf);
     }
-    NH_CK(cudaStreamSynchronize(st));
     nudft2_err_tls.clear();
     return NUDFT2_OK;
   } catch (Error& e) {

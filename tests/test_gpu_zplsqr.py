@@ -65,13 +65,7 @@ def test_plsqr_inconsistent_data_and_zero_column(nh):
 def _polar_handle(nh, n, eps, levels):
     from synthetic import polar_grid
     x, y = polar_grid(n)
-    try:
-        h = nh.NudftHSS(torch.from_numpy(x), torch.from_numpy(y), n, n, eps=eps, levels=levels).factor()
-    except nh.NudftError as e:
-        if "ERANK" in str(e) or "fewer rows" in str(e):
-            pytest.xfail("polar grid: a sparse corner leaf has fewer rows than eliminated columns "
-                         "(equal-depth trees; unbalanced product trees are a later extension)")
-        raise
+    h = nh.NudftHSS(torch.from_numpy(x), torch.from_numpy(y), n, n, eps=eps, levels=levels).factor()
     return x, y, h
 
 
