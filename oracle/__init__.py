@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py``; never by the library.  Every function is pinne
 non-GPU tests in tests/test_oracle_pins.py.  Shares no code with the CUDA path.
 """
 from .nudft_oracle import (  # noqa: F401
-    nudft_1d, nudft_matrix, forward, adjoint, householder_qr, apply_qh, apply_q, back_substitute,
+    normal_cg, lstsq_grad_rows, nudft_1d, nudft_matrix, forward, adjoint, householder_qr, apply_qh, apply_q, back_substitute,
     lstsq, cgls, dft_matrix, tilde_1d, tilde_2d, idft2, relres, relerr, forward_substitute_h, pinv_adjoint,
     lstsq_grad,
 )

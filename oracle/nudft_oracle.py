@@ -24,6 +24,9 @@ What it computes, each by its plain definition (Li & Liu, "A superfast direct so
   least-squares solution with respect to f and to the point coordinates (the derivative of
   the normal equations; the paper itself states no gradient).  Pinned by central finite
   differences of ``lstsq`` and by the minimum-norm characterisation of (A^+)^* g.
+* ``normal_cg`` / ``lstsq_grad_rows`` -- the same gradient without the dense matrix (CG on the
+  normal equations with the direct applies), at sampled point indices, for sizes where A does
+  not fit.  Pinned against ``lstsq_grad`` and against a dense solve of the normal equations.
 
 Pins (tests/test_oracle_pins.py) tie every function to something other than itself: the 2D
 FFT on an unperturbed grid, A^*A = N I, brute-force normal equations in extended precision,
@@ -235,10 +238,13 @@ def lstsq_grad(x, y, nx, ny, f, G):
     return c, lam, gx, gy
 
 
-def cgls(x, y, f, nx, ny, tol=1e-13, maxit=500):
+def cgls(x, y, f, nx, ny, tol=1e-13, maxit=500, rtol=None, history=None):
     """CG on the normal equations A^*A c = A^*f with the direct apply (never forms A^*A).
 
-    Stops when ||A^* r|| <= tol * ||A^* f||.  f is (M,) or (M, s); columns are solved together.
+    Stops when ||A^* r|| <= tol * ||A^* f|| (or, when rtol is given, as soon as
+    ||r|| <= rtol * ||f||) for every column.  f is (M,) or (M, s); columns are solved together.
+    history, if a list, receives max over columns of ||r|| / ||f|| after each iteration (r is the
+    recurrence's residual f - A c).
     """
     f = np.asarray(f, dtype=np.complex128)
     squeeze = f.ndim == 1
@@ -251,6 +257,7 @@ def cgls(x, y, f, nx, ny, tol=1e-13, maxit=500):
     p = g.copy()
     gg = np.sum(np.abs(g) ** 2, axis=0)
     g0 = np.sqrt(gg)
+    f0 = np.linalg.norm(F, axis=0)
     it = 0
     for it in range(1, maxit + 1):
         q = forward(x, y, p, nx, ny)
@@ -258,6 +265,11 @@ def cgls(x, y, f, nx, ny, tol=1e-13, maxit=500):
         alpha = np.where(qq > 0, gg / np.where(qq > 0, qq, 1.0), 0.0)
         c += alpha * p
         r -= alpha * q
+        rel = float(np.max(np.linalg.norm(r, axis=0) / np.where(f0 > 0, f0, 1.0)))
+        if history is not None:
+            history.append(rel)
+        if rtol is not None and rel <= rtol:
+            break
         g = adjoint(x, y, r, nx, ny)
         gg_new = np.sum(np.abs(g) ** 2, axis=0)
         if np.all(np.sqrt(gg_new) <= tol * g0):
@@ -267,6 +279,60 @@ def cgls(x, y, f, nx, ny, tol=1e-13, maxit=500):
         p = g + beta * p
         gg = gg_new
     return (c[:, 0] if squeeze else c), it
+
+
+def normal_cg(x, y, b, nx, ny, tol=1e-13, maxit=500):
+    """Solve the normal equations (A^* A) z = b by conjugate gradients with the direct applies
+    (A^* A is Hermitian positive definite for full-column-rank A and is never formed).
+
+    Stops when ||b - A^* A z|| <= tol * ||b|| per column.  b is (N,) or (N, s).  Returns (z, its)."""
+    b = np.asarray(b, dtype=np.complex128)
+    squeeze = b.ndim == 1
+    B = b[:, None] if squeeze else b
+    z = np.zeros_like(B)
+    r = B.copy()
+    p = r.copy()
+    rr = np.sum(np.abs(r) ** 2, axis=0)
+    b0 = np.sqrt(rr)
+    it = 0
+    for it in range(1, maxit + 1):
+        q = adjoint(x, y, forward(x, y, p, nx, ny), nx, ny)
+        pq = np.real(np.sum(np.conj(p) * q, axis=0))
+        alpha = np.where(pq > 0, rr / np.where(pq > 0, pq, 1.0), 0.0)
+        z += alpha * p
+        r -= alpha * q
+        rr_new = np.sum(np.abs(r) ** 2, axis=0)
+        if np.all(np.sqrt(rr_new) <= tol * b0):
+            break
+        p = r + (rr_new / np.where(rr > 0, rr, 1.0)) * p
+        rr = rr_new
+    return (z[:, 0] if squeeze else z), it
+
+
+def lstsq_grad_rows(x, y, nx, ny, f, G, rows, c=None, tol=1e-13):
+    """The gradient of lstsq_grad without the dense matrix, at the point indices `rows`.
+
+    c = A^+ f by cgls (unless given), mu = (A^* A)^{-1} G by normal_cg, lam = A mu (so that
+    lam = (A^+)^* G, the minimum-norm solution of A^* lam = G), r = f - A c, and
+        dL/dx_j = sum_q Re[ -conj(lam_jq) (A_x c)_jq + conj((A_x mu)_jq) r_jq ]
+    with (A_x)_jk = -2 pi i kx A_jk, evaluated only at the rows j in `rows` (row j of each product
+    needs only the point (x_j, y_j)).  Returns (c, lam, gx[rows], gy[rows]); lam has every row."""
+    f = np.asarray(f, dtype=np.complex128).reshape(len(x), -1)
+    G = np.asarray(G, dtype=np.complex128).reshape(nx * ny, -1)
+    if c is None:
+        c, _ = cgls(x, y, f, nx, ny, tol=tol)
+    c = np.asarray(c, dtype=np.complex128).reshape(nx * ny, -1)
+    mu, _ = normal_cg(x, y, G, nx, ny, tol=tol)
+    lam = forward(x, y, mu, nx, ny)
+    xr, yr = x[rows], y[rows]
+    kx = np.repeat(np.arange(nx, dtype=np.float64), ny)[:, None]
+    ky = np.tile(np.arange(ny, dtype=np.float64), nx)[:, None]
+    r = f[rows] - forward(xr, yr, c, nx, ny)
+    gx = np.sum(np.real(-np.conj(lam[rows]) * forward(xr, yr, -1j * TWO_PI * kx * c, nx, ny)
+                        + np.conj(forward(xr, yr, -1j * TWO_PI * kx * mu, nx, ny)) * r), axis=1)
+    gy = np.sum(np.real(-np.conj(lam[rows]) * forward(xr, yr, -1j * TWO_PI * ky * c, nx, ny)
+                        + np.conj(forward(xr, yr, -1j * TWO_PI * ky * mu, nx, ny)) * r), axis=1)
+    return c, lam, gx, gy
 
 
 def dft_matrix(n: int) -> np.ndarray:

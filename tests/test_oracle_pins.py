@@ -369,3 +369,32 @@ def test_gradient_pin_accepts_the_oracle_and_catches_planted_slips():
     assert _grad_fd_error(lambda *a: _grad_x_variant(*a, mu_sign=-1.0)) > 1e-3       # residual term sign
     assert _grad_fd_error(lambda *a: _grad_x_variant(*a, mu_sign=0.0)) > 1e-3        # residual term dropped
     assert _grad_fd_error(lambda *a: _grad_x_variant(*a, deriv_sign=1.0)) > 1e-3     # d/dx of exp(+2 pi i ...)
+
+
+# ---------------------------------------------------------------- matrix-free gradient
+def test_normal_cg_matches_dense_normal_equations():
+    x, y = jittered_grid(24, 12, -0.3, 0.3, 501)
+    nx, ny = 12, 10
+    A = orc.nudft_matrix(x, y, nx, ny)
+    b = complex_normal((nx * ny, 2), 502)
+    z, it = orc.normal_cg(x, y, b, nx, ny, tol=1e-14)
+    ref = np.linalg.solve(A.conj().T @ A, b)
+    assert np.max(np.linalg.norm(z - ref, axis=0) / np.linalg.norm(ref, axis=0)) < 1e-12
+    assert it < 200
+
+
+def test_matrix_free_gradient_matches_dense_gradient():
+    """lstsq_grad_rows (CG, direct applies, sampled rows) against the dense lstsq_grad, which the
+    finite-difference and minimum-norm pins above tie to the definition; inconsistent data, so
+    both terms of the formula count."""
+    w = WORKLOADS["fp64_n16"]
+    x, y, _ = make_workload(w)
+    f = complex_normal((w.M, 2), 503)
+    G = complex_normal((w.N, 2), 504)
+    c_d, lam_d, gx_d, gy_d = orc.lstsq_grad(x, y, w.nx, w.ny, f, G)
+    rows = np.array([0, 7, 100, 255, 511])
+    c_m, lam_m, gx_m, gy_m = orc.lstsq_grad_rows(x, y, w.nx, w.ny, f, G, rows, tol=1e-14)
+    assert np.max(np.abs(c_m - c_d)) < 1e-11 * np.max(np.abs(c_d))
+    assert np.max(np.abs(lam_m - lam_d)) < 1e-11 * np.max(np.abs(lam_d))
+    assert np.max(np.abs(gx_m - gx_d[rows])) < 1e-10 * np.max(np.abs(gx_d))
+    assert np.max(np.abs(gy_m - gy_d[rows])) < 1e-10 * np.max(np.abs(gy_d))
