@@ -1,20 +1,37 @@
 // Complex FP32 GEMM on the 5th-generation tensor cores (tcgen05.mma, kind::tf32) with the
-// 3xTF32 split, for the FP32 generator products of the mixed-precision path.
+// 3xTF32 split, for the FP32 generator products of the mixed-precision path (Sec. 2.2-2.3:
+// F B G^*, P^* B Q, U2 B V2^*, the URV trailing updates).
 //
-// Every FP32 operand x is split as x = hi + lo, hi = tf32(x) (round to nearest), lo = x - hi
-// (exact in FP32); each real product X Y is formed as Xhi Yhi + Xhi Ylo + Xlo Yhi, which keeps
-// FP32-level accuracy.  A complex product needs four real ones:
-//   Cr += Ar Br - Ai Bi,   Ci += Ar Bi + Ai Br,
-// so one 128 x 128 x 8 step of the tile is 12 MMAs (the -Ai Bi ones through the A-negate bit of
-// the instruction descriptor).  The two accumulators live in tensor memory (2 x 128 columns).
+// Every FP32 operand x is split as x = hi + lo, hi = tf32(x), lo = tf32(x - hi) (both rounded to
+// nearest; x - hi is exact in FP32); each real product X Y is formed as
+// Xhi Yhi + Xhi Ylo + Xlo Yhi, which keeps FP32-level accuracy.  A complex product needs four
+// real ones:  Cr += Ar Br - Ai Bi,  Ci += Ar Bi + Ai Br,  so one k = 8 step of a tile is 12 MMAs
+// (the -Ai Bi ones through the A-negate bit of the instruction descriptor).
 //
-// Per CTA (128 threads): one 128 x 128 output tile of one problem.  The k loop stages 16-deep
-// slices of A and B through shared memory (two stages), split into hi/lo planes of real and
-// imaginary parts, in the canonical K-major layout without swizzle (8-row x 16-byte core
-// matrices).  One thread issues the MMAs and commits them to the stage's mbarrier; the stage is
-// refilled once that mbarrier reports the MMAs that read it complete.  Every wait is bounded: a
-// wait that runs out sets g_tc_error, the CTA waits (bounded) for its MMAs in flight, frees its
-// tensor memory and returns without writing C.
+// The tensor core's FP32 accumulation truncates, so an error that grows linearly with k builds
+// up in a long accumulation (measured: about 1.5e-8 k relative).  The k range is therefore cut
+// into chunks of 64: the MMAs of one chunk accumulate in a chunk accumulator in tensor memory,
+// which the epilogue warps then add (FP32, round to nearest) into a running total kept in a
+// second tensor-memory region.  The error is then that of a 64-term tensor-core sum, about 1e-6
+// relative for any k, below the CUDA-core FP32 kernel's.
+//
+// Two passes:
+//  1. pack: op(A) (m x k) and op(B)^T (n x k) are split into four planes (re hi, re lo, im hi,
+//     im lo) and written tile by tile, zero padded, in exactly the shared-memory image the MMA
+//     reads: the canonical K-major layout without swizzle (8-row x 16-byte core matrices).  One
+//     packed block covers 128 rows x 8 k: 4 planes of 128 x 8 x 4 bytes.  The blocks of one row
+//     tile are contiguous along k.  Packing removes every alignment and ragged-edge case from the
+//     main kernel and does the conjugation.
+//  2. gemm: one CTA of six warps per 128 x 128 output tile.  Warp 4 (one lane) streams packed A
+//     and B blocks into a ring of shared-memory stages with cp.async.bulk (TMA bulk copies,
+//     completion counted on the stage's "full" mbarrier); warp 5 (one lane) waits for a full
+//     stage, issues its 12 MMAs and commits them to the stage's "empty" mbarrier, which releases
+//     the stage to the producer, and to the chunk barrier at the end of a chunk.  Warps 0-3 drain
+//     each chunk into the total (tcgen05.ld / tcgen05.st) and release the chunk accumulator to
+//     the MMA warp; after the last chunk they apply alpha, beta and write C.  Every wait is
+//     bounded: a wait that runs out sets g_tc_error and the CTA stops issuing, waits (bounded)
+//     for its copies and MMAs in flight, frees its tensor memory and returns without writing C.
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -24,17 +41,17 @@
 namespace nh {
 
 namespace {
-constexpr int TC_BM = 128, TC_BN = 128, TC_KT = 16, TC_THREADS = 128;
-constexpr int TC_PLANE_A = TC_BM * TC_KT * 4;                       // bytes of one operand plane
-constexpr int TC_PLANE_B = TC_BN * TC_KT * 4;
-constexpr int TC_STAGE = 4 * TC_PLANE_A + 4 * TC_PLANE_B;           // Ar_hi, Ar_lo, Ai_hi, Ai_lo, then B's
-constexpr int TC_SMEM = 2 * TC_STAGE + 1024;                        // two stages + alignment slack
-constexpr uint32_t TC_TMEM_COLS = 2 * TC_BN;                        // Cr, Ci
-constexpr int TC_SBO = (TC_KT / 4) * 128;                           // bytes between 8-row core groups
-constexpr int TC_LBO = 128;                                         // bytes between core matrices along k
-constexpr long long TC_SPIN = 1LL << 22;                            // try_wait attempts per wait
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 8;
+constexpr int TC_KC = 8;                                   // k blocks (of 8) per accumulation chunk
+constexpr int TC_STAGES = 6;
+constexpr int TC_BLK = 4 * 128 * TC_BK * 4;                // 16 KB: one packed 128-row block
+constexpr int TC_STAGE = 2 * TC_BLK;                       // A block + B block
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE + 1024;       // + alignment slack
+constexpr int TC_THREADS = 192;                            // warps 0-3 drain / epilogue, 4 producer, 5 MMA
+constexpr uint32_t TC_TMEM_COLS = 512;                     // chunk Cr, Ci; total Cr, Ci (128 each)
+constexpr long long TC_SPIN = 1LL << 22;                   // try_wait attempts per wait
 
-// kind::tf32 instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = TC_BN.
+// kind::tf32 instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = 128.
 constexpr uint32_t tc_idesc(bool negate_a) {
   return (1u << 4) | (2u << 7) | (2u << 10) | (negate_a ? (1u << 13) : 0u) | ((uint32_t)(TC_BN >> 3) << 17) |
          ((uint32_t)(TC_BM >> 4) << 24);
@@ -43,33 +60,76 @@ constexpr uint32_t tc_idesc(bool negate_a) {
 
 __device__ int g_tc_error;
 
-// problem of tile t: last i with pre[i] <= t (exclusive tile prefix)
-__device__ __forceinline__ int tc_find_prob(const int* pre, int n, int t) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (pre[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
+// ------------------------------------------------------------------------------------- packing
+// P(r, k) = op(X) element: kcontig ? X[k + r*ld] : X[r + k*ld], conjugated when conj.
+struct PackD {
+  const float2* X;
+  unsigned char* out;   // tiles_r * ktiles blocks of 4 * 128 * 8 * 4 bytes
+  int rows, k, ld;
+  int kcontig, conj;
+  int tiles_r, ktiles;
+};
 
-__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of element (r, k) of a rows x TC_KT plane in the canonical no-swizzle K-major layout
-__device__ __forceinline__ uint32_t tc_kmajor(int r, int k) {
-  return (uint32_t)((r >> 3) * TC_SBO + (k >> 2) * TC_LBO + (r & 7) * 16 + (k & 3) * 4);
-}
-
-// shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), descriptor version 1,
-// base offset 0, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
-         (1ull << 46);
+// byte offset of (r, kk) inside one plane of a packed block (no-swizzle K-major core matrices:
+// 8 rows x 16 bytes each; the two core matrices of one 8-row group are adjacent along k)
+__host__ __device__ __forceinline__ uint32_t tc_kmajor(int r, int kk) {
+  return (uint32_t)((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4);
 }
 
 __device__ __forceinline__ void tc_split(float x, uint32_t& hi, uint32_t& lo) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(x - __uint_as_float(hi)));   // x - hi is exact in FP32
+}
+
+// One CTA of 256 threads per packed block; thread (kq, r) writes row r, k quad kq of each plane
+// as one 16-byte store.
+__global__ void __launch_bounds__(256) k_tc_pack(const PackD* __restrict__ ds, const int* __restrict__ pre, int np) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const PackD d = ds[lo];
+  const int b = blockIdx.x - pre[lo];
+  const int tr = b / d.ktiles, tk = b - tr * d.ktiles;
+  constexpr int R = 128;
+  const int r = threadIdx.x % R, kq = threadIdx.x / R;
+  const int gr = tr * R + r;
+  const int gk0 = tk * TC_BK + kq * 4;
+  uint32_t p[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int gk = gk0 + e;
+    float2 v = make_float2(0.f, 0.f);
+    if (gr < d.rows && gk < d.k)
+      v = d.kcontig ? d.X[(size_t)gk + (size_t)gr * d.ld] : d.X[(size_t)gr + (size_t)gk * d.ld];
+    if (d.conj) v.y = -v.y;
+    tc_split(v.x, p[0][e], p[1][e]);
+    tc_split(v.y, p[2][e], p[3][e]);
+  }
+  unsigned char* blk = d.out + (size_t)b * (4 * R * TC_BK * 4);
+  const uint32_t off = tc_kmajor(r, kq * 4);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<uint4*>(blk + q * (R * TC_BK * 4) + off) = make_uint4(p[q][0], p[q][1], p[q][2], p[q][3]);
+}
+
+// ------------------------------------------------------------------------------------- gemm
+struct TcProb {
+  const unsigned char* Ap;   // tiles_m * ktiles packed A blocks
+  const unsigned char* Bp;   // tiles_n * ktiles packed B blocks (128 rows = output columns each)
+  float2* C;
+  int m, n, ldc, ktiles, tiles_m;
+  float alpha, beta;
+};
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, LBO = 128 B (next core matrix along k),
+// SBO = 256 B (next 8-row group), descriptor version 1, base offset 0, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         (1ull << 46);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -82,6 +142,19 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem_u32(bar))
                : "memory");
+}
+
+__device__ __forceinline__ void tc_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc_smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(tc_smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
@@ -107,19 +180,36 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "r"(taddr));
 }
 
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc3(const GemmD<float>* __restrict__ ds,
-                                                           const int* __restrict__ pre, int np) {
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const TcProb* __restrict__ ds, const int* __restrict__ pre, int np) {
+  constexpr int S = TC_STAGES;
   extern __shared__ unsigned char tc_raw[];
-  __shared__ uint64_t bar[3];          // two stage barriers and the final one
+  __shared__ uint64_t full[S], empty[S], chunk_full, chunk_free, mma_done;
   __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
   const uint32_t raw_s = tc_smem_u32(tc_raw);
   unsigned char* sm = tc_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
-  const int pi = tc_find_prob(pre, np, blockIdx.x);
-  const GemmD<float> g = ds[pi];
-  const int lt = blockIdx.x - pre[pi];
-  const int tiles_m = (g.m + TC_BM - 1) / TC_BM;
-  const int row0 = (lt % tiles_m) * TC_BM, col0 = (lt / tiles_m) * TC_BN;
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const TcProb g = ds[lo];
+  const int lt = blockIdx.x - pre[lo];
+  const int tm = lt % g.tiles_m, tn = lt / g.tiles_m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -128,143 +218,199 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc3(const GemmD<float>* 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&bar[i])));
+    for (int i = 0; i < S; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&chunk_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(tc_smem_u32(&chunk_free)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&mma_done)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tslot;
+  const int KT = g.ktiles;
+  const int NCH = (KT + TC_KC - 1) / TC_KC;
+  volatile int* abort_v = &abort_flag;
 
-  const float sa = g.opA == OP_C ? -1.f : 1.f, sb = g.opB == OP_C ? -1.f : 1.f;
-  const int ktiles = (g.k + TC_KT - 1) / TC_KT;
-  const uint32_t id_pos = tc_idesc(false), id_neg = tc_idesc(true);
-  int ok = 1;
-  for (int kt = 0; kt < ktiles; ++kt) {
-    const int s = kt & 1;
-    unsigned char* st = sm + s * TC_STAGE;
-    if (kt >= 2) ok = tc_wait(&bar[s], (uint32_t)(((kt - 2) >> 1) & 1));   // MMAs of tile kt-2 read this stage
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    const int k0 = kt * TC_KT;
-#pragma unroll 4
-    for (int q = 0; q < TC_BM * TC_KT / TC_THREADS; ++q) {
-      const int e = tid + q * TC_THREADS;
-      int i, kk;
-      if (!TA) { i = e % TC_BM; kk = e / TC_BM; } else { kk = e % TC_KT; i = e / TC_KT; }
-      const int gi = row0 + i, gk = k0 + kk;
-      float2 v = make_float2(0.f, 0.f);
-      if (gi < g.m && gk < g.k) v = !TA ? g.A[(size_t)gi + (size_t)gk * g.lda] : g.A[(size_t)gk + (size_t)gi * g.lda];
-      uint32_t rh, rl, ih, il;
-      tc_split(v.x, rh, rl);
-      tc_split(sa * v.y, ih, il);
-      const uint32_t o = tc_kmajor(i, kk);
-      *(uint32_t*)(st + 0 * TC_PLANE_A + o) = rh;
-      *(uint32_t*)(st + 1 * TC_PLANE_A + o) = rl;
-      *(uint32_t*)(st + 2 * TC_PLANE_A + o) = ih;
-      *(uint32_t*)(st + 3 * TC_PLANE_A + o) = il;
-    }
-#pragma unroll 4
-    for (int q = 0; q < TC_BN * TC_KT / TC_THREADS; ++q) {
-      const int e = tid + q * TC_THREADS;
-      int j, kk;
-      if (!TB) { kk = e % TC_KT; j = e / TC_KT; } else { j = e % TC_BN; kk = e / TC_BN; }
-      const int gj = col0 + j, gk = k0 + kk;
-      float2 v = make_float2(0.f, 0.f);
-      if (gj < g.n && gk < g.k) v = !TB ? g.B[(size_t)gk + (size_t)gj * g.ldb] : g.B[(size_t)gj + (size_t)gk * g.ldb];
-      uint32_t rh, rl, ih, il;
-      tc_split(v.x, rh, rl);
-      tc_split(sb * v.y, ih, il);
-      const uint32_t o = tc_kmajor(j, kk);
-      unsigned char* b0 = st + 4 * TC_PLANE_A;
-      *(uint32_t*)(b0 + 0 * TC_PLANE_B + o) = rh;
-      *(uint32_t*)(b0 + 1 * TC_PLANE_B + o) = rl;
-      *(uint32_t*)(b0 + 2 * TC_PLANE_B + o) = ih;
-      *(uint32_t*)(b0 + 3 * TC_PLANE_B + o) = il;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy stores -> tensor core
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = tc_smem_u32(st), b0 = a0 + 4 * TC_PLANE_A;
-      const uint32_t cr = tmem, ci = tmem + TC_BN;
-#pragma unroll
-      for (int ks = 0; ks < TC_KT / 8; ++ks) {
-        const uint32_t ko = (uint32_t)ks * 2 * TC_LBO;                 // 8 k = two core matrices
-        const uint64_t arh = tc_desc(a0 + 0 * TC_PLANE_A + ko), arl = tc_desc(a0 + 1 * TC_PLANE_A + ko);
-        const uint64_t aih = tc_desc(a0 + 2 * TC_PLANE_A + ko), ail = tc_desc(a0 + 3 * TC_PLANE_A + ko);
-        const uint64_t brh = tc_desc(b0 + 0 * TC_PLANE_B + ko), brl = tc_desc(b0 + 1 * TC_PLANE_B + ko);
-        const uint64_t bih = tc_desc(b0 + 2 * TC_PLANE_B + ko), bil = tc_desc(b0 + 3 * TC_PLANE_B + ko);
-        const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
-        tc_mma(cr, arh, brh, id_pos, first);
-        tc_mma(cr, arh, brl, id_pos, 1u);
-        tc_mma(cr, arl, brh, id_pos, 1u);
-        tc_mma(cr, aih, bih, id_neg, 1u);
-        tc_mma(cr, aih, bil, id_neg, 1u);
-        tc_mma(cr, ail, bih, id_neg, 1u);
-        tc_mma(ci, arh, bih, id_pos, first);
-        tc_mma(ci, arh, bil, id_pos, 1u);
-        tc_mma(ci, arl, bih, id_pos, 1u);
-        tc_mma(ci, aih, brh, id_pos, 1u);
-        tc_mma(ci, aih, brl, id_pos, 1u);
-        tc_mma(ci, ail, brh, id_pos, 1u);
+  if (warp == 4) {
+    if (lane == 0) {
+      // producer: packed A block (tm, kt) and B block (tn, kt) into stage kt % S
+      const unsigned char* a0 = g.Ap + (size_t)tm * KT * TC_BLK;
+      const unsigned char* b0 = g.Bp + (size_t)tn * KT * TC_BLK;
+      int issued = 0;
+      for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % S;
+        if (kt >= S && !tc_wait(&empty[s], (uint32_t)(((kt / S) - 1) & 1))) { *abort_v = 1; break; }
+        if (*abort_v) break;
+        unsigned char* st = sm + s * TC_STAGE;
+        tc_expect(&full[s], (uint32_t)TC_STAGE);
+        tc_bulk(st, a0 + (size_t)kt * TC_BLK, TC_BLK, &full[s]);
+        tc_bulk(st + TC_BLK, b0 + (size_t)kt * TC_BLK, TC_BLK, &full[s]);
+        issued = kt + 1;
       }
-      tc_commit(&bar[s]);
+      // every copy issued must have landed before the CTA can exit: wait for the last fill of
+      // each stage (a no-op when the MMA warp already consumed it)
+      for (int kt = (issued > S ? issued - S : 0); kt < issued; ++kt)
+        if (!tc_wait(&full[kt % S], (uint32_t)((kt / S) & 1))) *abort_v = 1;
     }
-  }
-  // every MMA issued so far (none if a wait ran out before the first tile) completes before the
-  // accumulators are read or the tensor memory is freed
-  if (tid == 0) tc_commit(&bar[2]);
-  const int fin = __syncthreads_and(tc_wait(&bar[2], 0u));
-  if (!ok || !fin) {
-    if (tid == 0) atomicExch(&g_tc_error, 1);
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // MMA issuer: chunk accumulator in columns [0, 256) (Cr, Ci)
+      const uint32_t idp = tc_idesc(false), idn = tc_idesc(true);
+      const uint32_t cr = tmem, ci = tmem + TC_BN;
+      constexpr uint32_t PL = 128 * TC_BK * 4;   // plane bytes
+      for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % S, c = kt / TC_KC, kc = kt - c * TC_KC;
+        if (kc == 0 && c > 0 && !tc_wait(&chunk_free, (uint32_t)((c - 1) & 1))) { *abort_v = 1; break; }
+        if (!tc_wait(&full[s], (uint32_t)((kt / S) & 1))) { *abort_v = 1; break; }
+        if (*abort_v) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a = tc_smem_u32(sm + s * TC_STAGE), b = a + TC_BLK;
+        const uint64_t arh = tc_desc(a), arl = tc_desc(a + PL), aih = tc_desc(a + 2 * PL), ail = tc_desc(a + 3 * PL);
+        const uint64_t brh = tc_desc(b), brl = tc_desc(b + PL), bih = tc_desc(b + 2 * PL), bil = tc_desc(b + 3 * PL);
+        const uint32_t f = kc == 0 ? 0u : 1u;
+        tc_mma(cr, arh, brh, idp, f);
+        tc_mma(cr, arh, brl, idp, 1u);
+        tc_mma(cr, arl, brh, idp, 1u);
+        tc_mma(cr, aih, bih, idn, 1u);
+        tc_mma(cr, aih, bil, idn, 1u);
+        tc_mma(cr, ail, bih, idn, 1u);
+        tc_mma(ci, arh, bih, idp, f);
+        tc_mma(ci, arh, bil, idp, 1u);
+        tc_mma(ci, arl, bih, idp, 1u);
+        tc_mma(ci, aih, brh, idp, 1u);
+        tc_mma(ci, aih, brl, idp, 1u);
+        tc_mma(ci, ail, brh, idp, 1u);
+        tc_commit(&empty[s]);                                   // the stage is free once these MMAs read it
+        if (kc == TC_KC - 1 || kt == KT - 1) tc_commit(&chunk_full);   // the chunk is complete
+      }
+      tc_commit(&mma_done);                                     // every MMA issued above is complete
+    }
   } else {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int r = row0 + warp * 32 + lane;
+    // warps 0-3: lane t of warp w owns row 32 w + t of the tile (tensor-memory lane 32 w + t)
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < TC_BN; c0 += 16) {
-      uint32_t vr[16], vi[16];
-      tc_ld16(lane_addr + (uint32_t)c0, vr);
-      tc_ld16(lane_addr + (uint32_t)(TC_BN + c0), vi);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (r < g.m) {
+    const uint32_t tot = lane_addr + 2 * TC_BN;                 // running total: columns [256, 512)
+    for (int c = 0; c + 1 < NCH; ++c) {
+      bool ok = tc_wait(&chunk_full, (uint32_t)(c & 1));
+      if (!ok || *abort_v) { *abort_v = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int c0 = 0; c0 < 2 * TC_BN; c0 += 16) {
+        uint32_t v[16], t[16];
+        tc_ld16(lane_addr + (uint32_t)c0, v);
+        if (c > 0) tc_ld16(tot + (uint32_t)c0, t);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c > 0) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = col0 + c0 + j;
-          if (c >= g.n) break;
-          float2* cp = g.C + (size_t)r + (size_t)c * g.ldc;
-          const float2 acc = ktiles > 0 ? make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]))
-                                        : make_float2(0.f, 0.f);
-          float2 v = g.alpha * acc;
-          if (g.beta != 0.f) v = v + g.beta * (*cp);
-          *cp = v;
+          for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(t[j]));
+        }
+        tc_st16(tot + (uint32_t)c0, v);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      tc_arrive(&chunk_free);
+    }
+    // last chunk (or none): total + chunk, alpha, beta, store C
+    bool ok = true;
+    if (NCH > 0) ok = tc_wait(&chunk_full, (uint32_t)((NCH - 1) & 1));
+    if (!ok) *abort_v = 1;
+    ok = ok && !*abort_v;
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int r = tm * TC_BM + warp * 32 + lane;
+      const int col0 = tn * TC_BN;
+      for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+        if (col0 + c0 >= g.n) break;
+        uint32_t vr[16], vi[16], tr[16], ti[16];
+        tc_ld16(lane_addr + (uint32_t)c0, vr);
+        tc_ld16(lane_addr + (uint32_t)(TC_BN + c0), vi);
+        if (NCH > 1) {
+          tc_ld16(tot + (uint32_t)c0, tr);
+          tc_ld16(tot + (uint32_t)(TC_BN + c0), ti);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (r < g.m) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int cc = col0 + c0 + j;
+            if (cc >= g.n) break;
+            float2 acc = make_float2(0.f, 0.f);
+            if (NCH > 0) acc = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+            if (NCH > 1) acc = make_float2(acc.x + __uint_as_float(tr[j]), acc.y + __uint_as_float(ti[j]));
+            float2* cp = g.C + (size_t)r + (size_t)cc * g.ldc;
+            float2 v = g.alpha * acc;
+            if (g.beta != 0.f) v = v + g.beta * (*cp);
+            *cp = v;
+          }
         }
       }
     }
   }
+  // MMAs in flight complete before the tensor memory is freed
+  __syncwarp();
+  const bool fin = tc_wait(&mma_done, 0u);
+  const int good = __syncthreads_and(fin && !*abort_v);
+  if (!good && tid == 0) atomicExch(&g_tc_error, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
+// ------------------------------------------------------------------------------------- host
 bool gemm_tc_enabled() {
   const char* e = std::getenv("NH_GEMM_TC");
-  return e && std::strcmp(e, "1") == 0;
+  return !(e && std::strcmp(e, "0") == 0);
 }
 
-void gemm_tc_launch(int cls, const GemmD<float>* dd, const int* dp, int np, int tiles, cudaStream_t st) {
-  if (tiles <= 0) return;
-  auto go = [&](auto kern) {
-    NH_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    kern<<<tiles, TC_THREADS, TC_SMEM, st>>>(dd, dp, np);
-    NH_LAUNCH_CK();
-  };
-  switch (cls) {
-    case 0: go(k_gemm_tc3<false, false>); break;
-    case 1: go(k_gemm_tc3<false, true>); break;
-    case 2: go(k_gemm_tc3<true, false>); break;
-    default: go(k_gemm_tc3<true, true>); break;
+int gemm_tc_run(const std::vector<GemmD<float>>& d, int cls, Arena& ar, cudaStream_t st,
+                void* (*stage)(void*, const void*, size_t), void* ctx) {
+  if (d.empty()) return 0;
+  const bool ta = cls >= 2, tb = (cls & 1) != 0;
+  std::vector<PackD> pk;
+  std::vector<int> prek, pre;
+  std::vector<TcProb> pr;
+  int nk = 0, nt = 0;
+  for (const auto& g : d) {
+    const int kt = (g.k + TC_BK - 1) / TC_BK;
+    const int tmn = (g.m + TC_BM - 1) / TC_BM, tnn = (g.n + TC_BN - 1) / TC_BN;
+    TcProb p;
+    p.C = g.C; p.m = g.m; p.n = g.n; p.ldc = g.ldc; p.ktiles = kt; p.tiles_m = tmn;
+    p.alpha = g.alpha; p.beta = g.beta;
+    p.Ap = p.Bp = nullptr;
+    if (kt > 0) {
+      unsigned char* Ap = (unsigned char*)ar.alloc((size_t)tmn * kt * TC_BLK);
+      unsigned char* Bp = (unsigned char*)ar.alloc((size_t)tnn * kt * TC_BLK);
+      // A: P(r, k) = op(A)(r, k); k is contiguous when op(A) reads A transposed
+      pk.push_back({g.A, Ap, g.m, g.k, g.lda, ta ? 1 : 0, g.opA == OP_C ? 1 : 0, tmn, kt});
+      prek.push_back(nk);
+      nk += tmn * kt;
+      // B: P(r, k) = op(B)(k, r); k is contiguous when op(B) reads B as stored
+      pk.push_back({g.B, Bp, g.n, g.k, g.ldb, tb ? 0 : 1, g.opB == OP_C ? 1 : 0, tnn, kt});
+      prek.push_back(nk);
+      nk += tnn * kt;
+      p.Ap = Ap; p.Bp = Bp;
+    }
+    pr.push_back(p);
+    pre.push_back(nt);
+    nt += tmn * tnn;
   }
+  int launches = 1;
+  if (nk > 0) {
+    auto* dpk = (PackD*)stage(ctx, pk.data(), pk.size() * sizeof(PackD));
+    auto* dpr = (int*)stage(ctx, prek.data(), prek.size() * sizeof(int));
+    k_tc_pack<<<nk, 256, 0, st>>>(dpk, dpr, (int)pk.size());
+    NH_LAUNCH_CK();
+    launches++;
+  }
+  auto* dpb = (TcProb*)stage(ctx, pr.data(), pr.size() * sizeof(TcProb));
+  auto* dpre = (int*)stage(ctx, pre.data(), pre.size() * sizeof(int));
+  NH_CK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  k_gemm_tc<<<nt, TC_THREADS, TC_SMEM, st>>>(dpb, dpre, (int)pr.size());
+  NH_LAUNCH_CK();
+  return launches;
 }
 
 int gemm_tc_error(bool reset) {

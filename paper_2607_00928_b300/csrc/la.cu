@@ -54,7 +54,7 @@ template <typename R> int* Ops<R>::upload_ints(const std::vector<int>& v) {
 
 // =============================================================================== profiling
 const char* kclass_name(int c) {
-  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other", "qrcp"};
+  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other", "qrcp", "sweep", "gemm_tc"};
   return (c >= 0 && c < K_NCLASS) ? n[c] : "?";
 }
 Prof::~Prof() {
@@ -279,7 +279,7 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
   d.reserve(d0.size());
   std::vector<int> pre;
   int tiles = 0, tiles_big = 0;
-  double work = 0, work_big_ok = 0;
+  double work = 0, work_big_ok = 0, work_tc = 0;
   for (const auto& g : d0) {
     d.push_back(g);
     pre.push_back(tiles);
@@ -288,6 +288,9 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
     const double w = (double)g.m * g.n * std::max(g.k, 1);
     work += w;
     if (g.m >= 128 && g.n >= 128) work_big_ok += w;
+    // the tensor-core kernel pays for operand packing and a pipeline fill per tile: it wins on
+    // products with long reductions or large faces (measured: 128^3 products run faster on CUDA cores)
+    if (g.m >= 128 && g.n >= 128 && (g.k >= 256 || std::min(g.m, g.n) >= 256)) work_tc += w;
   }
   if (d.empty()) return;
   // FP32 batches dominated by large products use 128 x 128 tiles (8 x 8 complex per thread)
@@ -298,19 +301,25 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
       preb.push_back(t);
       t += ((g.m + 127) / 128) * ((g.n + 127) / 128);
     }
-    GemmD<R>* dd = upload(d);
-    int* dp = upload_ints(preb);
     double fl = 0;
     if (prof.on)
       for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
-    prof.begin(st_);
-    bool tc = false;
-    if constexpr (sizeof(R) == 4) tc = gemm_tc_enabled();
-    if (tc) {
-      if constexpr (sizeof(R) == 4) gemm_tc_launch(cls, dd, dp, (int)d.size(), t, st_);
-    } else {
-      launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
+    if constexpr (sizeof(R) == 4) {
+      if (gemm_tc_enabled() && work_tc >= 0.8 * work) {
+        // the packed operands live until the GEMM has run; later scratch users on this stream are
+        // ordered after it, so the space is handed back at once
+        auto mk = ar_->mark();
+        prof.begin(st_);
+        count(gemm_tc_run(d, cls, *ar_, st_, &Ops<R>::stage_cb, this));
+        prof.end(st_, K_GEMM_TC, fl, 0);
+        ar_->release(mk);
+        return;
+      }
     }
+    GemmD<R>* dd = upload(d);
+    int* dp = upload_ints(preb);
+    prof.begin(st_);
+    launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
     prof.end(st_, K_GEMM, fl, 0);
     count();
     return;

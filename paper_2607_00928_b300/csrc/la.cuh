@@ -70,7 +70,11 @@ template <typename R> struct QFac {
 
 // Per-kernel-class accounting (CUDA events around each launch on the launching stream),
 // enabled per handle for measurement runs.  flops are the algorithmic counts of the launch.
-enum KClass { K_GEMM = 0, K_QR_PANEL = 1, K_JACOBI = 2, K_OTHER = 3, K_QRCP = 4, K_NCLASS = 5 };
+// K_SWEEP: one whole URV solve (Sec. 2.3 sweeps) replayed from its CUDA graph, with the bytes of
+// the factors it streams.
+// K_GEMM_TC: the tensor-core complex GEMM (operand packing included); K_GEMM: the CUDA-core one.
+enum KClass { K_GEMM = 0, K_QR_PANEL = 1, K_JACOBI = 2, K_OTHER = 3, K_QRCP = 4, K_SWEEP = 5, K_GEMM_TC = 6,
+              K_NCLASS = 7 };
 struct KStat { double ms = 0, flops = 0, bytes = 0; int launches = 0; };
 const char* kclass_name(int c);
 
@@ -98,13 +102,15 @@ class Prof {
 void gemm_launch_raw(const GemmD<double>* desc, const int* pre, int np, int tiles, cudaStream_t st);
 int gemm_tiles(const GemmD<double>& g);
 
-// Tensor-core (tcgen05, 3xTF32) complex FP32 GEMM on 128 x 128 tiles, opt-in through the
-// environment (NH_GEMM_TC=1): used in place of the CUDA-core kernel for batches of large FP32
-// products.  cls is the operand-layout class (2 * (opA != N) + (opB != N)); desc / pre as for
-// gemm_launch_raw with 128 x 128 tiles.  gemm_tc_error reads (and optionally clears) the flag set
-// when one of the kernel's bounded waits ran out.
+// Tensor-core (tcgen05, 3xTF32) complex FP32 GEMM: used in place of the CUDA-core kernel for
+// batches of large FP32 products (on by default; NH_GEMM_TC=0 turns it off).  cls is the
+// operand-layout class (2 * (opA != N) + (opB != N)).  The operands are packed into split TF32
+// planes in scratch memory from `ar`; descriptor arrays are uploaded through `stage(ctx, src,
+// bytes)`.  Returns the number of kernel launches.  gemm_tc_error reads (and optionally clears)
+// the flag set when one of the kernel's bounded waits ran out.
 bool gemm_tc_enabled();
-void gemm_tc_launch(int cls, const GemmD<float>* desc, const int* pre, int np, int tiles, cudaStream_t st);
+int gemm_tc_run(const std::vector<GemmD<float>>& d, int cls, Arena& ar, cudaStream_t st,
+                void* (*stage)(void*, const void*, size_t), void* ctx);
 int gemm_tc_error(bool reset);
 
 template <typename R> class Ops {
@@ -144,6 +150,9 @@ template <typename R> class Ops {
   // Capture mode: host->device descriptor copies are staged in `pool` (kept alive with the graph).
   void set_capture(PinnedPool* pool) { pool_ = pool; }
   int* upload_ints(const std::vector<int>& v);
+  // host -> device copy of bytes into the scratch arena (capture-safe), for launchers outside
+  // this class; ctx is the Ops object
+  static void* stage_cb(void* ctx, const void* src, size_t bytes) { return ((Ops*)ctx)->stage(src, bytes); }
 
  private:
   void gemm_class(const std::vector<GemmD<R>>& d, int cls);   // one operand-layout class

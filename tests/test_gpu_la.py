@@ -137,13 +137,14 @@ def test_gemm(nh, m, n, k, ops, dtype):
     assert err < 20 * u * float(scale) * max(1.0, float(ref.abs().max()))
 
 
-@pytest.mark.skipif(os.environ.get("NH_GEMM_TC") != "1",
-                    reason="tensor-core GEMM path is opt-in (NH_GEMM_TC=1)")
-@pytest.mark.parametrize("m,n,k,batch", [(2048, 2048, 300, 2), (1030, 2100, 517, 4), (4100, 700, 64, 2)])
+@pytest.mark.skipif(os.environ.get("NH_GEMM_TC") == "0", reason="tensor-core GEMM path turned off (NH_GEMM_TC=0)")
+@pytest.mark.parametrize("m,n,k,batch", [(2048, 2048, 300, 2), (1030, 2100, 517, 4), (4100, 700, 64, 2),
+                                         (4096, 300, 100, 10), (2050, 260, 5, 12)])
 @pytest.mark.parametrize("ops", ["NN", "CN", "NC", "TT"])
 def test_gemm_tensor_cores_3xtf32(nh, m, n, k, batch, ops):
-    """The tcgen05 3xTF32 complex GEMM (large FP32 batches when NH_GEMM_TC=1) against complex128
-    matmul: FP32-level accuracy, ragged tile edges, all layout classes."""
+    """The tcgen05 3xTF32 complex GEMM (batches of large FP32 products: m, n >= 128 with k >= 256 or
+    min(m, n) >= 256) against complex128 matmul: FP32-level accuracy, ragged tile edges, k not a
+    multiple of 8 and a single k block, all layout classes."""
     opa, opb = ops
     sa = (m, k) if opa == "N" else (k, m)
     sb = (k, n) if opb == "N" else (n, k)
