@@ -89,12 +89,18 @@ def peaks():
 
 
 # ------------------------------------------------------------------------------------------ oracle arm
+CGLS_COUNTS = os.path.join(ROOT, "oracle", "cgls_iterations.json")
+
+
 def oracle_cgls_sample(w, iters: int = 2):
     """The oracle's CGLS (CG on the normal equations with its direct O(MN) applies of A and A^*)
-    on this very workload, one right-hand side, a bounded number of iterations (about 20-30 s at
-    N = 256^2).  Dense Householder LS is out of reach at these sizes.  Returns (seconds of the
-    timed sample, iterations needed for a 1e-8 relative residual at the contraction measured
-    over the sample, estimated seconds per right-hand side, measured relative residual)."""
+    on this very workload, one right-hand side, timed over a bounded number of iterations (about
+    20-30 s at N = 256^2).  The iteration count to a 1e-8 relative residual is the one measured by
+    running the same CGLS to that stop (oracle/measure_cgls.py, stored in
+    oracle/cgls_iterations.json); without a stored count it is extrapolated from the contraction
+    over the sample.  Dense Householder LS is out of reach at these sizes.  Returns (seconds of the
+    timed sample, iterations for 1e-8, estimated seconds per right-hand side, how the count was
+    obtained)."""
     import math
 
     import oracle as orc
@@ -103,23 +109,25 @@ def oracle_cgls_sample(w, iters: int = 2):
     t0 = time.perf_counter()
     c, _ = orc.cgls(x, y, f, w.nx, w.ny, tol=1e-300, maxit=iters)
     dt = time.perf_counter() - t0
-    r = f - orc.forward(x, y, c, w.nx, w.ny)                      # residual, not timed
-    rel = float(np.linalg.norm(r) / np.linalg.norm(f))
-    if rel <= 0:
-        need = iters
-    else:
-        rho = rel ** (1.0 / iters)
-        need = 500 if rho >= 1 else max(iters, int(math.ceil(math.log(1e-8) / math.log(rho))))
+    try:
+        rec = json.load(open(CGLS_COUNTS))[w.name]
+        need, how = int(rec["iterations"]), f"measured: {rec['iterations']} iterations to {rec['rtol']:g}"
+    except Exception:
+        r = f - orc.forward(x, y, c, w.nx, w.ny)                  # residual, not timed
+        rel = float(np.linalg.norm(r) / np.linalg.norm(f))
+        rho = rel ** (1.0 / iters) if rel > 0 else 0.0
+        need = 500 if rho >= 1 else (iters if rho == 0 else max(iters, int(math.ceil(math.log(1e-8) / math.log(rho)))))
+        how = f"extrapolated from the contraction over the sample: {need} iterations"
     # the sample is one adjoint apply plus `iters` iterations of one forward and one adjoint apply
     per_rhs = dt * (need + 0.5) / (iters + 0.5)
-    return dt, need, per_rhs, rel
+    return dt, need, per_rhs, how
 
 
 def oracle_rate(w):
-    dt, need, per_rhs, rel = oracle_cgls_sample(w)
+    dt, need, per_rhs, how = oracle_cgls_sample(w)
     sample = (f"oracle CGLS with direct O(MN) applies (FP64, numpy) on this workload, 1 RHS: 2 iterations took "
-              f"{dt:.2f} s (relative residual {rel:.2e}); {need} iterations reach 1e-8 at that contraction, "
-              f"i.e. ~{per_rhs:.1f} s per RHS")
+              f"{dt:.2f} s; to a 1e-8 relative residual it takes {need} iterations ({how}), i.e. ~{per_rhs:.1f} s "
+              f"per RHS")
     return 1.0 / per_rhs, per_rhs, sample
 
 
@@ -191,6 +199,8 @@ def run_ours(args, w):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
+    pk, src = peaks()
+    pipes = measured_pipes(nh, pk, src)
     x, y, ct = make_workload(w)
     eps = args.eps if args.eps else (1e-6 if w.mixed else w.eps)
     prec = "mixed" if w.mixed else "fp64"
@@ -283,14 +293,13 @@ def run_ours(args, w):
         rate, _, sample = oracle_rate(w)
         cpu = {"value": rate, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample}
 
-    pk, src = peaks()
     kst = {}
     for i in infos:
         for k, v in i["kstats"].items():
             a = kst.setdefault(k, {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
             for f2 in a:
                 a[f2] += v[f2]
-    roof = roofline(kst, w, pk, src)
+    roof = roofline(kst, w, pipes)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -304,39 +313,83 @@ def run_ours(args, w):
                 "refine_relres": infos[-1]["refine_relres"],
                 "e2e": {"value": world * w.nrhs / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu}
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
+                "peaks": {k: v for k, v in pipes.items()}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def class_peak(name: str, mixed: bool):
-    """(peak TFLOP/s, source) of the pipe a kernel class runs on: FP64 classes (all of them in FP64
-    mode, the "_fp64" ones in mixed mode) on the DFMA pipe, the rest on FP32 FFMA (complex GEMMs,
-    QR and Jacobi all run on CUDA cores)."""
+TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rates of B300
+
+
+def class_pipe(name: str, mixed: bool, pipes: dict):
+    """(bound, peak, unit, source) of the pipe a kernel class runs on.
+
+    gemm_tc: the tcgen05 3xTF32 complex GEMM, against the useful complex-FP32 rate of the TF32
+    tensor pipe (TF32 rate / 3, the TF32 rate taken as the measured BF16 burst rate times the
+    nominal TF32/BF16 ratio).  sweep: one URV solve replayed from its graph, against the measured
+    HBM copy bandwidth.  FP64 classes (all classes of an FP64 run, the "_fp64" ones of a mixed run)
+    against the measured DFMA rate; the other mixed-run classes (CUDA-core GEMM, QR, Jacobi)
+    against the measured FFMA rate."""
+    if name == "sweep" or name == "sweep_fp64":
+        return "hbm", pipes["hbm_gbs"], "GB/s", pipes["hbm_src"]
+    if name == "gemm_tc":
+        return ("tensor", pipes["bf16"] * TF32_OVER_BF16 / 3.0, "TFLOP/s",
+                f"3xTF32 useful rate = bf16 {pipes['bf16']:.0f} TFLOP/s ({pipes['bf16_src']}) x 1.1/2.25 / 3")
     if name.endswith("_fp64") or not mixed:
-        return DFMA_TFLOPS_NOMINAL, "FP64 B300 nominal 1.25 TFLOP/s"
-    return FFMA_TFLOPS_NOMINAL, "FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz"
+        return "alu", pipes["dfma"], "TFLOP/s", pipes["dfma_src"]
+    return "alu", pipes["ffma"], "TFLOP/s", pipes["ffma_src"]
 
 
-def roofline(kst, w, pk, src):
-    """Dominant kernel class (most device time) against its pipe peak, plus every class's rate."""
+def default_pipes(pk=None, src="fallback"):
+    pk = pk or {}
+    return {"hbm_gbs": pk.get("hbm_gbs", 6400.0), "hbm_src": f"HBM copy, {src}",
+            "bf16": pk.get("bf16_tflops", 1800.0), "bf16_src": src,
+            "ffma": FFMA_TFLOPS_NOMINAL, "ffma_src": "FP32 FFMA nominal: 148 SM x 128 lanes x 2 x 2.032 GHz",
+            "dfma": DFMA_TFLOPS_NOMINAL, "dfma_src": "FP64 DFMA nominal 1.25 TFLOP/s"}
+
+
+def measured_pipes(nh, pk, src):
+    """Roofline denominators: HBM and BF16 from the driver's measured peaks file, FFMA and DFMA
+    measured here by the library's FMA probe."""
+    p = default_pipes(pk, src)
+    try:
+        p["ffma"] = nh.peak_fma(nh.MIXED)
+        p["ffma_src"] = "FP32 FFMA measured (nudft2_peak_fma)"
+        p["dfma"] = nh.peak_fma(nh.FP64)
+        p["dfma_src"] = "FP64 DFMA measured (nudft2_peak_fma)"
+    except Exception as e:   # keep the nominal figures, say so
+        p["ffma_src"] += f" (probe failed: {e})"
+    return p
+
+
+def roofline(kst, w, pipes):
+    """Dominant kernel class (most device time) against its pipe's peak, plus every class."""
     if not kst:
         return None
     classes = []
     for name, s in sorted(kst.items(), key=lambda kv: -kv[1]["ms"]):
         if s["ms"] <= 0 or s["launches"] == 0:
             continue
-        peak, psrc = class_peak(name, w.mixed)
-        achieved = s["flops"] / (s["ms"] / 1e3) / 1e12
-        classes.append({"kernel": name, "ms": s["ms"], "achieved": achieved, "peak": peak,
-                        "frac": achieved / peak, "launches": s["launches"], "peak_source": psrc})
+        bound, peak, unit, psrc = class_pipe(name, w.mixed, pipes)
+        sec = s["ms"] / 1e3
+        achieved = (s["bytes"] / sec / 1e9) if bound == "hbm" else (s["flops"] / sec / 1e12)
+        classes.append({"kernel": name, "bound": bound, "ms": s["ms"], "achieved": achieved, "peak": peak,
+                        "unit": unit, "frac": achieved / peak, "launches": s["launches"],
+                        "avg_launch_ms": s["ms"] / s["launches"], "peak_source": psrc})
     if not classes:
         return None
     d = classes[0]
-    return {"kernel": d["kernel"], "bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
-            "frac": d["frac"], "traffic": None, "launches": d["launches"], "avg_launch_ms": d["ms"] / d["launches"],
-            "peak_source": d["peak_source"], "peaks_file": src, "classes": classes}
+    return {"kernel": d["kernel"], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+            "unit": d["unit"], "frac": d["frac"], "traffic": TRAFFIC_PER_LAUNCH.get(d["kernel"]),
+            "launches": d["launches"], "avg_launch_ms": d["avg_launch_ms"], "peak_source": d["peak_source"],
+            "classes": classes}
+
+
+# DRAM bytes (read + write) per launch of a class's kernel from an ncu capture, where one exists for
+# the current kernel (None otherwise).
+TRAFFIC_PER_LAUNCH: dict = {}
 
 
 def main():

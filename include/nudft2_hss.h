@@ -38,7 +38,7 @@ typedef enum {
   NUDFT2_ENOMEM = 2,   /* device allocation failed */
   NUDFT2_ECUDA = 3,    /* CUDA runtime error (message in nudft2_last_error) */
   NUDFT2_ERANK = 4,    /* a URV block is rank deficient (fewer rows than eliminated columns) */
-  NUDFT2_ETIMEOUT = 5, /* reserved: a bounded device wait expired */
+  NUDFT2_ETIMEOUT = 5, /* a bounded device wait (tensor-core GEMM pipeline) expired */
   NUDFT2_ESTATE = 6,   /* call out of order (factor before build, solve before factor) */
   NUDFT2_ENOTIMPL = 7  /* operation not available in this build */
 } nudft2_status;
@@ -50,7 +50,8 @@ typedef enum {
 
 typedef enum {
   NUDFT2_FAST_FWD = 0,  /* out (M x nrhs) = G~_hss F in: the HSS forward map (Sec. 4.1, A_fast)   */
-  NUDFT2_FAST_ADJ = 1,  /* reserved */
+  NUDFT2_FAST_ADJ = 1,  /* out (N x nrhs) = (G~_hss F)^* in = F^* G~_hss^* in: the adjoint of
+                           FAST_FWD (Sec. 4.1), by the transposed HSS product sweeps            */
   NUDFT2_EXACT_FWD = 2, /* out (M x nrhs) = A in, direct O(MN) sum of Eq. 1 in FP64              */
   NUDFT2_EXACT_ADJ = 3, /* out (N x nrhs) = A^* in, direct O(MN) sum in FP64                     */
   NUDFT2_PINV = 4,      /* out (N x nrhs) = F^{-1} G~_hss^+ in (same as nudft2_hss_solve)         */
@@ -108,14 +109,16 @@ nudft2_status nudft2_hss_factor(nudft2_hss_t h, void* stream);
 /* c = F^{-1} G~_hss^+ f (Alg. 1 step 5): URV sweeps then the 2D inverse DFT.
  * d_f: M x nrhs complex128 (ld ldf >= M), point order as given to build.
  * d_c: N x nrhs complex128 (ld ldc >= N), lexicographic ky + kx*ny.
- * MIXED handles refine with the exact FP64 residual (opts.refine_tol / refine_max).
+ * MIXED handles refine with the exact FP64 residual (opts.refine_tol / refine_max): c += the FP32
+ * solve of r = f - A c until ||r|| / ||f|| <= refine_tol, or, after the first step, until the
+ * correction is at most refine_tol ||c|| per column (data with a nonzero least-squares residual).
  * Errors: ESTATE (not factorised), EINVAL (ld too small, nrhs < 0). */
 nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
                                void* stream);
 
-/* Apply one operator of nudft2_op to nrhs columns: EXACT_FWD/EXACT_ADJ need only build;
- * FAST_FWD needs build; PINV and PINV_ADJ need factor.  Shapes as documented on nudft2_op.
- * Errors: EINVAL (op unknown, ld too small), ESTATE, ENOTIMPL (reserved ops). */
+/* Apply one operator of nudft2_op to nrhs columns: EXACT_FWD/EXACT_ADJ, FAST_FWD and FAST_ADJ
+ * need only build; PINV and PINV_ADJ need factor.  Shapes as documented on nudft2_op.
+ * Errors: EINVAL (op unknown, ld too small), ESTATE. */
 nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t ldi, int nrhs, void* d_out,
                                int64_t ldo, void* stream);
 
@@ -129,7 +132,9 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
  *     dL/dx_j = sum_q Re[ -conj(lam_jq) (A_x c)_jq + conj((A_x mu)_jq) r_jq ],
  *   with mu = A^+ lam, r = f - A c, (A_x)_jk = -2 pi i kx A_jk (Golub-Pereyra derivative of a
  *   full-rank least-squares solution; the paper has no gradient).  Products with A are the FP64
- *   exact apply of Eq. 1.  Synchronises the stream.
+ *   exact apply of Eq. 1.  With a MIXED handle mu is the refined solve of lam and the returned
+ *   lam is A mu, which puts it in range(A) (the refined adjoint alone meets A^* lam = g but
+ *   carries an O(eps) part outside range(A)).  Synchronises the stream.
  * Errors: ESTATE (not factored), EINVAL. */
 nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, const void* d_c, int64_t ldc,
                               const void* d_g, int64_t ldg, int nrhs, void* d_gf, int64_t ldgf, double* d_gx,
@@ -176,7 +181,9 @@ nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);
 
 /* Per-class kernel statistics recorded since build (needs NUDFT2_FLAG_PROFILE; synchronises
  * the recorded events).  Writes at most max entries to out and their count to *n.  Classes:
- * gemm, qr_panel, jacobi, other, qrcp; in MIXED mode the handle's FP64 work (exact applies of the
+ * gemm (CUDA cores), gemm_tc (tensor cores, operand packing included), qr_panel, jacobi, other,
+ * qrcp, and sweep (one URV solve replayed from its CUDA graph; bytes = the factor entries it
+ * streams + right-hand sides in and out); in MIXED mode the handle's FP64 work (exact applies of the
  * refinement, DFTs) is listed apart with the suffix "_fp64".
  * Errors: EINVAL (NULL arguments). */
 nudft2_status nudft2_hss_kstats(nudft2_hss_t h, nudft2_kstat* out, int max, int* n);
@@ -242,6 +249,12 @@ nudft2_status nudft2_la_gemm(int prec, int opa, int opb, int64_t m, int64_t n, i
  * Errors: EINVAL (bad sizes, ldc != nx*ny, M or ldf >= 2^31, workspace too small), ECUDA. */
 nudft2_status nudft2_exact_fwd_noalloc(const double* d_x, const double* d_y, int64_t M, int nx, int ny,
                                        const void* d_c, int64_t ldc, int nrhs, void* d_f, int64_t ldf, void* stream);
+
+/* Measured FMA throughput of the current GPU in TFLOP/s (2 flops per FMA), for roofline
+ * denominators: prec = NUDFT2_MIXED measures the FP32 FFMA pipe, NUDFT2_FP64 the DFMA pipe.  Not part
+ * of the paper's method.  Runs a few fixed-length kernels (well under a second) on `stream`, with
+ * a small temporary allocation, and synchronises it.  Errors: EINVAL, ECUDA. */
+nudft2_status nudft2_peak_fma(int prec, double* tflops, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* nudft2_last_error(void);

@@ -84,11 +84,12 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_double, vp, i64, i64, ci, vp]
     L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
+    L.nudft2_peak_fma.argtypes = [ci, ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
               "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_plsqr",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
-              "nudft2_exact_fwd_noalloc"):
+              "nudft2_exact_fwd_noalloc", "nudft2_peak_fma"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -110,6 +111,13 @@ def _colmajor(a: torch.Tensor, rows: int) -> torch.Tensor:
         a = a[:, None]
     assert a.shape[0] == rows, (a.shape, rows)
     return a.to(device="cuda", dtype=torch.complex128).t().contiguous()
+
+
+def peak_fma(prec: int) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP32 FFMA for MIXED, DFMA for FP64)."""
+    v = ctypes.c_double()
+    _check(lib().nudft2_peak_fma(prec, ctypes.byref(v), _stream()))
+    return v.value
 
 
 def psi_eval(x: torch.Tensor, n: int) -> torch.Tensor:

@@ -210,7 +210,13 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
   G = it->second.get();
   convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, G->f2, M, 1.0);
   if (G->exec && !G->failed) {
+    Prof& pf = H.ops().prof;
+    pf.begin(h->st);
     NH_CK(cudaGraphLaunch(G->exec, h->st));
+    if (pf.on) {
+      const double e = H.solve_entries();
+      pf.end(h->st, K_SWEEP, 8.0 * e * s, e * sizeof(cplx<R>) + 2.0 * ((double)M + N) * s * sizeof(cplx<R>));
+    }
     H.ops().count((int)G->kernels);
   } else {
     H.solve(G->f2, M, s, G->yt, N);
@@ -672,6 +678,8 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
       h->h32->build(opt.eps);
     }
     NH_CK(cudaStreamSynchronize(h->st));
+    if (h->h32 && gemm_tc_error(true))
+      throw Error(ST_ETIMEOUT, "build: a bounded wait of the tensor-core GEMM ran out");
     h->t_build = now_ms() - t0;
     *out = h;
   });
@@ -691,6 +699,8 @@ nudft2_status nudft2_hss_factor(nudft2_hss_t h, void* stream) {
     if (h->h64) h->h64->factor();
     else h->h32->factor();
     NH_CK(cudaStreamSynchronize(h->st));
+    if (h->h32 && gemm_tc_error(true))
+      throw Error(ST_ETIMEOUT, "factor: a bounded wait of the tensor-core GEMM ran out");
     h->t_factor = now_ms() - t0;
     h->factored = true;
   });
@@ -711,26 +721,37 @@ static void do_solve(nudft2_hss_t h, const double2* f, int64_t ldf, int s, doubl
     double2* d = h->scr.arr<double2>((size_t)N * s);
     double* fn = h->scr.arr<double>(s);
     double* rn = h->scr.arr<double>(s);
+    double* dn = h->scr.arr<double>(2 * s);
     NH_CK(cudaMemcpy2DAsync(r, M * sizeof(double2), f, ldf * sizeof(double2), M * sizeof(double2), s,
                             cudaMemcpyDeviceToDevice, h->st));
     NH_CK(cudaMemset2DAsync(c, ldc * sizeof(double2), 0, N * sizeof(double2), s, h->st));
     colnorm2(h->st, M, s, r, M, fn);
-    std::vector<double> hf(s), hr(s);
+    std::vector<double> hf(s), hr(s), hd(2 * s);
     NH_CK(cudaMemcpyAsync(hf.data(), fn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     int it = 0;
     double worst = 1.0;
+    // Stops when the relative residual ||f - A c|| / ||f|| reaches refine_tol (consistent data), or
+    // when the last correction is below refine_tol relative to c (data with a nonzero
+    // least-squares residual, whose residual norm levels off at ||r_LS||).
     for (it = 1; it <= std::max(1, h->opt.refine_max); ++it) {
       hss_solve_lex<float>(h, *h->h32, r, M, s, ylex);
       dft2(h, ylex, N, s, d, N, true);
       axpy2(h->st, N, s, 1.0, d, N, c, (int)ldc);
+      colnorm2(h->st, N, s, d, N, dn);
+      colnorm2(h->st, N, s, c, (int)ldc, dn + s);
       exact_fwd(h, c, ldc, s, r, M);                  // r = A c (FP64, Eq. 1)
       axpy2(h->st, M, s, -1.0, f, (int)ldf, r, M);    // r = A c - f
       colnorm2(h->st, M, s, r, M, rn);
       NH_CK(cudaMemcpyAsync(hr.data(), rn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      NH_CK(cudaMemcpyAsync(hd.data(), dn, 2 * s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       NH_CK(cudaStreamSynchronize(h->st));
       worst = 0;
-      for (int q = 0; q < s; ++q) worst = std::max(worst, std::sqrt(hr[q] / std::max(hf[q], 1e-300)));
-      if (worst <= h->opt.refine_tol) break;
+      double dworst = 0;
+      for (int q = 0; q < s; ++q) {
+        worst = std::max(worst, std::sqrt(hr[q] / std::max(hf[q], 1e-300)));
+        if (hd[s + q] > 0) dworst = std::max(dworst, std::sqrt(hd[q] / hd[s + q]));
+      }
+      if (worst <= h->opt.refine_tol || (it > 1 && dworst <= h->opt.refine_tol)) break;
       axpy2(h->st, M, s, -2.0, r, M, r, M);            // r = f - A c
     }
     h->iters = std::min(it, std::max(1, h->opt.refine_max));
@@ -802,8 +823,28 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
         NH_REQUIRE(ldi >= N && ldo >= M, ST_EINVAL, "apply: leading dimension too small");
         do_solve_adj(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
         break;
-      case NUDFT2_FAST_ADJ:
-        throw Error(ST_ENOTIMPL, "apply: operator not available in this build");
+      case NUDFT2_FAST_ADJ: {
+        // A_fast^* = (G~_hss F)^* = F^* G~_hss^* with F^* = N F^{-1} (F symmetric, F^{-1} = conj(F) / N)
+        NH_REQUIRE(ldi >= M && ldo >= N, ST_EINVAL, "apply: leading dimension too small");
+        auto mk = h->scr.mark();
+        double2* y = h->scr.arr<double2>((size_t)N * nrhs);
+        if (h->h64) {
+          double2* z2 = h->scr.arr<double2>((size_t)M * nrhs);
+          double2* yt = h->scr.arr<double2>((size_t)N * nrhs);
+          convert_gather<double, double>(h->st, (const double2*)d_in, (int)ldi, h->pl.perm2, M, nrhs, z2, M, 1.0);
+          h->h64->matvec_adj(z2, M, nrhs, yt, N);
+          convert_scatter<double, double>(h->st, yt, N, h->pl.colmap, N, nrhs, y, N, 1.0);
+        } else {
+          float2* z2 = h->scr.arr<float2>((size_t)M * nrhs);
+          float2* yt = h->scr.arr<float2>((size_t)N * nrhs);
+          convert_gather<double, float>(h->st, (const double2*)d_in, (int)ldi, h->pl.perm2, M, nrhs, z2, M, 1.0);
+          h->h32->matvec_adj(z2, M, nrhs, yt, N);
+          convert_scatter<float, double>(h->st, yt, N, h->pl.colmap, N, nrhs, y, N, 1.0);
+        }
+        dft2(h, y, N, nrhs, (double2*)d_out, ldo, true, (double)N);
+        h->scr.release(mk);
+        break;
+      }
       default:
         throw Error(ST_EINVAL, "apply: unknown operator");
     }
@@ -827,10 +868,21 @@ nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, cons
     double2* lam = d_gf ? (double2*)d_gf : h->scr.arr<double2>((size_t)M * s);
     const int64_t ldl = d_gf ? ldgf : M;
     do_solve_adj(h, (const double2*)d_g, ldg, s, lam, ldl);
-    if (d_gx) {
-      // mu = A^+ lam ; W = [c, Dx c, Dy c, Dx mu, Dy mu] ; E = A W (exact, FP64)
-      double2* mu = h->scr.arr<double2>((size_t)N * s);
+    double2* mu = nullptr;
+    if (d_gx || !h->h64) {
+      // mu = A^+ lam
+      mu = h->scr.arr<double2>((size_t)N * s);
       do_solve(h, lam, ldl, s, mu, N);
+    }
+    if (!h->h64) {
+      // MIXED: the refined adjoint solves A^* lam = g, but its fixed point lies in the range of the
+      // FP32 HSS adjoint, which differs from range(A) by O(eps).  mu = A^+ lam is refined to the
+      // exact least-squares solution, and A^+ annihilates the part of lam outside range(A), so
+      // lam = A mu (exact FP64 apply) is the minimum-norm solution (A^+)^* g itself.
+      exact_fwd(h, mu, N, s, lam, ldl);
+    }
+    if (d_gx) {
+      // W = [c, Dx c, Dy c, Dx mu, Dy mu] ; E = A W (exact, FP64)
       double2* W = h->scr.arr<double2>((size_t)N * 5 * s);
       double2* E = h->scr.arr<double2>((size_t)M * 5 * s);
       NH_CK(cudaMemcpy2DAsync(W, N * sizeof(double2), d_c, ldc * sizeof(double2), N * sizeof(double2), s,

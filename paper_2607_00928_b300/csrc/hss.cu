@@ -1232,6 +1232,94 @@ template <typename R> void Hss<R>::matvec(const cplx<R>* x, int ldx, int s, cplx
   scr_.release(mk);
 }
 
+// ------------------------------------------------------------------------------- HSS adjoint matvec
+// The adjoint of the nested product above (Def. 2.2): the row bases U (leaf) and R (transfer)
+// now project the input, the column bases V and W expand the output, and each coupling
+// B_{c,c'} acts as B_{c,c'}^* from the row side of c to the column side of c':
+//   up:   z^_leaf = U^* z_leaf ;  z^_tau = sum_c R_c^* z^_c
+//   down: x^_c = W_c x^_tau + sum_{c' != c} B_{c',c}^* z^_{c'}
+//   leaf: x_leaf = D^* z_leaf + V x^_leaf
+template <typename R> void Hss<R>::matvec_adj(const cplx<R>* y, int ldy, int s, cplx<R>* x, int ldx) {
+  const int L = pl_->L;
+  auto mk = scr_.mark();
+  std::vector<std::vector<Mat<R>>> zh(L + 1), xh(L + 1);
+  {
+    std::vector<GemmD<R>> g;
+    zh[L].resize(t_[L].size());
+    for (int p = 0; p < (int)t_[L].size(); ++p) {
+      Node2<R>& nd = t_[L][p];
+      zh[L][p] = scr_.mat<R>(nd.ku, s);
+      Mat<R> yl;
+      yl.p = const_cast<cplx<R>*>(y) + pl_->r0[L][p]; yl.m = pl_->m[L][p]; yl.n = s; yl.ld = ldy;
+      g.push_back(gd<R>(nd.U, OP_C, yl, OP_N, zh[L][p]));
+    }
+    ops_.gemm(g);
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    zh[l].resize(t_[l].size());
+    for (int p = 0; p < (int)t_[l].size(); ++p) zh[l][p] = scr_.mat<R>(t_[l][p].ku, s);
+    for (int c = 0; c < 4; ++c) {
+      std::vector<GemmD<R>> g;
+      for (int p = 0; p < (int)t_[l].size(); ++p)
+        g.push_back(gd<R>(t_[l + 1][4 * p + c].R_, OP_C, zh[l + 1][4 * p + c], OP_N, zh[l][p], R(1), c ? R(1) : R(0)));
+      ops_.gemm(g);
+    }
+  }
+  for (int l = 1; l <= L; ++l) {
+    const int nn = (int)t_[l].size();
+    xh[l].resize(nn);
+    for (int q = 0; q < nn; ++q) xh[l][q] = scr_.mat<R>(t_[l][q].kv, s);
+    for (int j = 0; j < 4; ++j) {
+      std::vector<GemmD<R>> g;
+      for (int q = 0; q < nn; ++q) {
+        const int p = q >> 2, c = q & 3;
+        if (j == 0) {
+          if (l >= 2) g.push_back(gd<R>(t_[l][q].W, OP_N, xh[l - 1][p], OP_N, xh[l][q]));
+          else {
+            GemmD<R> z = gd<R>(t_[l][q].W, OP_N, xh[l][q], OP_N, xh[l][q], R(0), R(0));
+            z.k = 0;
+            g.push_back(z);
+          }
+        } else {
+          const int c2 = (c + j) & 3;
+          g.push_back(gd<R>(t_[l][4 * p + c2].B[c], OP_C, zh[l][4 * p + c2], OP_N, xh[l][q], R(1), R(1)));
+        }
+      }
+      ops_.gemm(g);
+    }
+  }
+  {
+    std::vector<GemmD<R>> g1, g2;
+    for (int p = 0; p < (int)t_[L].size(); ++p) {
+      Node2<R>& nd = t_[L][p];
+      Mat<R> xl, yl;
+      yl.p = const_cast<cplx<R>*>(y) + pl_->r0[L][p]; yl.m = pl_->m[L][p]; yl.n = s; yl.ld = ldy;
+      xl.p = x + pl_->c0[L][p]; xl.m = pl_->nc[L][p]; xl.n = s; xl.ld = ldx;
+      g1.push_back(gd<R>(nd.D, OP_C, yl, OP_N, xl));
+      g2.push_back(gd<R>(nd.V, OP_N, xh[L][p], OP_N, xl, R(1), R(1)));
+    }
+    ops_.gemm(g1);
+    ops_.gemm(g2);
+  }
+  NH_CK(cudaStreamSynchronize(st_));
+  scr_.release(mk);
+}
+
+template <typename R> double Hss<R>::solve_entries() const {
+  double e = 0;
+  const int L = pl_->L;
+  for (int l = 1; l <= L; ++l)
+    for (const Node2<R>& nd : t_[l]) {
+      if (nd.omega) e += (double)nd.Om.m * nd.Om.k;
+      e += (double)nd.P.m * nd.P.k + (double)nd.Qv.m * nd.Qv.k;
+      e += (double)nd.n1 * nd.n1 + (double)nd.n1 * (nd.kv + nd.ku) + (double)nd.kv * nd.kv;
+      for (int c = 0; c < 4; ++c) e += (double)nd.B[c].m * nd.B[c].n;
+      if (l >= 2) e += (double)nd.R_.m * nd.R_.n;
+    }
+  e += (double)Proot_.m * Proot_.k + (double)root_cols_ * root_cols_;
+  return e;
+}
+
 template <typename R> int Hss<R>::max_rank() const {
   int r = 0;
   for (auto& lv : t_)

@@ -75,6 +75,12 @@ template <typename R> class Hss {
   void solve_adj(const cplx<R>* ytree, int ldy, int s, cplx<R>* f2, int ldf);
   // y = G~_hss x (x: N x s tree order, y: M x s 2D order): the HSS matrix-vector product
   void matvec(const cplx<R>* x, int ldx, int s, cplx<R>* y, int ldy);
+  // x = G~_hss^* y (y: M x s 2D order, x: N x s tree order): the adjoint of matvec()
+  void matvec_adj(const cplx<R>* y, int ldy, int s, cplx<R>* x, int ldx);
+  // Complex entries of the factors one URV solve streams (Householder vectors of Omega, P, Q_v
+  // and the root, D11^{-1}, D12, U1, V2, B, R, the root R^{-1}); every one is read at least once
+  // per right-hand-side batch.
+  double solve_entries() const;
   int max_rank() const;
   std::vector<int> level_ranks() const;
   size_t bytes() const { return keep_.reserved(); }

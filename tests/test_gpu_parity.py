@@ -196,3 +196,54 @@ def test_repeated_solves_replay_the_captured_graph(nh, prec):
     assert relerr_cols(c4, c3) < 1e-13
     assert relerr_cols(c3, ct[:, :1]) < 1e-8
     h.close()
+
+
+# ------------------------------------------------------------------ adjoint of the HSS forward map
+@pytest.mark.parametrize("name", ["fp64_n16", "fp64_n32"])
+def test_hss_adjoint_map_is_the_adjoint(nh, name):
+    """FAST_ADJ applies (G~_hss F)^*: <A_fast c, g> = <c, A_fast^* g> to rounding, and A_fast^* g
+    stays within the Thm. 3.7 error bound of the exact adjoint A^* g (oracle)."""
+    w = WORKLOADS[name]
+    x, y, _ = make_workload(w)
+    h = nh.NudftHSS(x, y, w.nx, w.ny, eps=w.eps, levels=w.levels)
+    c = complex_normal((w.N, 3), 78)
+    g = complex_normal((w.M, 3), 79)
+    fa = to_np(h.apply(nh.FAST_FWD, torch.from_numpy(c)))
+    ga = to_np(h.apply(nh.FAST_ADJ, torch.from_numpy(g)))
+    h.close()
+    lhs = np.sum(np.conj(g) * fa, axis=0)
+    rhs = np.sum(np.conj(ga) * c, axis=0)
+    assert np.max(np.abs(lhs - rhs) / (np.linalg.norm(g, axis=0) * np.linalg.norm(fa, axis=0))) < 1e-13
+    assert relerr_cols(ga, orc.adjoint(x, y, g, w.nx, w.ny)) < 100 * w.eps
+
+
+# ------------------------------------------------------------------ degenerate grids
+def test_unperturbed_square_grid_identity_kernel(nh):
+    """Uniform grid x = i/n, y = j/n, M = N: every point sits on a bin boundary (x = 0 included),
+    G~ = I, so every off-diagonal HSS rank is 0 and A^* A = N I: the solve is the inverse DFT,
+    c = A^* f / N, exactly up to rounding."""
+    from synthetic import uniform_grid
+    n = 32
+    x, y = uniform_grid(n, n)
+    ct = complex_normal((n * n, 2), 81)
+    f = orc.forward(x, y, ct, n, n)
+    h = nh.NudftHSS(x, y, n, n, eps=1e-10, levels=3).factor()
+    assert max(h.info()["level_rank"][1:]) == 0
+    c = to_np(h.solve(torch.from_numpy(f)))
+    h.close()
+    assert relerr_cols(c, orc.adjoint(x, y, f, n, n) / (n * n)) < 1e-13
+    assert relerr_cols(c, ct) < 1e-13
+
+
+def test_oversampled_uniform_grid_on_bin_boundaries(nh):
+    """Uniform 2n x n grid: half of the x coordinates sit exactly on column-bin boundaries and
+    A^* A = M I; the solve must return c = A^* f / M (= c_true for consistent data)."""
+    from synthetic import uniform_grid
+    n = 32
+    x, y = uniform_grid(2 * n, n)
+    ct = complex_normal((n * n, 2), 82)
+    f = orc.forward(x, y, ct, n, n) + 0.1 * complex_normal((x.size, 2), 83)   # inconsistent data
+    h = nh.NudftHSS(x, y, n, n, eps=1e-10, levels=3).factor()
+    c = to_np(h.solve(torch.from_numpy(f)))
+    h.close()
+    assert relerr_cols(c, orc.adjoint(x, y, f, n, n) / x.size) < 1e-10

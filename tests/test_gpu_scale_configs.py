@@ -7,8 +7,9 @@ Checked instead:
 * the solution: consistent data (plus 1e-12 relative noise for config 2) has the LS solution
   c_true up to ~cond(A) * noise, so c must match c_true to the 1e-8 target;
 * sampled residuals: r_j = f_j - (A c)_j evaluated by the oracle at sampled points j.
-The handles use the same options as bench.py.  The differentiation workload is checked through
-A^* grad_f = g and a directional central difference of the GPU map."""
+The handles use the same options as bench.py.  The differentiation workload is checked against
+the oracle's matrix-free least-squares gradient at 64 sampled points and by a central difference
+of the map."""
 import numpy as np
 import pytest
 
@@ -70,40 +71,74 @@ def test_config3_mixed_n256_full_size(nh):
     assert _sampled_residual(x, y, c, f, w.nx, w.ny, idx) < 1e-8
 
 
-def test_grad_config5_scale_properties(nh):
-    """n = 128, M = 32768, 16 right-hand sides (the differentiation workload): grad_f solves
-    A^* lam = g (checked with the exact adjoint), and the point gradient matches a directional
-    central difference of the GPU map along a random direction.  The handles run in mixed
-    precision refined to 1e-12 with the FP64 exact applies, so the map and its gradient are the
-    FP64 least-squares ones while each build takes seconds (an FP64 build at this size takes
-    minutes)."""
+@pytest.fixture(scope="module")
+def grad5():
+    """The differentiation workload (n = 128, M = 32768, 16 right-hand sides), consistent data
+    f = A c_true formed by the oracle, loss L = sum |c - c_target|^2, and the oracle's gradient at
+    64 sampled points (matrix-free: CG on the normal equations with the direct applies, ~1 min on
+    the host).  For consistent data the least-squares solution is c_true."""
     w = WORKLOADS["grad_n128"]
     x, y, c_true = make_workload(w)
-    ct = complex_normal((w.N, w.nrhs), 55)
-    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    opts = dict(eps=1e-6, levels=w.levels, prec="mixed", refine_tol=1e-12, refine_max=30)
-    h = nh.NudftHSS(xt, yt, w.nx, w.ny, **opts).factor()
-    f = h.apply(nh.EXACT_FWD, torch.from_numpy(c_true).cuda())
-    c = h.solve(f)
-    g = 2 * (c - torch.from_numpy(ct).cuda())
-    gf, gx, gy = h.grad(f, c, g)
-    back = h.apply(nh.EXACT_ADJ, gf)
-    assert float(torch.linalg.norm(back - g) / torch.linalg.norm(g)) < 1e-8
+    ctg = complex_normal((w.N, w.nrhs), 55)
+    f = orc.forward(x, y, c_true, w.nx, w.ny)
+    rows = np.random.default_rng(57).choice(w.M, 64, replace=False)
+    g = 2 * (c_true - ctg)
+    _, lam, gx, gy = orc.lstsq_grad_rows(x, y, w.nx, w.ny, f, g, rows, c=c_true, tol=1e-13)
+    return dict(w=w, x=x, y=y, ctg=ctg, f=f, rows=rows, lam=lam, gx=gx, gy=gy)
+
+
+def _gpu_grad(nh, d, **opts):
+    w = d["w"]
+    xt, yt = torch.from_numpy(d["x"]).cuda(), torch.from_numpy(d["y"]).cuda()
+    h = nh.NudftHSS(xt, yt, w.nx, w.ny, levels=w.levels, **opts).factor()
+    ft = torch.from_numpy(d["f"]).cuda()
+    c = h.solve(ft)
+    gf, gx, gy = h.grad(ft, c, 2 * (c - torch.from_numpy(d["ctg"]).cuda()))
     h.close()
+    return gf.cpu().numpy(), gx.cpu().numpy(), gy.cpu().numpy()
+
+
+MIXED_13 = dict(eps=1e-6, prec="mixed", refine_tol=1e-13, refine_max=30)
+
+
+def test_grad_config5_mixed_refined_matches_oracle_and_central_differences(nh, grad5):
+    """Mixed precision refined to 1e-13 with the FP64 exact applies: grad_f and the point
+    gradient match the oracle's exact least-squares gradient at the sampled points to 1e-8, and
+    a central difference (h = 1e-6) of the map along a random direction of all 2M coordinates
+    matches the gradient's directional derivative to 1e-6."""
+    d = grad5
+    w, x, y = d["w"], d["x"], d["y"]
+    gf, gx, gy = _gpu_grad(nh, d, **MIXED_13)
+    rows = d["rows"]
+    assert _relcols(gf, d["lam"]) < 1e-8
+    assert float(np.linalg.norm(gx[rows] - d["gx"]) / np.linalg.norm(d["gx"])) < 1e-8
+    assert float(np.linalg.norm(gy[rows] - d["gy"]) / np.linalg.norm(d["gy"])) < 1e-8
     rng = np.random.default_rng(56)
     dx, dy = rng.standard_normal(w.M), rng.standard_normal(w.M)
-    step = 1e-5   # phase changes ~2 pi 128 step: central-difference truncation ~1e-5 relative
+    step = 1e-6   # truncation ~ (2 pi 128 * 4.5e-6)^2 / 6 < 1e-7 relative
+    ft = torch.from_numpy(d["f"]).cuda()
+    ctg = torch.from_numpy(d["ctg"]).cuda()
 
     def L(sgn):
         # A is 1-periodic in each coordinate, so wrapping back into [0, 1) leaves the map unchanged
         xs, ys = np.mod(x + sgn * step * dx, 1.0), np.mod(y + sgn * step * dy, 1.0)
-        hh = nh.NudftHSS(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), w.nx, w.ny, **opts).factor()
-        cc = hh.solve(f)
+        hh = nh.NudftHSS(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda(), w.nx, w.ny, levels=w.levels,
+                         **MIXED_13).factor()
+        cc = hh.solve(ft)
         hh.close()
-        return float(torch.sum(torch.abs(cc - torch.from_numpy(ct).cuda()) ** 2))
+        return float(torch.sum(torch.abs(cc - ctg) ** 2))
 
     fd = (L(1) - L(-1)) / (2 * step)
-    dd = float(np.dot(gx.cpu().numpy(), dx) + np.dot(gy.cpu().numpy(), dy))
-    # both solutions are refined to ~1e-12; the bound covers the O(eps) error of the mixed-mode
-    # adjoint (its fixed point lies in the range of the FP32 HSS adjoint) and the truncation error
-    assert abs(fd - dd) < 3e-4 * abs(dd)
+    dd = float(np.dot(gx, dx) + np.dot(gy, dy))
+    assert abs(fd - dd) < 1e-6 * abs(dd)
+
+
+def test_grad_config5_fp64_mode_matches_oracle(nh, grad5):
+    """FP64 mode (eps 1e-10, no refinement) at the full size: the gradient of the HSS
+    pseudo-inverse matches the oracle's at the sampled points to 1e-7."""
+    d = grad5
+    gf, gx, gy = _gpu_grad(nh, d, eps=1e-10)
+    rows = d["rows"]
+    assert _relcols(gf, d["lam"]) < 1e-7
+    assert float(np.linalg.norm(gx[rows] - d["gx"]) / np.linalg.norm(d["gx"])) < 1e-7
+    assert float(np.linalg.norm(gy[rows] - d["gy"]) / np.linalg.norm(d["gy"])) < 1e-7
