@@ -72,6 +72,9 @@ typedef struct {
 
 /* opts.flags bits */
 #define NUDFT2_FLAG_PROFILE 1u   /* time every launch of the main kernel classes with CUDA events */
+#define NUDFT2_FLAG_FP64_RESIDUALS 2u   /* MIXED: every refinement residual from the exact FP64 apply
+                                           (default: the first; later steps subtract A d of the
+                                           O(eps)-small correction d in FP32)               */
 
 /* Accumulated device time of one kernel class (NUDFT2_FLAG_PROFILE), with its algorithmic
  * flop and byte counts summed over launches. */
@@ -93,6 +96,11 @@ typedef struct {
   double refine_relres;      /* max relative residual after the last MIXED solve       */
   size_t device_bytes;       /* device memory reserved by the handle                   */
   int launches;              /* kernel launches issued by the handle so far            */
+  int gemm_tuned;            /* GEMM shape classes the autotuner has measured in this
+                                process (kernel choice cached per class)              */
+  int solve_graphs;          /* URV solves captured into CUDA graphs (one per RHS count) */
+  int solve_graph_failures;  /* captures that failed (those solves run uncaptured)     */
+  int solve_replays;         /* solves run by replaying a captured graph               */
 } nudft2_info;
 
 /* Build the HSS approximation of G~ = A F^{-1} (Alg. 1 steps 1-3, Sec. 3 and Sec. 2.2).
@@ -109,9 +117,16 @@ nudft2_status nudft2_hss_factor(nudft2_hss_t h, void* stream);
 /* c = F^{-1} G~_hss^+ f (Alg. 1 step 5): URV sweeps then the 2D inverse DFT.
  * d_f: M x nrhs complex128 (ld ldf >= M), point order as given to build.
  * d_c: N x nrhs complex128 (ld ldc >= N), lexicographic ky + kx*ny.
- * MIXED handles refine with the exact FP64 residual (opts.refine_tol / refine_max): c += the FP32
- * solve of r = f - A c until ||r|| / ||f|| <= refine_tol, or, after the first step, until the
+ * MIXED handles refine with the exact residual (opts.refine_tol / refine_max): c += d, d the FP32
+ * solve of r = f - A c, until ||r|| / ||f|| <= refine_tol, or, after the first step, until the
  * correction is at most refine_tol ||c|| per column (data with a nonzero least-squares residual).
+ * The first residual comes from the exact FP64 apply; later ones are updated as r -= A d with the
+ * exact apply of the small correction d in FP32 (its rounding is O(eps u_32) ||f||), unless
+ * NUDFT2_FLAG_FP64_RESIDUALS asks for the FP64 apply at every step.  When the residual does not
+ * reach refine_tol (data outside the range of A), the stop above is the fixed point of the FP32
+ * pseudo-inverse, O(eps) ||r_LS|| away from the least-squares solution; the solve then polishes on
+ * the normal equations, c += P P^* A^* r (A^* r in FP64, P the FP32 solve), until the correction
+ * is at most refine_tol ||c||: the least-squares solution itself.
  * Errors: ESTATE (not factorised), EINVAL (ld too small, nrhs < 0). */
 nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
                                void* stream);

@@ -31,7 +31,8 @@ class Info(ctypes.Structure):
                 ("prec", ctypes.c_int), ("max_rank", ctypes.c_int), ("level_rank", ctypes.c_int * 16),
                 ("t_build_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("refine_iters", ctypes.c_int), ("refine_relres", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int)]
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int), ("gemm_tuned", ctypes.c_int),
+                ("solve_graphs", ctypes.c_int), ("solve_graph_failures", ctypes.c_int), ("solve_replays", ctypes.c_int)]
 
 
 class KStat(ctypes.Structure):
@@ -40,6 +41,7 @@ class KStat(ctypes.Structure):
 
 
 FLAG_PROFILE = 1
+FLAG_FP64_RESIDUALS = 2
 
 
 class NudftError(RuntimeError):
@@ -206,7 +208,7 @@ class NudftHSS:
 
     def __init__(self, x, y, nx: int, ny: int, eps: float = 1e-10, levels: int = 0, leaf: int = 64,
                  prec: str = "fp64", refine_tol: float = 1e-8, refine_max: int = 8, stream=None,
-                 profile: bool = False):
+                 profile: bool = False, fp64_residuals: bool = False):
         self._h = ctypes.c_void_p()
         self.x = torch.as_tensor(x).to(device="cuda", dtype=torch.float64).contiguous()
         self.y = torch.as_tensor(y).to(device="cuda", dtype=torch.float64).contiguous()
@@ -214,7 +216,7 @@ class NudftHSS:
         self.nx, self.ny, self.N = nx, ny, nx * ny
         self.stream = stream
         o = Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
-                 FLAG_PROFILE if profile else 0)
+                 (FLAG_PROFILE if profile else 0) | (FLAG_FP64_RESIDUALS if fp64_residuals else 0))
         _check(lib().nudft2_hss_build(ctypes.c_void_p(self.x.data_ptr()), ctypes.c_void_p(self.y.data_ptr()),
                                       self.M, nx, ny, ctypes.byref(o), _stream(stream), ctypes.byref(self._h)))
 
@@ -279,7 +281,9 @@ class NudftHSS:
         return {"M": i.M, "nx": i.nx, "ny": i.ny, "levels": i.levels, "prec": i.prec, "max_rank": i.max_rank,
                 "level_rank": list(i.level_rank)[: i.levels + 1], "t_build_ms": i.t_build_ms,
                 "t_factor_ms": i.t_factor_ms, "t_solve_ms": i.t_solve_ms, "refine_iters": i.refine_iters,
-                "refine_relres": i.refine_relres, "device_bytes": i.device_bytes, "launches": i.launches}
+                "refine_relres": i.refine_relres, "device_bytes": i.device_bytes, "launches": i.launches,
+                "gemm_tuned": i.gemm_tuned, "solve_graphs": i.solve_graphs,
+                "solve_graph_failures": i.solve_graph_failures, "solve_replays": i.solve_replays}
 
     def kstats(self) -> dict:
         """Per kernel class: device ms, algorithmic flops and bytes, launches (profile=True)."""

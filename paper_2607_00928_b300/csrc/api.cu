@@ -45,9 +45,11 @@ struct nudft2_hss_s {
   std::unique_ptr<Hss<float>> h32;
   std::unique_ptr<Ops<double>> ops;
   double2 *Ax = nullptr, *Ay = nullptr;              // exp(-2 pi i k x_j), caller order
+  float2 *Ax32 = nullptr, *Ay32 = nullptr;           // the same in FP32 (MIXED: correction applies)
   double2 *Fxi = nullptr, *Fyi = nullptr;            // inverse DFT matrices (1/n included)
   double2 *Fxf = nullptr, *Fyf = nullptr;            // forward DFT matrices
   bool factored = false;
+  int graphs_ok = 0, graphs_failed = 0, replays = 0;
   double t_build = 0, t_factor = 0, t_solve = 0, relres = 0;
   int iters = 0;
 };
@@ -126,6 +128,46 @@ static void exact_adj_impl(Ops<double>& ops, Arena& scr, cudaStream_t st, const 
   scr.release(mk);
 }
 
+// r -= A d in FP32 arithmetic (tables, products and sums in FP32 on the tensor-core GEMM path;
+// the subtraction in FP64).  Used for the refinement residual after its first step, where d is
+// a correction of size O(eps) ||c||, so its FP32 rounding is O(eps u_32) ||f|| (see do_solve).
+static void exact_fwd_sub32(nudft2_hss_s* h, const double2* d, int64_t ldd, int s, double2* r, int64_t ldr) {
+  const int M = h->M, nx = h->nx, ny = h->ny, N = h->N;
+  Ops<float>& ops = h->h32->ops();
+  const int sc = std::max(1, std::min(s, (int)std::max<int64_t>(1, ((int64_t)1 << 31) / ((int64_t)M * nx * 8))));
+  auto mk = h->scr.mark();
+  float2* T = h->scr.arr<float2>((size_t)M * nx * sc);
+  float2* C = h->scr.arr<float2>((size_t)N * sc);
+  for (int q0 = 0; q0 < s; q0 += sc) {
+    const int qs = std::min(sc, s - q0);
+    convert_gather<double, float>(h->st, d + (size_t)q0 * ldd, (int)ldd, nullptr, N, qs, C, N, 1.0);
+    ops.gemm({GemmD<float>{h->Ay32, C, T, M, nx * qs, ny, M, ny, M, OP_N, OP_N, 1.f, 0.f}});
+    rowdot_sub32(h->st, h->Ax32, M, T, M, M, nx, qs, r + (size_t)q0 * ldr, (int)ldr);
+    ops.count(2);
+  }
+  h->scr.release(mk);
+}
+
+// out -= A^* e in FP32 arithmetic, the adjoint counterpart of exact_fwd_sub32.
+static void exact_adj_sub32(nudft2_hss_s* h, const double2* e, int64_t lde, int s, double2* out, int64_t ldo) {
+  const int M = h->M, nx = h->nx, ny = h->ny, N = h->N;
+  Ops<float>& ops = h->h32->ops();
+  const int sc = std::max(1, std::min(s, (int)std::max<int64_t>(1, ((int64_t)1 << 31) / ((int64_t)M * nx * 8))));
+  auto mk = h->scr.mark();
+  float2* Z = h->scr.arr<float2>((size_t)M * nx * sc);
+  float2* O = h->scr.arr<float2>((size_t)N * sc);
+  double2* O64 = h->scr.arr<double2>((size_t)N * sc);
+  for (int q0 = 0; q0 < s; q0 += sc) {
+    const int qs = std::min(sc, s - q0);
+    scale_rows_conj32(h->st, h->Ax32, M, e + (size_t)q0 * lde, (int)lde, M, nx, qs, Z, M);
+    ops.gemm({GemmD<float>{h->Ay32, Z, O, ny, nx * qs, M, M, M, ny, OP_C, OP_N, 1.f, 0.f}});
+    convert_gather<float, double>(h->st, O, N, nullptr, N, qs, O64, N, 1.0);
+    axpy2(h->st, N, qs, -1.0, O64, N, out + (size_t)q0 * ldo, (int)ldo);
+    ops.count(3);
+  }
+  h->scr.release(mk);
+}
+
 static void exact_fwd(nudft2_hss_s* h, const double2* c, int64_t ldc, int s, double2* f, int64_t ldf) {
   exact_fwd_impl(*h->ops, h->scr, h->st, Exact{h->M, h->nx, h->ny, h->Ax, h->Ay}, c, ldc, s, f, ldf);
 }
@@ -202,6 +244,7 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
       if (graph) cudaGraphDestroy(graph);
     }
     if (e != cudaSuccess) { G->failed = true; cudaGetLastError(); }
+    if (G->failed) h->graphs_failed++; else h->graphs_ok++;
     H.freeze_scratch(false);
     H.ops().set_capture(nullptr);
     H.ops().prof.on = prof;
@@ -218,6 +261,7 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
       pf.end(h->st, K_SWEEP, 8.0 * e * s, e * sizeof(cplx<R>) + 2.0 * ((double)M + N) * s * sizeof(cplx<R>));
     }
     H.ops().count((int)G->kernels);
+    h->replays++;
   } else {
     H.solve(G->f2, M, s, G->yt, N);
   }
@@ -327,19 +371,24 @@ static void do_solve_adj(nudft2_hss_s* h, const double2* g, int64_t ldg, int s, 
     NH_CK(cudaMemcpyAsync(hg.data(), gn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     int it = 0;
     double worst = 1.0;
+    const bool full = (h->opt.flags & NUDFT2_FLAG_FP64_RESIDUALS) != 0;
     for (it = 1; it <= std::max(1, h->opt.refine_max); ++it) {
       dft2(h, r, N, s, ylex, N, false, 1.0 / N);
       hss_solve_adj_lex<float>(h, *h->h32, ylex, s, d, M);
       axpy2(h->st, M, s, 1.0, d, M, lam, (int)ldl);
-      exact_adj(h, lam, ldl, s, r, N);                // r = A^* lam (FP64)
-      axpy2(h->st, N, s, -1.0, g, (int)ldg, r, N);    // r = A^* lam - g
+      if (it == 1 || full) {
+        exact_adj(h, lam, ldl, s, r, N);              // r = A^* lam (FP64)
+        axpy2(h->st, N, s, -1.0, g, (int)ldg, r, N);  // r = A^* lam - g
+        axpy2(h->st, N, s, -2.0, r, N, r, N);         // r = g - A^* lam
+      } else {
+        exact_adj_sub32(h, d, M, s, r, N);            // r -= A^* d: the correction is O(eps) small
+      }
       colnorm2(h->st, N, s, r, N, rn);
       NH_CK(cudaMemcpyAsync(hr.data(), rn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       NH_CK(cudaStreamSynchronize(h->st));
       worst = 0;
       for (int q = 0; q < s; ++q) worst = std::max(worst, std::sqrt(hr[q] / std::max(hg[q], 1e-300)));
       if (worst <= h->opt.refine_tol) break;
-      axpy2(h->st, N, s, -2.0, r, N, r, N);            // r = g - A^* lam
     }
     h->iters = std::min(it, std::max(1, h->opt.refine_max));
     h->relres = worst;
@@ -675,6 +724,10 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     } else {
       h->h32.reset(new Hss<float>(h->st, &h->pl));
       h->h32->ops().prof.on = prof;
+      h->Ax32 = h->keep.arr<float2>((size_t)M * nx);
+      h->Ay32 = h->keep.arr<float2>((size_t)M * ny);
+      convert_gather<double, float>(h->st, h->Ax, (int)M, nullptr, (int)M, nx, h->Ax32, (int)M, 1.0);
+      convert_gather<double, float>(h->st, h->Ay, (int)M, nullptr, (int)M, ny, h->Ay32, (int)M, 1.0);
       h->h32->build(opt.eps);
     }
     NH_CK(cudaStreamSynchronize(h->st));
@@ -733,14 +786,20 @@ static void do_solve(nudft2_hss_t h, const double2* f, int64_t ldf, int s, doubl
     // Stops when the relative residual ||f - A c|| / ||f|| reaches refine_tol (consistent data), or
     // when the last correction is below refine_tol relative to c (data with a nonzero
     // least-squares residual, whose residual norm levels off at ||r_LS||).
+    const bool full = (h->opt.flags & NUDFT2_FLAG_FP64_RESIDUALS) != 0;
     for (it = 1; it <= std::max(1, h->opt.refine_max); ++it) {
       hss_solve_lex<float>(h, *h->h32, r, M, s, ylex);
       dft2(h, ylex, N, s, d, N, true);
       axpy2(h->st, N, s, 1.0, d, N, c, (int)ldc);
       colnorm2(h->st, N, s, d, N, dn);
       colnorm2(h->st, N, s, c, (int)ldc, dn + s);
-      exact_fwd(h, c, ldc, s, r, M);                  // r = A c (FP64, Eq. 1)
-      axpy2(h->st, M, s, -1.0, f, (int)ldf, r, M);    // r = A c - f
+      if (it == 1 || full) {
+        exact_fwd(h, c, ldc, s, r, M);                // r = A c (FP64, Eq. 1)
+        axpy2(h->st, M, s, -1.0, f, (int)ldf, r, M);  // r = A c - f
+        axpy2(h->st, M, s, -2.0, r, M, r, M);         // r = f - A c
+      } else {
+        exact_fwd_sub32(h, d, N, s, r, M);            // r -= A d: the correction is O(eps) small
+      }
       colnorm2(h->st, M, s, r, M, rn);
       NH_CK(cudaMemcpyAsync(hr.data(), rn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       NH_CK(cudaMemcpyAsync(hd.data(), dn, 2 * s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -752,9 +811,45 @@ static void do_solve(nudft2_hss_t h, const double2* f, int64_t ldf, int s, doubl
         if (hd[s + q] > 0) dworst = std::max(dworst, std::sqrt(hd[q] / hd[s + q]));
       }
       if (worst <= h->opt.refine_tol || (it > 1 && dworst <= h->opt.refine_tol)) break;
-      axpy2(h->st, M, s, -2.0, r, M, r, M);            // r = f - A c
     }
     h->iters = std::min(it, std::max(1, h->opt.refine_max));
+    // Data with a nonzero least-squares residual: the loop above stops at the fixed point
+    // P (f - A c) = 0 of the FP32 pseudo-inverse P, which differs from the least-squares solution
+    // by O(eps) ||r_LS||.  Polish on the normal equations: c += P P^* A^* r with A^* r from the exact
+    // FP64 adjoint; P P^* approximates (A^* A)^{-1}, and the fixed point is A^* (f - A c) = 0.
+    if (worst > h->opt.refine_tol) {
+      double2* t = h->scr.arr<double2>((size_t)N * s);
+      double2* u = h->scr.arr<double2>((size_t)M * s);
+      for (int k = 1; k <= std::max(1, h->opt.refine_max); ++k) {
+        exact_adj(h, r, M, s, t, N);                     // t = A^* r (FP64)
+        dft2(h, t, N, s, ylex, N, false, 1.0 / N);       // P^* t = G~^{+*} F t / N
+        hss_solve_adj_lex<float>(h, *h->h32, ylex, s, u, M);
+        hss_solve_lex<float>(h, *h->h32, u, M, s, ylex); // d = P u
+        dft2(h, ylex, N, s, d, N, true);
+        axpy2(h->st, N, s, 1.0, d, N, c, (int)ldc);
+        colnorm2(h->st, N, s, d, N, dn);
+        colnorm2(h->st, N, s, c, (int)ldc, dn + s);
+        if (full) {
+          exact_fwd(h, c, ldc, s, r, M);
+          axpy2(h->st, M, s, -1.0, f, (int)ldf, r, M);
+          axpy2(h->st, M, s, -2.0, r, M, r, M);
+        } else {
+          exact_fwd_sub32(h, d, N, s, r, M);
+        }
+        colnorm2(h->st, M, s, r, M, rn);
+        NH_CK(cudaMemcpyAsync(hr.data(), rn, s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        NH_CK(cudaMemcpyAsync(hd.data(), dn, 2 * s * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        NH_CK(cudaStreamSynchronize(h->st));
+        worst = 0;
+        double dworst = 0;
+        for (int q = 0; q < s; ++q) {
+          worst = std::max(worst, std::sqrt(hr[q] / std::max(hf[q], 1e-300)));
+          if (hd[s + q] > 0) dworst = std::max(dworst, std::sqrt(hd[q] / hd[s + q]));
+        }
+        h->iters++;
+        if (dworst <= h->opt.refine_tol) break;
+      }
+    }
     h->relres = worst;
   }
   h->scr.release(mk);
@@ -933,6 +1028,10 @@ nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info) {
     info->refine_relres = h->relres;
     info->device_bytes = h->keep.reserved() + h->scr.reserved() + (h->h64 ? h->h64->bytes() : h->h32->bytes());
     info->launches = h->ops->launches() + (h->h64 ? h->h64->ops().launches() : h->h32->ops().launches());
+    info->gemm_tuned = gemm_tune_entries();
+    info->solve_graphs = h->graphs_ok;
+    info->solve_graph_failures = h->graphs_failed;
+    info->solve_replays = h->replays;
   });
 }
 

@@ -6,6 +6,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cooperative_groups.h>
 
@@ -273,57 +276,151 @@ template <typename R> void Ops<R>::gemm(const std::vector<GemmD<R>>& d0) {
     if (!part[c].empty()) gemm_class(part[c], c);
 }
 
-template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, int cls) {
-  constexpr int BM = 16 * GemmCfg<R>::TM, BN = 16 * GemmCfg<R>::TN;
-  std::vector<GemmD<R>> d;
-  d.reserve(d0.size());
-  std::vector<int> pre;
-  int tiles = 0, tiles_big = 0;
-  double work = 0, work_big_ok = 0, work_tc = 0;
-  for (const auto& g : d0) {
-    d.push_back(g);
-    pre.push_back(tiles);
-    tiles += ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
-    tiles_big += ((g.m + 127) / 128) * ((g.n + 127) / 128);
-    const double w = (double)g.m * g.n * std::max(g.k, 1);
-    work += w;
-    if (g.m >= 128 && g.n >= 128) work_big_ok += w;
-    // the tensor-core kernel pays for operand packing and a pipeline fill per tile: it wins on
-    // products with long reductions or large faces (measured: 128^3 products run faster on CUDA cores)
-    if (g.m >= 128 && g.n >= 128 && (g.k >= 256 || std::min(g.m, g.n) >= 256)) work_tc += w;
-  }
-  if (d.empty()) return;
-  // FP32 batches dominated by large products use 128 x 128 tiles (8 x 8 complex per thread)
-  if constexpr (sizeof(R) == 4) if (work_big_ok >= 0.8 * work && tiles_big >= 2 * 148) {
-    std::vector<int> preb;
-    int t = 0;
+// ------------------------------------------------------------------------------- kernel choice
+// Three kernels serve a batch of one operand-layout class: CUDA-core 64 x 64 tiles (32 x 32 in
+// FP64) with split-K when the tiles cannot fill the GPU, CUDA-core 128 x 128 tiles (FP32), and
+// the tensor-core kernel (FP32).  gemm_heuristic is the static rule; the autotuner replaces it per
+// shape class by measurement.
+enum GemmKind { GK_TILE64 = 0, GK_TILE128 = 1, GK_TC = 2 };
+
+template <typename R> static int gemm_heuristic(const std::vector<GemmD<R>>& d) {
+  if constexpr (sizeof(R) == 8) {
+    return GK_TILE64;
+  } else {
+    int tiles_big = 0;
+    double work = 0, work_big_ok = 0, work_tc = 0;
     for (const auto& g : d) {
-      preb.push_back(t);
-      t += ((g.m + 127) / 128) * ((g.n + 127) / 128);
+      tiles_big += ((g.m + 127) / 128) * ((g.n + 127) / 128);
+      const double w = (double)g.m * g.n * std::max(g.k, 1);
+      work += w;
+      if (g.m >= 128 && g.n >= 128) work_big_ok += w;
+      // the tensor-core kernel pays for operand packing and a pipeline fill per tile: it wins on
+      // products with long reductions or large faces (measured: 128^3 products run faster on CUDA cores)
+      if (g.m >= 128 && g.n >= 128 && (g.k >= 256 || std::min(g.m, g.n) >= 256)) work_tc += w;
     }
-    double fl = 0;
-    if (prof.on)
-      for (const auto& g : d) fl += 8.0 * g.m * g.n * std::max(g.k, 0);
-    if constexpr (sizeof(R) == 4) {
-      if (gemm_tc_enabled() && work_tc >= 0.8 * work) {
-        // the packed operands live until the GEMM has run; later scratch users on this stream are
-        // ordered after it, so the space is handed back at once
-        auto mk = ar_->mark();
-        prof.begin(st_);
-        count(gemm_tc_run(d, cls, *ar_, st_, &Ops<R>::stage_cb, this));
-        prof.end(st_, K_GEMM_TC, fl, 0);
-        ar_->release(mk);
-        return;
-      }
-    }
-    GemmD<R>* dd = upload(d);
-    int* dp = upload_ints(preb);
-    prof.begin(st_);
-    launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
-    prof.end(st_, K_GEMM, fl, 0);
-    count();
-    return;
+    if (work_big_ok >= 0.8 * work && tiles_big >= 2 * 148)
+      return (gemm_tc_enabled() && work_tc >= 0.8 * work) ? GK_TC : GK_TILE128;
+    return GK_TILE64;
   }
+}
+
+// Autotuner.  Key: precision, layout class, and log2 buckets of the largest m, n, k and of the
+// problem count of the batch.  The first batch with a new key runs every candidate kernel twice
+// on scratch outputs (beta = 0) and keeps the fastest second run; later batches with the key use
+// that kernel.  The cache lives for the process (NH_AUTOTUNE=0 turns tuning off and leaves the
+// static rule).  No tuning happens while the stream is being captured into a graph.
+namespace {
+struct TuneKey {
+  int prec, cls, lm, ln, lk, lb;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(prec, cls, lm, ln, lk, lb) < std::tie(o.prec, o.cls, o.lm, o.ln, o.lk, o.lb);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+int ilog2c(int v) { int l = 0; while ((1 << l) < std::max(v, 1)) ++l; return l; }
+bool autotune_enabled() {
+  const char* e = std::getenv("NH_AUTOTUNE");
+  return !(e && std::strcmp(e, "0") == 0);
+}
+}  // namespace
+
+int gemm_tune_entries() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
+}
+
+template <typename R> int Ops<R>::gemm_pick(const std::vector<GemmD<R>>& d, int cls) {
+  const int h = gemm_heuristic<R>(d);
+  if constexpr (sizeof(R) == 8) return h;   // one FP64 kernel
+  if (pool_ || !autotune_enabled()) return h;
+  int mx = 0, nx = 0, kx = 0;
+  for (const auto& g : d) { mx = std::max(mx, g.m); nx = std::max(nx, g.n); kx = std::max(kx, g.k); }
+  const TuneKey key{(int)sizeof(R), cls, ilog2c(mx), ilog2c(nx), ilog2c(kx), ilog2c((int)d.size())};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  std::vector<int> cand = {GK_TILE64, GK_TILE128};
+  if (gemm_tc_enabled()) cand.push_back(GK_TC);
+  auto mk = ar_->mark();
+  std::vector<GemmD<R>> dt(d);
+  for (auto& g : dt) {
+    g.C = (cplx<R>*)ar_->alloc((size_t)g.m * g.n * sizeof(cplx<R>));
+    g.ldc = g.m;
+    g.beta = R(0);
+  }
+  const bool pon = prof.on;
+  const int nl = launches_;
+  prof.on = false;
+  cudaEvent_t e0, e1;
+  NH_CK(cudaEventCreate(&e0));
+  NH_CK(cudaEventCreate(&e1));
+  int best = h;
+  float best_ms = 1e30f;
+  for (int kind : cand) {
+    gemm_run(dt, cls, kind);                 // first run: one-time launch set-up
+    NH_CK(cudaEventRecord(e0, st_));
+    gemm_run(dt, cls, kind);
+    NH_CK(cudaEventRecord(e1, st_));
+    NH_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    NH_CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) { best_ms = ms; best = kind; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  prof.on = pon;
+  launches_ = nl;
+  ar_->release(mk);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
+template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d, int cls) {
+  if (d.empty()) return;
+  gemm_run(d, cls, gemm_pick(d, cls));
+}
+
+template <typename R> void Ops<R>::gemm_run(const std::vector<GemmD<R>>& d, int cls, int kind) {
+  constexpr int BM = 16 * GemmCfg<R>::TM, BN = 16 * GemmCfg<R>::TN;
+  double fl = 0, by = 0;
+  if (prof.on)
+    for (const auto& g : d) {
+      fl += 8.0 * g.m * g.n * std::max(g.k, 0);
+      by += (double)sizeof(cplx<R>) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != R(0) ? 2.0 : 1.0) * g.m * g.n);
+    }
+  if constexpr (sizeof(R) == 4) {
+    if (kind == GK_TC) {
+      // the packed operands live until the GEMM has run; later scratch users on this stream are
+      // ordered after it, so the space is handed back at once
+      auto mk = ar_->mark();
+      prof.begin(st_);
+      count(gemm_tc_run(d, cls, *ar_, st_, &Ops<R>::stage_cb, this));
+      prof.end(st_, K_GEMM_TC, fl, by);
+      ar_->release(mk);
+      return;
+    }
+    if (kind == GK_TILE128) {
+      std::vector<int> preb;
+      int t = 0;
+      for (const auto& g : d) {
+        preb.push_back(t);
+        t += ((g.m + 127) / 128) * ((g.n + 127) / 128);
+      }
+      GemmD<R>* dd = upload(d);
+      int* dp = upload_ints(preb);
+      prof.begin(st_);
+      launch_gemm<R, 8, 8, 8>(cls, t, st_, dd, dp, (int)d.size(), nullptr, nullptr);
+      prof.end(st_, K_GEMM, fl, by);
+      count();
+      return;
+    }
+  }
+  int tiles = 0;
+  for (const auto& g : d) tiles += ((g.m + BM - 1) / BM) * ((g.n + BN - 1) / BN);
   // split long reductions when the output tiles alone cannot fill the GPU
   std::vector<int> ks(d.size(), 1);
   bool any_split = false;
@@ -351,18 +448,9 @@ template <typename R> void Ops<R>::gemm_class(const std::vector<GemmD<R>>& d0, i
   int* dp = upload_ints(pre2);
   int* dks = any_split ? upload_ints(ks) : nullptr;
   cplx<R>* const* dws = any_split ? upload(wsp) : nullptr;
-  double fl = 0, by = 0;
-  if (prof.on)
-    for (const auto& g : d) {
-      fl += 8.0 * g.m * g.n * std::max(g.k, 0);
-      by += (double)sizeof(cplx<R>) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != R(0) ? 2.0 : 1.0) * g.m * g.n);
-    }
   prof.begin(st_);
   launch_gemm<R, GemmCfg<R>::TM, GemmCfg<R>::TN, GemmCfg<R>::BK>(cls, tiles2, st_, dd, dp, (int)d.size(), dks, dws);
   if (any_split) {
-    std::vector<int> epre;
-    int ne = 0;
-    for (size_t i = 0; i < d.size(); ++i) { epre.push_back(ne); ne += (ks[i] > 1) ? d[i].m * d[i].n : 0; }
     // elements of unsplit problems are skipped inside the kernel; number only the split ones
     std::vector<GemmD<R>> ds2;
     std::vector<int> ks2, ep2;

@@ -112,6 +112,8 @@ bool gemm_tc_enabled();
 int gemm_tc_run(const std::vector<GemmD<float>>& d, int cls, Arena& ar, cudaStream_t st,
                 void* (*stage)(void*, const void*, size_t), void* ctx);
 int gemm_tc_error(bool reset);
+// Number of shape classes the GEMM autotuner has measured in this process.
+int gemm_tune_entries();
 
 template <typename R> class Ops {
  public:
@@ -156,6 +158,8 @@ template <typename R> class Ops {
 
  private:
   void gemm_class(const std::vector<GemmD<R>>& d, int cls);   // one operand-layout class
+  int gemm_pick(const std::vector<GemmD<R>>& d, int cls);     // kernel kind: static rule or autotuner
+  void gemm_run(const std::vector<GemmD<R>>& d, int cls, int kind);
   template <typename D> D* upload(const std::vector<D>& v);
   void* stage(const void* src, size_t bytes);
   cudaStream_t st_;

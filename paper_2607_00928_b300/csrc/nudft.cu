@@ -107,6 +107,47 @@ __global__ void k_rowdot(const double2* __restrict__ A, int lda, const double2* 
   out[(size_t)j + (size_t)q * ldo] = acc;
 }
 
+// out(j, q) -= sum_k A(j, k) T(j, k + q nk) with FP32 operands and sum, subtracted in FP64
+__global__ void k_rowdot_sub32(const float2* __restrict__ A, int lda, const float2* __restrict__ T, int ldt, int M,
+                               int nk, int nrhs, double2* __restrict__ out, int ldo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (j >= M || q >= nrhs) return;
+  float2 acc = make_float2(0.f, 0.f);
+  const float2* Tq = T + (size_t)q * nk * ldt;
+  for (int k = 0; k < nk; ++k) cfma(acc, A[(size_t)j + (size_t)k * lda], Tq[(size_t)j + (size_t)k * ldt]);
+  double2& o = out[(size_t)j + (size_t)q * ldo];
+  o = make_double2(o.x - (double)acc.x, o.y - (double)acc.y);
+}
+
+void rowdot_sub32(cudaStream_t st, const float2* A, int lda, const float2* T, int ldt, int M, int nk, int nrhs,
+                  double2* out, int ldo) {
+  if (M <= 0 || nrhs <= 0) return;
+  dim3 grid((M + 255) / 256, nrhs);
+  k_rowdot_sub32<<<grid, 256, 0, st>>>(A, lda, T, ldt, M, nk, nrhs, out, ldo);
+  NH_LAUNCH_CK();
+}
+
+// Z(j, k + q n) = (FP32) f(j, q) * conj(A(j, k))
+__global__ void k_scale_rows_conj32(const float2* __restrict__ A, int lda, const double2* __restrict__ f, int ldf,
+                                    int M, int n, float2* __restrict__ Z, int ldz) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (j >= M) return;
+  const double2 fd = f[(size_t)j + (size_t)q * ldf];
+  const float2 fj = make_float2((float)fd.x, (float)fd.y);
+  float2* Zq = Z + (size_t)q * n * ldz;
+  for (int k = 0; k < n; ++k) Zq[(size_t)j + (size_t)k * ldz] = fj * conj(A[(size_t)j + (size_t)k * lda]);
+}
+
+void scale_rows_conj32(cudaStream_t st, const float2* A, int lda, const double2* f, int ldf, int M, int n, int nrhs,
+                       float2* Z, int ldz) {
+  if (M <= 0 || nrhs <= 0) return;
+  dim3 grid((M + 255) / 256, nrhs);
+  k_scale_rows_conj32<<<grid, 256, 0, st>>>(A, lda, f, ldf, M, n, Z, ldz);
+  NH_LAUNCH_CK();
+}
+
 void rowdot(cudaStream_t st, const double2* A, int lda, const double2* T, int ldt, int M, int nk, int nrhs,
             double2* out, int ldo) {
   if (M <= 0 || nrhs <= 0) return;

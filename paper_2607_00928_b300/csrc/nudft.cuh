@@ -18,6 +18,12 @@ void twiddle_table(cudaStream_t st, const double* x, int M, int n, double2* tab)
 // out_j(q) = sum_k A(j, k) T(j, k) for every column q of T (T has M rows, nk cols per column block)
 void rowdot(cudaStream_t st, const double2* A, int lda, const double2* T, int ldt, int M, int nk, int nrhs,
             double2* out, int ldo);
+// out(j, q) -= sum_k A(j, k) T(j, k + q nk): FP32 operands and sum, subtracted from the FP64 out
+void rowdot_sub32(cudaStream_t st, const float2* A, int lda, const float2* T, int ldt, int M, int nk, int nrhs,
+                  double2* out, int ldo);
+// Z(j, k + q n) = (FP32) f(j, q) * conj(A(j, k)) for k < n, q < nrhs
+void scale_rows_conj32(cudaStream_t st, const float2* A, int lda, const double2* f, int ldf, int M, int n, int nrhs,
+                       float2* Z, int ldz);
 // Z(j, k) = f_j * conj(A(j, k)) for k < n
 void scale_rows_conj(cudaStream_t st, const double2* A, int lda, const double2* f, int M, int n, double2* Z,
                      int ldz);

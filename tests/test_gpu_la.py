@@ -160,3 +160,20 @@ def test_gemm_tensor_cores_3xtf32(nh, m, n, k, batch, ops):
     out = nh.la_gemm(A.cuda(), B.cuda(), opa, opb, alpha=-1.5, beta=0.5, C=C.cuda()).cpu().to(torch.complex128)
     err = (out - ref).abs().max().item()
     assert err < 20 * 2.0 ** -24 * (1.5 * 4 * np.sqrt(k) + 1) * max(1.0, float(ref.abs().max()))
+
+
+def test_gemm_autotuner_measures_shape_classes(nh):
+    """A mixed-precision build runs its FP32 products through the autotuner: shape classes get
+    measured (kernel choice cached per class), and the refined solve still meets the 1e-8 target."""
+    import oracle as orc
+    from synthetic import WORKLOADS, make_workload
+    w = WORKLOADS["mixed_n64"]
+    x, y, ct = make_workload(w)
+    f = orc.forward(x, y, ct[:, :2], w.nx, w.ny)
+    h = nh.NudftHSS(torch.from_numpy(x), torch.from_numpy(y), w.nx, w.ny, eps=1e-6, levels=w.levels, prec="mixed",
+                    refine_tol=1e-10, refine_max=10).factor()
+    c = h.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    info = h.info()
+    h.close()
+    assert info["gemm_tuned"] > 0
+    assert np.max(np.linalg.norm(c - ct[:, :2], axis=0) / np.linalg.norm(ct[:, :2], axis=0)) < 1e-8

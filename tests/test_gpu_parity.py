@@ -195,6 +195,9 @@ def test_repeated_solves_replay_the_captured_graph(nh, prec):
     assert relerr_cols(c2, c1) < 1e-13
     assert relerr_cols(c4, c3) < 1e-13
     assert relerr_cols(c3, ct[:, :1]) < 1e-8
+    info = h.info()
+    assert info["solve_graphs"] == 2 and info["solve_graph_failures"] == 0
+    assert info["solve_replays"] >= 2
     h.close()
 
 
@@ -247,3 +250,25 @@ def test_oversampled_uniform_grid_on_bin_boundaries(nh):
     c = to_np(h.solve(torch.from_numpy(f)))
     h.close()
     assert relerr_cols(c, orc.adjoint(x, y, f, n, n) / x.size) < 1e-10
+
+
+def test_mixed_refinement_incremental_residual(nh):
+    """MIXED refinement: the default (first residual from the exact FP64 apply, later ones updated
+    by the FP32 exact apply of the small correction) reaches the same solution as an FP64 residual
+    at every step, to the 1e-8 target, with less FP64 apply time."""
+    w = WORKLOADS["mixed_n64"]
+    x, y, ct = make_workload(w)
+    f = orc.forward(x, y, ct[:, :4], w.nx, w.ny)
+    out = {}
+    for full in (False, True):
+        h = nh.NudftHSS(x, y, w.nx, w.ny, eps=1e-6, levels=w.levels, prec="mixed", refine_tol=1e-11,
+                        refine_max=12, profile=True, fp64_residuals=full).factor()
+        c = to_np(h.solve(torch.from_numpy(f)))
+        out[full] = (c, h.info(), h.kstats())
+        h.close()
+    for full in (False, True):
+        c, info, _ = out[full]
+        assert relerr_cols(c, ct[:, :4]) < 1e-9
+        assert info["refine_relres"] <= 1e-11
+    fp64_ms = {full: sum(v["ms"] for k, v in out[full][2].items() if k.endswith("_fp64")) for full in (False, True)}
+    assert fp64_ms[False] < fp64_ms[True]
