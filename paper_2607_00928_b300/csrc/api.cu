@@ -213,9 +213,12 @@ template <typename R> static void hss_solve_lex(nudft2_hss_s* h, Hss<R>& H, cons
     G = g.get();
     gm[s] = std::move(g);
     convert_gather<double, R>(h->st, f, (int)ldf, h->pl.perm2, M, s, G->f2, M, 1.0);
+    H.ops().reset_staged();
     H.solve(G->f2, M, s, G->yt, N);            // ordinary run: result used, arenas sized
     convert_scatter<R, double>(h->st, G->yt, N, h->pl.colmap, N, s, ylex, N, 1.0);
-    // capture the sweeps for the next calls
+    // capture the sweeps for the next calls; their descriptor copies come from pinned memory that
+    // lives with the graph, reserved here (no allocation is allowed during the capture)
+    G->pool.reserve(H.ops().staged() * 2 + 65536);
     const bool prof = H.ops().prof.on;
     H.ops().prof.on = false;
     H.ops().set_capture(&G->pool);

@@ -128,6 +128,14 @@ class Arena {
       }
     }
     if (frozen_) throw Error(ST_ENOMEM, "arena is frozen during graph capture and has no room left");
+    // Every chunk from the stack top on was tried and none fits.  Trailing chunks that hold
+    // nothing (used == 0: all their allocations were released) are handed back before growing, so
+    // that scratch of varying large sizes does not pile up as dedicated chunks.  The frees are
+    // stream-ordered: work still queued on the memory completes first.
+    while (!chunks_.empty() && chunks_.back().used == 0) {
+      cudaFreeAsync(chunks_.back().p, st_);
+      chunks_.pop_back();
+    }
     size_t sz = bytes > chunk_ ? bytes : chunk_;
     void* p = nullptr;
     NH_CK(cudaMallocAsync(&p, sz, st_));
@@ -183,10 +191,27 @@ class Arena {
 
 // Pinned host memory that stays valid as long as the object lives: descriptors uploaded while a
 // CUDA graph is captured are copied from here at every replay.
+// Allocating pinned memory is not allowed while a stream is being captured, so reserve() takes
+// one block up front (outside the capture) and alloc() sub-allocates from it; only when the
+// reservation is used up does alloc() fall back to a fresh cudaMallocHost.
 class PinnedPool {
  public:
   ~PinnedPool() { for (void* p : blocks_) cudaFreeHost(p); }
+  void reserve(size_t bytes) {
+    void* p = nullptr;
+    NH_CK(cudaMallocHost(&p, bytes > 0 ? bytes : 1));
+    blocks_.push_back(p);
+    base_ = (char*)p;
+    cap_ = bytes;
+    off_ = 0;
+  }
   void* alloc(size_t bytes) {
+    bytes = (bytes + 15) & ~(size_t)15;
+    if (base_ && off_ + bytes <= cap_) {
+      void* p = base_ + off_;
+      off_ += bytes;
+      return p;
+    }
     void* p = nullptr;
     NH_CK(cudaMallocHost(&p, bytes > 0 ? bytes : 1));
     blocks_.push_back(p);
@@ -194,6 +219,8 @@ class PinnedPool {
   }
  private:
   std::vector<void*> blocks_;
+  char* base_ = nullptr;
+  size_t cap_ = 0, off_ = 0;
 };
 
 }  // namespace nh

@@ -333,17 +333,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (r < g.m) {
+          // every load of the 16 columns is issued before the first store, so the C reads of a
+          // beta != 0 update overlap instead of waiting out one memory latency per column
+          float2* cp = g.C + (size_t)r + (size_t)(col0 + c0) * g.ldc;
+          const int nc = min(16, g.n - col0 - c0);
+          float2 old[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) old[j] = (g.beta != 0.f && j < nc) ? cp[(size_t)j * g.ldc] : make_float2(0.f, 0.f);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int cc = col0 + c0 + j;
-            if (cc >= g.n) break;
+            if (j >= nc) break;
             float2 acc = make_float2(0.f, 0.f);
             if (NCH > 0) acc = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
             if (NCH > 1) acc = make_float2(acc.x + __uint_as_float(tr[j]), acc.y + __uint_as_float(ti[j]));
-            float2* cp = g.C + (size_t)r + (size_t)cc * g.ldc;
-            float2 v = g.alpha * acc;
-            if (g.beta != 0.f) v = v + g.beta * (*cp);
-            *cp = v;
+            cp[(size_t)j * g.ldc] = g.alpha * acc + g.beta * old[j];
           }
         }
       }

@@ -37,6 +37,7 @@ __device__ __forceinline__ int find_prob(const int* pre, int n, int t) {
 
 template <typename R> void* Ops<R>::stage(const void* src, size_t bytes) {
   void* d = ar_->alloc(bytes);
+  staged_ += (bytes + 15) & ~(size_t)15;
   const void* from = src;
   if (pool_) {                      // graph capture: copy from memory that outlives the graph
     void* h = pool_->alloc(bytes);
@@ -212,18 +213,21 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmD<R>* __restrict__ ds, c
     }
     return;
   }
+  // per output row: all loads of a beta != 0 update are issued before the stores, so they overlap
 #pragma unroll
   for (int a = 0; a < TM; ++a) {
     const int i = row0 + ty + 16 * a;
     if (i >= g.m) continue;
+    cplx<R> old[TN];
 #pragma unroll
     for (int b = 0; b < TN; ++b) {
       const int j = col0 + tx + 16 * b;
-      if (j >= g.n) continue;
-      cplx<R>* c = g.C + (size_t)i + (size_t)j * g.ldc;
-      cplx<R> v = g.alpha * acc[a][b];
-      if (g.beta != R(0)) v = v + g.beta * (*c);
-      *c = v;
+      old[b] = (g.beta != R(0) && j < g.n) ? g.C[(size_t)i + (size_t)j * g.ldc] : czero<R>();
+    }
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int j = col0 + tx + 16 * b;
+      if (j < g.n) g.C[(size_t)i + (size_t)j * g.ldc] = g.alpha * acc[a][b] + g.beta * old[b];
     }
   }
 }
@@ -305,10 +309,10 @@ template <typename R> static int gemm_heuristic(const std::vector<GemmD<R>>& d) 
 }
 
 // Autotuner.  Key: precision, layout class, and log2 buckets of the largest m, n, k and of the
-// problem count of the batch.  The first batch with a new key runs every candidate kernel twice
-// on scratch outputs (beta = 0) and keeps the fastest second run; later batches with the key use
-// that kernel.  The cache lives for the process (NH_AUTOTUNE=0 turns tuning off and leaves the
-// static rule).  No tuning happens while the stream is being captured into a graph.
+// problem count of the batch.  The first batch of at least 4 GFLOP with a new key runs every
+// candidate kernel twice on scratch outputs (beta = 0) and keeps the fastest second run; later
+// batches with the key use that kernel.  The cache lives for the process (NH_AUTOTUNE=0 turns
+// tuning off and leaves the static rule).  No tuning happens while the stream is being captured.
 namespace {
 struct TuneKey {
   int prec, cls, lm, ln, lk, lb;
@@ -335,7 +339,15 @@ template <typename R> int Ops<R>::gemm_pick(const std::vector<GemmD<R>>& d, int 
   if constexpr (sizeof(R) == 8) return h;   // one FP64 kernel
   if (pool_ || !autotune_enabled()) return h;
   int mx = 0, nx = 0, kx = 0;
-  for (const auto& g : d) { mx = std::max(mx, g.m); nx = std::max(nx, g.n); kx = std::max(kx, g.k); }
+  double fl = 0, out_bytes = 0;
+  for (const auto& g : d) {
+    mx = std::max(mx, g.m); nx = std::max(nx, g.n); kx = std::max(kx, g.k);
+    fl += 8.0 * g.m * g.n * std::max(g.k, 0);
+    out_bytes += (double)g.m * g.n * sizeof(cplx<R>);
+  }
+  // only batches where the choice matters are measured (at least 4 GFLOP), and only when the
+  // scratch outputs stay modest; the rest follow the static rule
+  if (fl < 4e9 || out_bytes > 4e9) return h;
   const TuneKey key{(int)sizeof(R), cls, ilog2c(mx), ilog2c(nx), ilog2c(kx), ilog2c((int)d.size())};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

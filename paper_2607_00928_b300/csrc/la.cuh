@@ -151,6 +151,9 @@ template <typename R> class Ops {
   void count(int n = 1) { launches_ += n; }
   // Capture mode: host->device descriptor copies are staged in `pool` (kept alive with the graph).
   void set_capture(PinnedPool* pool) { pool_ = pool; }
+  // host bytes staged to the device since the last reset (sizes the pinned pool of a capture)
+  void reset_staged() { staged_ = 0; }
+  size_t staged() const { return staged_; }
   int* upload_ints(const std::vector<int>& v);
   // host -> device copy of bytes into the scratch arena (capture-safe), for launchers outside
   // this class; ctx is the Ops object
@@ -165,6 +168,7 @@ template <typename R> class Ops {
   cudaStream_t st_;
   Arena* ar_;
   PinnedPool* pool_ = nullptr;
+  size_t staged_ = 0;
   int launches_ = 0;
 };
 

@@ -110,8 +110,9 @@ def batched_uneven(count: int = 64, seed: int = 100, sizes=BATCH_SIZES, nrhs: in
                    ratio=(1.5, 4.0), theta=(-0.25, 0.35)):
     """Independent problems of uneven size (the batched workload): problem p draws n_x, n_y
     uniformly from `sizes` and an oversampling rho ~ U[ratio] from seed + p, then takes a
-    jittered m_x x m_y grid with m_x = ceil(n_x sqrt(rho)), m_y = ceil(n_y sqrt(rho)) (so
-    M ~ rho N >= N) and theta ~ U[theta], plus nrhs iid complex normal coefficient columns.
+    jittered m_x x m_y grid with m_x = round(n_x sqrt(rho)), m_y = round(n_y sqrt(rho)) (so
+    M ~ rho N, and M > N since rho >= 1.5) and theta ~ U[theta], plus nrhs iid complex normal
+    coefficient columns.
     Returns a list of dicts with nx, ny, x, y, c_true (N x nrhs, lexicographic ky + kx*ny)."""
     out = []
     for p in range(count):
@@ -119,8 +120,8 @@ def batched_uneven(count: int = 64, seed: int = 100, sizes=BATCH_SIZES, nrhs: in
         nx = int(rng.choice(sizes))
         ny = int(rng.choice(sizes))
         rho = float(rng.uniform(*ratio))
-        mx = int(np.ceil(nx * np.sqrt(rho)))
-        my = int(np.ceil(ny * np.sqrt(rho)))
+        mx = int(np.round(nx * np.sqrt(rho)))
+        my = int(np.round(ny * np.sqrt(rho)))
         x, y = jittered_grid(mx, my, theta[0], theta[1], seed + p + 10_000)
         c = complex_normal((nx * ny, nrhs), seed + p + 20_000)
         out.append({"nx": nx, "ny": ny, "x": x, "y": y, "c_true": c, "rho": rho})

@@ -70,3 +70,29 @@ def test_batched_names_the_failing_problem(nh):
     with pytest.raises(nh.NudftError) as e:
         nh.build_batched(ps, threads=3)
     assert "problem 1" in str(e.value)
+
+
+def test_config4_full_size_batch(nh):
+    """The batched workload at its full size: 64 problems, n_x, n_y in {32, ..., 256}, M/N in
+    [1.5, 4], 8 right-hand sides each, built, factored and solved together in mixed precision
+    refined to 1e-8.  Every problem recovers its c_true (consistent data) to the 1e-8 target, and
+    the oracle's direct sum confirms the data of the largest problem at sampled points."""
+    from synthetic import batched_uneven
+    ps = batched_uneven()
+    for p in ps:
+        p.update(eps=1e-6, prec="mixed", refine_tol=1e-8, refine_max=10)
+    fs = []
+    for p in ps:
+        ct = torch.from_numpy(p["c_true"]).cuda()
+        fs.append(nh.exact_apply(torch.from_numpy(p["x"]).cuda(), torch.from_numpy(p["y"]).cuda(), p["nx"], p["ny"],
+                                 nh.EXACT_FWD, ct))
+    big = max(range(len(ps)), key=lambda i: ps[i]["nx"] * ps[i]["ny"])
+    idx = np.random.default_rng(4).choice(ps[big]["x"].size, 16, replace=False)
+    ref = orc.forward(ps[big]["x"][idx], ps[big]["y"][idx], ps[big]["c_true"], ps[big]["nx"], ps[big]["ny"])
+    assert np.max(np.abs(fs[big].cpu().numpy()[idx] - ref)) < 1e-10 * np.max(np.abs(ref))
+    hs = nh.build_batched(ps, threads=16)
+    cs = nh.solve_batched(hs, fs, threads=16)
+    for p, c in zip(ps, cs):
+        assert _relcols(c.cpu().numpy(), p["c_true"]) < 1e-8
+    for h in hs:
+        h.close()

@@ -11,7 +11,9 @@ def test_batched_uneven_recipe():
         assert p["nx"] in BATCH_SIZES and p["ny"] in BATCH_SIZES
         N, M = p["nx"] * p["ny"], p["x"].size
         assert 1.5 <= p["rho"] <= 4.0
-        assert M >= p["rho"] * N * 0.999 and M <= (np.sqrt(p["rho"]) * p["nx"] + 1) * (np.sqrt(p["rho"]) * p["ny"] + 1)
+        r = np.sqrt(p["rho"])
+        assert M > N
+        assert (r * p["nx"] - 0.5) * (r * p["ny"] - 0.5) <= M <= (r * p["nx"] + 0.5) * (r * p["ny"] + 0.5)
         assert np.all((p["x"] >= 0) & (p["x"] < 1) & (p["y"] >= 0) & (p["y"] < 1))
         assert p["c_true"].shape == (N, 8)
     # uneven: several distinct shapes, and the recipe is reproducible
