@@ -101,6 +101,7 @@ typedef struct {
   int solve_graphs;          /* URV solves captured into CUDA graphs (one per RHS count) */
   int solve_graph_failures;  /* captures that failed (those solves run uncaptured)     */
   int solve_replays;         /* solves run by replaying a captured graph               */
+  int checkpointed_levels;   /* top levels whose factors are handed back (0 = none)    */
 } nudft2_info;
 
 /* Build the HSS approximation of G~ = A F^{-1} (Alg. 1 steps 1-3, Sec. 3 and Sec. 2.2).
@@ -190,6 +191,16 @@ nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const v
  * Errors: ESTATE (not factored), EINVAL. */
 nudft2_status nudft2_hss_plsqr(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
                                double tol, int maxit, int* iters, double* relres, void* stream);
+
+/* Per-level checkpointing of the URV factors (Sec. 2.3 storage; not in the paper): hand back the
+ * device memory of the factors of the top `levels` tree levels and of the root (levels >= L: all
+ * of them), keeping the HSS generators and the factors of the levels below.  The next call that
+ * needs the factorization (solve, PINV / PINV_ADJ apply, grad, plsqr) recomputes the handed-back
+ * levels first, level by level from the kept ones: the same factors, bit for bit, at the cost of
+ * factoring those levels again.  The top levels hold most of the factor memory (their blocks are
+ * O(sqrt(N)) wide), so this is the memory/time trade of a backward pass that keeps a handle
+ * between its forward solve and its adjoint.  Errors: ESTATE (not factored), EINVAL. */
+nudft2_status nudft2_hss_checkpoint(nudft2_hss_t h, int levels, void* stream);
 
 /* Statistics of the handle (ranks, stage times, memory).  Errors: EINVAL (NULL). */
 nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info);

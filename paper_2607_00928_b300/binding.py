@@ -32,7 +32,8 @@ class Info(ctypes.Structure):
                 ("t_build_ms", ctypes.c_double), ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("refine_iters", ctypes.c_int), ("refine_relres", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int), ("gemm_tuned", ctypes.c_int),
-                ("solve_graphs", ctypes.c_int), ("solve_graph_failures", ctypes.c_int), ("solve_replays", ctypes.c_int)]
+                ("solve_graphs", ctypes.c_int), ("solve_graph_failures", ctypes.c_int), ("solve_replays", ctypes.c_int),
+                ("checkpointed_levels", ctypes.c_int)]
 
 
 class KStat(ctypes.Structure):
@@ -87,11 +88,12 @@ def lib() -> ctypes.CDLL:
     L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_peak_fma.argtypes = [ci, ctypes.POINTER(ctypes.c_double), vp]
+    L.nudft2_hss_checkpoint.argtypes = [vp, ci, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
               "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_plsqr",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
-              "nudft2_exact_fwd_noalloc", "nudft2_peak_fma"):
+              "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -275,6 +277,12 @@ class NudftHSS:
                                       _stream(self.stream)))
         return (c[0] if squeeze else c.t()), it.value, rr.value
 
+    def checkpoint(self, levels: int):
+        """Hand back the factors of the top `levels` levels (and the root); they are recomputed
+        by the next call that needs them."""
+        _check(lib().nudft2_hss_checkpoint(self._h, int(levels), _stream(self.stream)))
+        return self
+
     def info(self) -> dict:
         i = Info()
         _check(lib().nudft2_hss_info(self._h, ctypes.byref(i)))
@@ -283,7 +291,8 @@ class NudftHSS:
                 "t_factor_ms": i.t_factor_ms, "t_solve_ms": i.t_solve_ms, "refine_iters": i.refine_iters,
                 "refine_relres": i.refine_relres, "device_bytes": i.device_bytes, "launches": i.launches,
                 "gemm_tuned": i.gemm_tuned, "solve_graphs": i.solve_graphs,
-                "solve_graph_failures": i.solve_graph_failures, "solve_replays": i.solve_replays}
+                "solve_graph_failures": i.solve_graph_failures, "solve_replays": i.solve_replays,
+                "checkpointed_levels": i.checkpointed_levels}
 
     def kstats(self) -> dict:
         """Per kernel class: device ms, algorithmic flops and bytes, launches (profile=True)."""
@@ -366,8 +375,12 @@ class _Lstsq(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, f, x, y, nx, ny, opts):
+        opts = dict(opts)
+        ck = int(opts.pop("checkpoint_levels", 0))
         h = NudftHSS(x.detach(), y.detach(), nx, ny, **opts).factor()
         c = h.solve(f.detach())
+        if ck > 0:
+            h.checkpoint(ck)      # the backward pass factors these levels again
         ctx.h = h
         ctx.save_for_backward(f, c)
         return c
@@ -383,5 +396,7 @@ class _Lstsq(torch.autograd.Function):
 
 def lstsq(f: torch.Tensor, x: torch.Tensor, y: torch.Tensor, nx: int, ny: int, **opts) -> torch.Tensor:
     """Differentiable c = argmin ||A(x, y) c - f|| (f (M,) or (M, s) complex128 on CUDA; x, y (M,)
-    float64).  opts go to NudftHSS (eps, levels, prec, ...); the handle is built per call."""
+    float64).  opts go to NudftHSS (eps, levels, prec, ...); the handle is built per call.
+    checkpoint_levels=k hands back the factors of the top k levels between the forward solve and
+    the backward pass, which factors them again (less memory held, one partial refactorization)."""
     return _Lstsq.apply(f, x, y, nx, ny, opts)

@@ -277,6 +277,16 @@ static void enter(nudft2_hss_s* h, void* user_stream) {
   NH_CK(cudaStreamWaitEvent(h->st, h->join, 0));
 }
 
+// Recompute factors handed back by nudft2_hss_checkpoint before a call that needs them; captured
+// solve graphs refer to the old factor addresses and are dropped when that happens.
+static void ensure_factors(nudft2_hss_s* h) {
+  const bool changed = h->h64 ? h->h64->ensure_factored() : h->h32->ensure_factored();
+  if (changed) {
+    h->g64.clear();
+    h->g32.clear();
+  }
+}
+
 // ----------------------------------------------------------------------------- LA test hooks
 template <typename R>
 static void la_tsvd(void* d_ct, int w, int r, int ldct, double eps, void* d_p, int ldp, int* rank, double* sig,
@@ -866,6 +876,7 @@ nudft2_status nudft2_hss_solve(nudft2_hss_t h, const void* d_f, int64_t ldf, int
     NH_REQUIRE(nrhs >= 0 && d_f && d_c && ldf >= h->M && ldc >= h->N, ST_EINVAL, "solve: bad arguments");
     enter(h, stream);
     if (nrhs == 0) return;
+    ensure_factors(h);
     const double t0 = now_ms();
     do_solve(h, (const double2*)d_f, ldf, nrhs, (double2*)d_c, ldc);
     NH_CK(cudaStreamSynchronize(h->st));
@@ -893,6 +904,7 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
       case NUDFT2_PINV:
         NH_REQUIRE(h->factored, ST_ESTATE, "apply PINV before factor");
         NH_REQUIRE(ldi >= M && ldo >= N, ST_EINVAL, "apply: leading dimension too small");
+        ensure_factors(h);
         do_solve(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
         break;
       case NUDFT2_FAST_FWD: {
@@ -919,6 +931,7 @@ nudft2_status nudft2_hss_apply(nudft2_hss_t h, int op, const void* d_in, int64_t
       case NUDFT2_PINV_ADJ:
         NH_REQUIRE(h->factored, ST_ESTATE, "apply PINV_ADJ before factor");
         NH_REQUIRE(ldi >= N && ldo >= M, ST_EINVAL, "apply: leading dimension too small");
+        ensure_factors(h);
         do_solve_adj(h, (const double2*)d_in, ldi, nrhs, (double2*)d_out, ldo);
         break;
       case NUDFT2_FAST_ADJ: {
@@ -961,6 +974,7 @@ nudft2_status nudft2_hss_grad(nudft2_hss_t h, const void* d_f, int64_t ldf, cons
                    ((d_gx == nullptr) == (d_gy == nullptr)),
                ST_EINVAL, "grad: bad arguments");
     enter(h, stream);
+    ensure_factors(h);
     auto mk = h->scr.mark();
     // lam = (A^+)^* g  (also the gradient with respect to f)
     double2* lam = d_gf ? (double2*)d_gf : h->scr.arr<double2>((size_t)M * s);
@@ -1007,12 +1021,26 @@ nudft2_status nudft2_hss_plsqr(nudft2_hss_t h, const void* d_f, int64_t ldf, int
     NH_REQUIRE(nrhs >= 1 && d_f && d_c && ldf >= h->M && ldc >= h->N && tol > 0 && maxit >= 1, ST_EINVAL,
                "plsqr: bad arguments");
     enter(h, stream);
+    ensure_factors(h);
     int it = 0;
     double rr = -1;
     do_plsqr(h, (const double2*)d_f, ldf, nrhs, (double2*)d_c, ldc, tol, maxit, &it, &rr);
     NH_CK(cudaStreamSynchronize(h->st));
     if (iters) *iters = it;
     if (relres) *relres = rr;
+  });
+}
+
+nudft2_status nudft2_hss_checkpoint(nudft2_hss_t h, int levels, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr, ST_ESTATE, "checkpoint: no handle");
+    NH_REQUIRE(h->factored, ST_ESTATE, "checkpoint before factor");
+    NH_REQUIRE(levels >= 0, ST_EINVAL, "checkpoint: levels must be >= 0");
+    enter(h, stream);
+    h->g64.clear();            // captured solves refer to the factors handed back here
+    h->g32.clear();
+    if (h->h64) h->h64->checkpoint(levels);
+    else h->h32->checkpoint(levels);
   });
 }
 
@@ -1035,6 +1063,7 @@ nudft2_status nudft2_hss_info(nudft2_hss_t h, nudft2_info* info) {
     info->solve_graphs = h->graphs_ok;
     info->solve_graph_failures = h->graphs_failed;
     info->solve_replays = h->replays;
+    info->checkpointed_levels = h->h64 ? h->h64->dropped_levels() : h->h32->dropped_levels();
   });
 }
 

@@ -37,6 +37,7 @@
 #include <cstring>
 
 #include "la.cuh"
+#include "tc.cuh"
 
 namespace nh {
 
@@ -49,13 +50,6 @@ constexpr int TC_STAGE = 2 * TC_BLK;                       // A block + B block
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE + 1024;       // + alignment slack
 constexpr int TC_THREADS = 192;                            // warps 0-3 drain / epilogue, 4 producer, 5 MMA
 constexpr uint32_t TC_TMEM_COLS = 512;                     // chunk Cr, Ci; total Cr, Ci (128 each)
-constexpr long long TC_SPIN = 1LL << 22;                   // try_wait attempts per wait
-
-// kind::tf32 instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = 128.
-constexpr uint32_t tc_idesc(bool negate_a) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (negate_a ? (1u << 13) : 0u) | ((uint32_t)(TC_BN >> 3) << 17) |
-         ((uint32_t)(TC_BM >> 4) << 24);
-}
 }  // namespace
 
 __device__ int g_tc_error;
@@ -70,16 +64,6 @@ struct PackD {
   int tiles_r, ktiles;
 };
 
-// byte offset of (r, kk) inside one plane of a packed block (no-swizzle K-major core matrices:
-// 8 rows x 16 bytes each; the two core matrices of one 8-row group are adjacent along k)
-__host__ __device__ __forceinline__ uint32_t tc_kmajor(int r, int kk) {
-  return (uint32_t)((r >> 3) * 256 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4);
-}
-
-__device__ __forceinline__ void tc_split(float x, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(x - __uint_as_float(hi)));   // x - hi is exact in FP32
-}
 
 // One CTA of 256 threads per packed block; thread (kq, r) writes row r, k quad kq of each plane
 // as one 16-byte store.
@@ -108,7 +92,7 @@ __global__ void __launch_bounds__(256) k_tc_pack(const PackD* __restrict__ ds, c
     tc_split(v.y, p[2][e], p[3][e]);
   }
   unsigned char* blk = d.out + (size_t)b * (4 * R * TC_BK * 4);
-  const uint32_t off = tc_kmajor(r, kq * 4);
+  const uint32_t off = tc_kmajor(r, kq * 4, 256);   // one packed block: 8 k, so 8-row groups are 256 B apart
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     *reinterpret_cast<uint4*>(blk + q * (R * TC_BK * 4) + off) = make_uint4(p[q][0], p[q][1], p[q][2], p[q][3]);
@@ -122,76 +106,6 @@ struct TcProb {
   int m, n, ldc, ktiles, tiles_m;
   float alpha, beta;
 };
-
-__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// shared-memory matrix descriptor: start address, LBO = 128 B (next core matrix along k),
-// SBO = 256 B (next 8-row group), descriptor version 1, base offset 0, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
-         (1ull << 46);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_expect(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          tc_smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(tc_smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = tc_smem_u32(bar);
-  for (long long it = 0; it < TC_SPIN; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_u32(bar)) : "memory");
-}
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const TcProb* __restrict__ ds, const int* __restrict__ pre, int np) {
@@ -260,7 +174,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 5) {
     if (lane == 0) {
       // MMA issuer: chunk accumulator in columns [0, 256) (Cr, Ci)
-      const uint32_t idp = tc_idesc(false), idn = tc_idesc(true);
+      const uint32_t idp = tc_idesc(TC_BM, TC_BN, false), idn = tc_idesc(TC_BM, TC_BN, true);
       const uint32_t cr = tmem, ci = tmem + TC_BN;
       constexpr uint32_t PL = 128 * TC_BK * 4;   // plane bytes
       for (int kt = 0; kt < KT; ++kt) {
@@ -270,8 +184,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (*abort_v) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a = tc_smem_u32(sm + s * TC_STAGE), b = a + TC_BLK;
-        const uint64_t arh = tc_desc(a), arl = tc_desc(a + PL), aih = tc_desc(a + 2 * PL), ail = tc_desc(a + 3 * PL);
-        const uint64_t brh = tc_desc(b), brl = tc_desc(b + PL), bih = tc_desc(b + 2 * PL), bil = tc_desc(b + 3 * PL);
+        const uint64_t arh = tc_desc(a, 256), arl = tc_desc(a + PL, 256), aih = tc_desc(a + 2 * PL, 256),
+                       ail = tc_desc(a + 3 * PL, 256);
+        const uint64_t brh = tc_desc(b, 256), brl = tc_desc(b + PL, 256), bih = tc_desc(b + 2 * PL, 256),
+                       bil = tc_desc(b + 3 * PL, 256);
         const uint32_t f = kc == 0 ? 0u : 1u;
         tc_mma(cr, arh, brh, idp, f);
         tc_mma(cr, arh, brl, idp, 1u);

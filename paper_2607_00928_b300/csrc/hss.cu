@@ -686,154 +686,160 @@ template <typename R> void Hss<R>::build(double eps) {
 }
 
 // ------------------------------------------------------------------------------- URV factorization (Sec. 2.3)
-template <typename R> void Hss<R>::factor() {
+// The factors of level l (and those of the root) are allocated from their own arena fac_[l]
+// (fac_[0] for the root), so that checkpoint() can hand back the top levels' factors and
+// ensure_factored() can recompute them from the generators and the kept lower-level factors.
+template <typename R> void Hss<R>::factor_level(int l) {
   const int L = pl_->L;
-  for (int l = L; l >= 1; --l) {
-    auto mk = scr_.mark();
-    auto tk = tmp_.mark();
-    const int nn = (int)t_[l].size();
-    // working matrix Wk = [U D] and V for every node of the level
-    std::vector<Mat<R>> Vs(nn);
-    std::vector<CopyD<R>> cp;
-    std::vector<GemmD<R>> gm;
-    for (int p = 0; p < nn; ++p) {
-      Node2<R>& nd = t_[l][p];
-      if (l == L) {
-        nd.m = nd.D.m; nd.n = nd.D.n;
-        nd.Wk = keep_.mat<R>(nd.m, nd.ku + nd.n);
-        cp.push_back({nd.U.p, nd.Wk.p, nd.m, nd.ku, nd.U.ld, nd.Wk.ld, OP_N, R(1), R(0)});
-        cp.push_back({nd.D.p, nd.Wk.at(0, nd.ku), nd.m, nd.n, nd.D.ld, nd.Wk.ld, OP_N, R(1), R(0)});
-        Vs[p] = tmp_.mat<R>(nd.V.m, nd.kv);
-        cp.push_back({nd.V.p, Vs[p].p, nd.V.m, nd.kv, nd.V.ld, Vs[p].ld, OP_N, R(1), R(0)});
-      } else {
-        // merge the children (Sec. 2.3): D+ blocks, U+ = stack U2_c R_c, V+ = stack V2_c W_c
-        int rows = 0, cols = 0;
-        for (int c = 0; c < 4; ++c) { rows += t_[l + 1][4 * p + c].rows2; cols += t_[l + 1][4 * p + c].kv; }
-        nd.m = rows; nd.n = cols;
-        nd.Wk = keep_.mat<R>(rows, nd.ku + cols);
-        Vs[p] = tmp_.mat<R>(cols, nd.kv);
-        int ro = 0;
-        for (int c = 0; c < 4; ++c) {
-          Node2<R>& a = t_[l + 1][4 * p + c];
-          Mat<R> U2 = a.Wk.block(a.n1, 0, a.rows2, a.ku);
-          gm.push_back(gd<R>(U2, OP_N, a.R_, OP_N, nd.Wk.block(ro, 0, a.rows2, nd.ku)));
-          int co = nd.ku;
-          for (int c2 = 0; c2 < 4; ++c2) {
-            Node2<R>& b = t_[l + 1][4 * p + c2];
-            Mat<R> dst = nd.Wk.block(ro, co, a.rows2, b.kv);
-            if (c2 == c) {
-              Mat<R> D22 = a.Wk.block(a.n1, a.ku, a.rows2, a.kv);
-              cp.push_back({D22.p, dst.p, a.rows2, a.kv, D22.ld, dst.ld, OP_N, R(1), R(0)});
-            } else {
-              Mat<R> T1 = tmp_.mat<R>(a.ku, b.kv);
-              gm.push_back(gd<R>(a.B[c2], OP_N, b.V2, OP_C, T1));
-              // second product issued after the first batch completes (ordering below)
-              (void)dst;
-            }
-            co += b.kv;
+  Arena& fa = *fac_[l];
+  auto mk = scr_.mark();
+  auto tk = tmp_.mark();
+  const int nn = (int)t_[l].size();
+  // working matrix Wk = [U D] and V for every node of the level
+  std::vector<Mat<R>> Vs(nn);
+  std::vector<CopyD<R>> cp;
+  std::vector<GemmD<R>> gm;
+  for (int p = 0; p < nn; ++p) {
+    Node2<R>& nd = t_[l][p];
+    if (l == L) {
+      nd.m = nd.D.m; nd.n = nd.D.n;
+      nd.Wk = fa.template mat<R>(nd.m, nd.ku + nd.n);
+      cp.push_back({nd.U.p, nd.Wk.p, nd.m, nd.ku, nd.U.ld, nd.Wk.ld, OP_N, R(1), R(0)});
+      cp.push_back({nd.D.p, nd.Wk.at(0, nd.ku), nd.m, nd.n, nd.D.ld, nd.Wk.ld, OP_N, R(1), R(0)});
+      Vs[p] = tmp_.mat<R>(nd.V.m, nd.kv);
+      cp.push_back({nd.V.p, Vs[p].p, nd.V.m, nd.kv, nd.V.ld, Vs[p].ld, OP_N, R(1), R(0)});
+    } else {
+      // merge the children (Sec. 2.3): D+ blocks, U+ = stack U2_c R_c, V+ = stack V2_c W_c
+      int rows = 0, cols = 0;
+      for (int c = 0; c < 4; ++c) { rows += t_[l + 1][4 * p + c].rows2; cols += t_[l + 1][4 * p + c].kv; }
+      nd.m = rows; nd.n = cols;
+      nd.Wk = fa.template mat<R>(rows, nd.ku + cols);
+      Vs[p] = tmp_.mat<R>(cols, nd.kv);
+      int ro = 0;
+      for (int c = 0; c < 4; ++c) {
+        Node2<R>& a = t_[l + 1][4 * p + c];
+        Mat<R> U2 = a.Wk.block(a.n1, 0, a.rows2, a.ku);
+        gm.push_back(gd<R>(U2, OP_N, a.R_, OP_N, nd.Wk.block(ro, 0, a.rows2, nd.ku)));
+        int co = nd.ku;
+        for (int c2 = 0; c2 < 4; ++c2) {
+          Node2<R>& b = t_[l + 1][4 * p + c2];
+          Mat<R> dst = nd.Wk.block(ro, co, a.rows2, b.kv);
+          if (c2 == c) {
+            Mat<R> D22 = a.Wk.block(a.n1, a.ku, a.rows2, a.kv);
+            cp.push_back({D22.p, dst.p, a.rows2, a.kv, D22.ld, dst.ld, OP_N, R(1), R(0)});
+          } else {
+            Mat<R> T1 = tmp_.mat<R>(a.ku, b.kv);
+            gm.push_back(gd<R>(a.B[c2], OP_N, b.V2, OP_C, T1));
+            // second product issued after the first batch completes (ordering below)
+            (void)dst;
           }
-          ro += a.rows2;
+          co += b.kv;
         }
-        int vo = 0;
-        for (int c = 0; c < 4; ++c) {
-          Node2<R>& a = t_[l + 1][4 * p + c];
-          gm.push_back(gd<R>(a.V2, OP_N, a.W, OP_N, Vs[p].block(vo, 0, a.kv, nd.kv)));
-          vo += a.kv;
-        }
+        ro += a.rows2;
+      }
+      int vo = 0;
+      for (int c = 0; c < 4; ++c) {
+        Node2<R>& a = t_[l + 1][4 * p + c];
+        gm.push_back(gd<R>(a.V2, OP_N, a.W, OP_N, Vs[p].block(vo, 0, a.kv, nd.kv)));
+        vo += a.kv;
       }
     }
-    ops_.copy(cp);
-    if (l < L) {
-      // gm holds: U+ products, T1 = B V2^*, V+ products.  Run them, then Wk blocks = U2 T1.
-      ops_.gemm(gm);
-      std::vector<GemmD<R>> g2;
-      // recompute the T1 pointers in the same order as allocated above
-      for (int p = 0, gi = 0; p < nn; ++p) {
-        Node2<R>& nd = t_[l][p];
-        int ro = 0;
-        for (int c = 0; c < 4; ++c) {
-          Node2<R>& a = t_[l + 1][4 * p + c];
-          gi++;   // U+ product
-          int co = nd.ku;
-          for (int c2 = 0; c2 < 4; ++c2) {
-            Node2<R>& b = t_[l + 1][4 * p + c2];
-            if (c2 != c) {
-              const GemmD<R>& t1 = gm[gi++];
-              Mat<R> T1;
-              T1.p = t1.C; T1.m = a.ku; T1.n = b.kv; T1.ld = t1.ldc;
-              Mat<R> U2 = a.Wk.block(a.n1, 0, a.rows2, a.ku);
-              g2.push_back(gd<R>(U2, OP_N, T1, OP_N, nd.Wk.block(ro, co, a.rows2, b.kv)));
-            }
-            co += b.kv;
-          }
-          ro += a.rows2;
-        }
-        gi += 4;   // V+ products
-      }
-      ops_.gemm(g2);
-    }
-    // 1. size reduction: QR of [U D] when m >= n + ku
-    std::vector<Mat<R>> Aq;
-    std::vector<int> qi;
-    for (int p = 0; p < nn; ++p) {
-      Node2<R>& nd = t_[l][p];
-      nd.omega = nd.m >= nd.n + nd.ku;
-      nd.mc = nd.omega ? nd.n + nd.ku : nd.m;
-      if (nd.omega) { Aq.push_back(nd.Wk); qi.push_back(p); }
-    }
-    if (!Aq.empty()) {
-      auto Q = ops_.qr(Aq, keep_);
-      ops_.group_wy(Q, keep_);
-      for (size_t i = 0; i < qi.size(); ++i) t_[l][qi[i]].Om = Q[i];
-    }
-    // 2. basis elimination: V = Q_v [V2; 0] (standard QR; columns of D Q_v reordered so the
-    //    eliminated block comes first, Sec. 2.3 Eq. for basis elimination)
-    {
-      auto Q = ops_.qr(Vs, keep_);
-      ops_.group_wy(Q, keep_);
-      std::vector<CopyD<R>> c2;
-      std::vector<Mat<R>> Dc;
-      for (int p = 0; p < nn; ++p) {
-        Node2<R>& nd = t_[l][p];
-        NH_REQUIRE(nd.kv <= nd.n, ST_ERANK, "column basis wider than the node");
-        nd.Qv = Q[p];
-        nd.V2 = keep_.mat<R>(nd.kv, nd.kv);
-        c2.push_back({Vs[p].p, nd.V2.p, nd.kv, nd.kv, Vs[p].ld, nd.V2.ld, OP_N, R(1), R(0)});
-        Dc.push_back(nd.Wk.block(0, nd.ku, nd.mc, nd.n));
-      }
-      ops_.copy(c2);
-      // 3. D~ = D Q_v
-      ops_.apply_q_right(Q, Dc, false);
-    }
-    // 4. partial decomposition: QR of the eliminated columns D~[:, kv:n]
-    {
-      std::vector<Mat<R>> A1, A2;
-      for (int p = 0; p < nn; ++p) {
-        Node2<R>& nd = t_[l][p];
-        nd.n1 = nd.n - nd.kv;
-        NH_REQUIRE(nd.mc >= nd.n1, ST_ERANK, "node has fewer rows than eliminated columns");
-        nd.rows2 = nd.mc - nd.n1;
-        A1.push_back(nd.Wk.block(0, nd.ku + nd.kv, nd.mc, nd.n1));
-        A2.push_back(nd.Wk.block(0, 0, nd.mc, nd.ku + nd.kv));
-      }
-      auto Q = ops_.qr(A1, keep_);
-      ops_.group_wy(Q, keep_);
-      for (int p = 0; p < nn; ++p) t_[l][p].P = Q[p];
-      // [U1; U2], [D12; D22] = P^* [U D~2]
-      ops_.apply_q_left(Q, A2, true);
-      // D11^{-1}
-      std::vector<Mat<R>> T, X;
-      for (int p = 0; p < nn; ++p) {
-        Node2<R>& nd = t_[l][p];
-        nd.D11inv = keep_.mat<R>(nd.n1, nd.n1);
-        T.push_back(nd.Wk.block(0, nd.ku + nd.kv, nd.n1, nd.n1));
-        X.push_back(nd.D11inv);
-      }
-      ops_.trinv(T, X);
-    }
-    tmp_.release(tk);
-    scr_.release(mk);
   }
+  ops_.copy(cp);
+  if (l < L) {
+    // gm holds: U+ products, T1 = B V2^*, V+ products.  Run them, then Wk blocks = U2 T1.
+    ops_.gemm(gm);
+    std::vector<GemmD<R>> g2;
+    // recompute the T1 pointers in the same order as allocated above
+    for (int p = 0, gi = 0; p < nn; ++p) {
+      Node2<R>& nd = t_[l][p];
+      int ro = 0;
+      for (int c = 0; c < 4; ++c) {
+        Node2<R>& a = t_[l + 1][4 * p + c];
+        gi++;   // U+ product
+        int co = nd.ku;
+        for (int c2 = 0; c2 < 4; ++c2) {
+          Node2<R>& b = t_[l + 1][4 * p + c2];
+          if (c2 != c) {
+            const GemmD<R>& t1 = gm[gi++];
+            Mat<R> T1;
+            T1.p = t1.C; T1.m = a.ku; T1.n = b.kv; T1.ld = t1.ldc;
+            Mat<R> U2 = a.Wk.block(a.n1, 0, a.rows2, a.ku);
+            g2.push_back(gd<R>(U2, OP_N, T1, OP_N, nd.Wk.block(ro, co, a.rows2, b.kv)));
+          }
+          co += b.kv;
+        }
+        ro += a.rows2;
+      }
+      gi += 4;   // V+ products
+    }
+    ops_.gemm(g2);
+  }
+  // 1. size reduction: QR of [U D] when m >= n + ku
+  std::vector<Mat<R>> Aq;
+  std::vector<int> qi;
+  for (int p = 0; p < nn; ++p) {
+    Node2<R>& nd = t_[l][p];
+    nd.omega = nd.m >= nd.n + nd.ku;
+    nd.mc = nd.omega ? nd.n + nd.ku : nd.m;
+    if (nd.omega) { Aq.push_back(nd.Wk); qi.push_back(p); }
+  }
+  if (!Aq.empty()) {
+    auto Q = ops_.qr(Aq, fa);
+    ops_.group_wy(Q, fa);
+    for (size_t i = 0; i < qi.size(); ++i) t_[l][qi[i]].Om = Q[i];
+  }
+  // 2. basis elimination: V = Q_v [V2; 0] (standard QR; columns of D Q_v reordered so the
+  //    eliminated block comes first, Sec. 2.3 Eq. for basis elimination)
+  {
+    auto Q = ops_.qr(Vs, fa);
+    ops_.group_wy(Q, fa);
+    std::vector<CopyD<R>> c2;
+    std::vector<Mat<R>> Dc;
+    for (int p = 0; p < nn; ++p) {
+      Node2<R>& nd = t_[l][p];
+      NH_REQUIRE(nd.kv <= nd.n, ST_ERANK, "column basis wider than the node");
+      nd.Qv = Q[p];
+      nd.V2 = fa.template mat<R>(nd.kv, nd.kv);
+      c2.push_back({Vs[p].p, nd.V2.p, nd.kv, nd.kv, Vs[p].ld, nd.V2.ld, OP_N, R(1), R(0)});
+      Dc.push_back(nd.Wk.block(0, nd.ku, nd.mc, nd.n));
+    }
+    ops_.copy(c2);
+    // 3. D~ = D Q_v
+    ops_.apply_q_right(Q, Dc, false);
+  }
+  // 4. partial decomposition: QR of the eliminated columns D~[:, kv:n]
+  {
+    std::vector<Mat<R>> A1, A2;
+    for (int p = 0; p < nn; ++p) {
+      Node2<R>& nd = t_[l][p];
+      nd.n1 = nd.n - nd.kv;
+      NH_REQUIRE(nd.mc >= nd.n1, ST_ERANK, "node has fewer rows than eliminated columns");
+      nd.rows2 = nd.mc - nd.n1;
+      A1.push_back(nd.Wk.block(0, nd.ku + nd.kv, nd.mc, nd.n1));
+      A2.push_back(nd.Wk.block(0, 0, nd.mc, nd.ku + nd.kv));
+    }
+    auto Q = ops_.qr(A1, fa);
+    ops_.group_wy(Q, fa);
+    for (int p = 0; p < nn; ++p) t_[l][p].P = Q[p];
+    // [U1; U2], [D12; D22] = P^* [U D~2]
+    ops_.apply_q_left(Q, A2, true);
+    // D11^{-1}
+    std::vector<Mat<R>> T, X;
+    for (int p = 0; p < nn; ++p) {
+      Node2<R>& nd = t_[l][p];
+      nd.D11inv = fa.template mat<R>(nd.n1, nd.n1);
+      T.push_back(nd.Wk.block(0, nd.ku + nd.kv, nd.n1, nd.n1));
+      X.push_back(nd.D11inv);
+    }
+    ops_.trinv(T, X);
+  }
+  tmp_.release(tk);
+  scr_.release(mk);
+}
+
+template <typename R> void Hss<R>::factor_root() {
+  Arena& fa = *fac_[0];
   // root: D+ = P_root R_root
   {
     auto mk = scr_.mark();
@@ -842,7 +848,7 @@ template <typename R> void Hss<R>::factor() {
     for (int c = 0; c < 4; ++c) { rows += t_[1][c].rows2; cols += t_[1][c].kv; }
     NH_REQUIRE(rows >= cols, ST_ERANK, "root block has fewer rows than columns");
     root_rows_ = rows; root_cols_ = cols;
-    Droot_ = keep_.mat<R>(rows, cols);
+    Droot_ = fa.template mat<R>(rows, cols);
     std::vector<CopyD<R>> cp;
     std::vector<GemmD<R>> g1, g2;
     int ro = 0;
@@ -866,17 +872,58 @@ template <typename R> void Hss<R>::factor() {
     ops_.copy(cp);
     ops_.gemm(g1);
     ops_.gemm(g2);
-    auto Q = ops_.qr({Droot_}, keep_);
-    ops_.group_wy(Q, keep_);
+    auto Q = ops_.qr({Droot_}, fa);
+    ops_.group_wy(Q, fa);
     Proot_ = Q[0];
-    Rinv_ = keep_.mat<R>(cols, cols);
+    Rinv_ = fa.template mat<R>(cols, cols);
     ops_.trinv({Droot_.block(0, 0, cols, cols)}, {Rinv_});
     tmp_.release(tk);
     scr_.release(mk);
   }
+}
+
+template <typename R> void Hss<R>::factor() {
+  const int L = pl_->L;
+  fac_.clear();
+  for (int l = 0; l <= L; ++l) {
+    fac_.emplace_back(new Arena((size_t)64 << 20));
+    fac_.back()->set_stream(st_);
+  }
+  for (int l = L; l >= 1; --l) factor_level(l);
+  factor_root();
   NH_CK(cudaStreamSynchronize(st_));
   tmp_.free_all();
   factored = true;
+  dropped_ = 0;
+}
+
+template <typename R> void Hss<R>::checkpoint(int levels) {
+  NH_REQUIRE(factored, ST_ESTATE, "checkpoint before factor");
+  const int L = pl_->L;
+  const int k = std::max(0, std::min(levels, L));
+  if (k <= dropped_) return;
+  NH_CK(cudaStreamSynchronize(st_));
+  for (int l = 1; l <= k; ++l) {
+    fac_[l]->free_all();
+    for (Node2<R>& nd : t_[l]) {
+      nd.Wk = Mat<R>(); nd.V2 = Mat<R>(); nd.D11inv = Mat<R>();
+      nd.Om = QFac<R>(); nd.Qv = QFac<R>(); nd.P = QFac<R>();
+    }
+  }
+  fac_[0]->free_all();
+  Droot_ = Mat<R>(); Rinv_ = Mat<R>(); Proot_ = QFac<R>();
+  dropped_ = k;
+}
+
+template <typename R> bool Hss<R>::ensure_factored() {
+  NH_REQUIRE(factored, ST_ESTATE, "solve before factor");
+  if (dropped_ == 0) return false;
+  for (int l = dropped_; l >= 1; --l) factor_level(l);
+  factor_root();
+  NH_CK(cudaStreamSynchronize(st_));
+  tmp_.free_all();
+  dropped_ = 0;
+  return true;
 }
 
 // ------------------------------------------------------------------------------- URV solve (Sec. 2.3)

@@ -69,6 +69,12 @@ template <typename R> class Hss {
   Hss(cudaStream_t st, const Plan* pl);
   void build(double eps);
   void factor();
+  // Per-level checkpointing: hand back the URV factors of the top `levels` levels (and the root);
+  // ensure_factored() recomputes them from the generators and the kept factors of the levels below
+  // (returns true when it did, i.e. device addresses of factors changed).
+  void checkpoint(int levels);
+  bool ensure_factored();
+  int dropped_levels() const { return dropped_; }
   // y (N x s, tree column order) = G~_hss^+ f (f: M x s in 2D row order); both device
   void solve(const cplx<R>* f2, int ldf, int s, cplx<R>* ytree, int ldy);
   // f2 (M x s, 2D order) = (G~_hss^+)^* y (N x s, tree column order): the adjoint of solve()
@@ -83,7 +89,11 @@ template <typename R> class Hss {
   double solve_entries() const;
   int max_rank() const;
   std::vector<int> level_ranks() const;
-  size_t bytes() const { return keep_.reserved(); }
+  size_t bytes() const {
+    size_t b = keep_.reserved();
+    for (auto& a : fac_) b += a->reserved();
+    return b;
+  }
   Ops<R>& ops() { return ops_; }
   // While a solve is captured into a CUDA graph the scratch arena must not grow.
   void freeze_scratch(bool f) { scr_.freeze(f); }
@@ -94,6 +104,8 @@ template <typename R> class Hss {
                 Mat<R>& G);
   void assemble_2d();
   void recompress(double eps);
+  void factor_level(int l);
+  void factor_root();
   cudaStream_t st_;
   const Plan* pl_;
   Arena keep_, scr_, tmp_;
@@ -101,6 +113,8 @@ template <typename R> class Hss {
   std::vector<std::vector<Gen1D<R>>> gx_, gy_;
   Mat<R> Gx_, Gy_;
   std::vector<std::vector<Node2<R>>> t_;
+  std::vector<std::unique_ptr<Arena>> fac_;   // factor storage per level (0 = root)
+  int dropped_ = 0;                            // top levels whose factors were handed back
   // root factor
   QFac<R> Proot_;
   Mat<R> Droot_, Rinv_;

@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "la.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1699,6 +1700,351 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   if (tid == 0) atomicAdd(rows_updated, (unsigned long long)d.r);
 }
 
+// =============================================================================== blocked Jacobi on tensor cores
+// The FP32 blocked Jacobi step of k_jacobi_blk with both of its products on the tensor cores
+// (tcgen05 kind::tf32, 3xTF32 split, M = N = 64), one CTA per block pair:
+//  1. Gram G = X_P^* X_P, X_P = the pair's 64 columns.  Chunks of 64 rows are split into TF32
+//     planes in shared memory (two buffers; the next chunk's loads are in flight while the current
+//     chunk's 96 MMAs run).  Each chunk accumulates in one of two tensor-memory accumulators, and
+//     the previous chunk's accumulator is added (FP32, round to nearest) into G in shared memory,
+//     so no tensor-core accumulation runs longer than 64 rows (its truncation stays at ~1e-6).
+//     With M = 64 the accumulator row i sits in tensor-memory lane 32 (i / 16) + i % 16.
+//  2. The largest cosine and the two-sided Jacobi on G -> V, exactly as in k_jacobi_blk.
+//  3. X_P <- X_P V over chunks of 64 rows: A = the chunk (K-major along the 64 columns), B = the
+//     planes of V^T, the product in tensor memory, written back in place.
+// Every wait is bounded: one that runs out sets g_jac_error, and the CTA leaves X untouched.
+namespace {
+constexpr int JT_W = 64, JT_CH = 64;             // pair width, rows per chunk
+constexpr uint32_t JT_SBO = (JT_CH / 4) * 128;   // 8-row group stride of a 64-deep K-major plane
+constexpr int JT_PLANE = JT_W * JT_CH * 4;       // 16 KB
+constexpr int JT_BUF = 4 * JT_PLANE;             // re hi, re lo, im hi, im lo
+constexpr int JT_LDG = JT_W + 1;
+constexpr size_t JT_SMEM = 2 * (size_t)JT_BUF + 2 * (size_t)JT_W * JT_LDG * sizeof(float2) + 1024;
+}  // namespace
+
+__device__ int g_jac_error;
+
+// the 12 MMAs of one k = 8 step of a complex product D = A B^T given as TF32 planes
+// (negA: the A-negate descriptor for the -Ai Bi terms; the conjugated Gram passes its own order)
+__device__ __forceinline__ void jt_mma12(uint32_t dr, uint32_t di, uint32_t a, uint32_t b, uint32_t ko, uint32_t f,
+                                         bool gram) {
+  const uint32_t idp = tc_idesc(64, 64, false), idn = tc_idesc(64, 64, true);
+  const uint64_t arh = tc_desc(a + ko, JT_SBO), arl = tc_desc(a + JT_PLANE + ko, JT_SBO),
+                 aih = tc_desc(a + 2 * JT_PLANE + ko, JT_SBO), ail = tc_desc(a + 3 * JT_PLANE + ko, JT_SBO);
+  const uint64_t brh = tc_desc(b + ko, JT_SBO), brl = tc_desc(b + JT_PLANE + ko, JT_SBO),
+                 bih = tc_desc(b + 2 * JT_PLANE + ko, JT_SBO), bil = tc_desc(b + 3 * JT_PLANE + ko, JT_SBO);
+  if (gram) {
+    // G = X^* X: Gr = Xr Xr + Xi Xi, Gi = Xr Xi - Xi Xr (A and B are the same planes)
+    tc_mma(dr, arh, brh, idp, f); tc_mma(dr, arh, brl, idp, 1u); tc_mma(dr, arl, brh, idp, 1u);
+    tc_mma(dr, aih, bih, idp, 1u); tc_mma(dr, aih, bil, idp, 1u); tc_mma(dr, ail, bih, idp, 1u);
+    tc_mma(di, arh, bih, idp, f); tc_mma(di, arh, bil, idp, 1u); tc_mma(di, arl, bih, idp, 1u);
+    tc_mma(di, aih, brh, idn, 1u); tc_mma(di, aih, brl, idn, 1u); tc_mma(di, ail, brh, idn, 1u);
+  } else {
+    // D = A B: Dr = Ar Br - Ai Bi, Di = Ar Bi + Ai Br
+    tc_mma(dr, arh, brh, idp, f); tc_mma(dr, arh, brl, idp, 1u); tc_mma(dr, arl, brh, idp, 1u);
+    tc_mma(dr, aih, bih, idn, 1u); tc_mma(dr, aih, bil, idn, 1u); tc_mma(dr, ail, bih, idn, 1u);
+    tc_mma(di, arh, bih, idp, f); tc_mma(di, arh, bil, idp, 1u); tc_mma(di, arl, bih, idp, 1u);
+    tc_mma(di, aih, brh, idp, 1u); tc_mma(di, aih, brl, idp, 1u); tc_mma(di, ail, brh, idp, 1u);
+  }
+}
+
+// four consecutive values along k of one operand row, split into the four planes at byte offset off
+__device__ __forceinline__ void jt_store4(unsigned char* buf, uint32_t off, const float2 (&v)[4]) {
+  uint32_t p[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    tc_split(v[e].x, p[0][e], p[1][e]);
+    tc_split(v[e].y, p[2][e], p[3][e]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<uint4*>(buf + q * JT_PLANE + off) = make_uint4(p[q][0], p[q][1], p[q][2], p[q][3]);
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_jacobi_tc(const JacD<float>* __restrict__ ds, int round, float tol, float tol_out, float negl2, int max_inner,
+                unsigned long long* __restrict__ rows_updated) {
+  constexpr int W = JT_W, LDG = JT_LDG;
+  const JacD<float> d = ds[blockIdx.y];
+  if (*d.done) return;
+  if (round >= d.nblk - 1 || (int)blockIdx.x >= d.nblk / 2) return;
+  extern __shared__ unsigned char jt_raw[];
+  const uint32_t raw_s = tc_smem_u32(jt_raw);
+  unsigned char* sm = jt_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
+  unsigned char* buf[2] = {sm, sm + JT_BUF};
+  float2* G = reinterpret_cast<float2*>(sm + 2 * JT_BUF);   // G[i * LDG + j] = x_i^* x_j
+  float2* V = G + W * LDG;
+  __shared__ int cidx[W];
+  __shared__ float rc[W / 2];
+  __shared__ float2 rse[W / 2];
+  __shared__ int ract[W / 2];
+  __shared__ int any_s, fail, skip;
+  __shared__ float offw[8];
+  __shared__ uint64_t mbar[4];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quad = warp & 3;
+  int I, J;
+  rr_pair(blockIdx.x, round, d.nblk, I, J);
+  if (tid < W) {
+    const int c = (tid < 32 ? I : J) * 32 + (tid & 31);
+    cidx[tid] = c < d.k ? c : -1;
+  }
+  if (warp == 0) tc_alloc(&tslot, 256);
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tc_bar_init(&mbar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail = 0;
+    skip = 0;
+  }
+  for (int e = tid; e < W * LDG; e += 256) G[e] = make_float2(0.f, 0.f);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  const float floor2 = negl2 * (*d.amax);
+  const int nch = (d.r + JT_CH - 1) / JT_CH;
+
+  // ---- 1. Gram.  Thread t stages 4 quads: quad e = t + 256 q -> column c = e / 16, rows 4 (e % 16)..+3
+  float2 pf[4][4];
+  auto load_gram = [&](int t) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q, c = e >> 4, r0 = t * JT_CH + 4 * (e & 15), col = cidx[c];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        pf[q][i] = (col >= 0 && r0 + i < d.r) ? d.X[(size_t)(r0 + i) + (size_t)col * d.ld] : make_float2(0.f, 0.f);
+    }
+  };
+  load_gram(0);
+  for (int t = 0; t <= nch; ++t) {
+    if (t < nch) {
+      unsigned char* b = buf[t & 1];   // last read by chunk t - 2, whose MMAs completed before its drain
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q;
+        jt_store4(b, tc_kmajor(e >> 4, 4 * (e & 15), JT_SBO), pf[q]);
+      }
+      tc_fence_async_smem();
+      __syncthreads();
+      if (tid == 0 && !fail) {
+        tc_fence_after();
+        const uint32_t a = tc_smem_u32(b), dr = tmem + (uint32_t)(t & 1) * 128, di = dr + 64;
+#pragma unroll
+        for (int ks = 0; ks < JT_CH / 8; ++ks) jt_mma12(dr, di, a, a, (uint32_t)ks * 256, ks == 0 ? 0u : 1u, true);
+        tc_commit(&mbar[t & 1]);
+      }
+      if (t + 1 < nch) load_gram(t + 1);
+    }
+    if (t >= 1) {
+      const int u = t - 1;
+      if (!fail && !tc_wait(&mbar[u & 1], (uint32_t)((u >> 1) & 1))) atomicExch(&fail, 1);
+      tc_fence_after();
+      // warps 0-3 add the real parts (columns 0-63 of the accumulator), warps 4-7 the imaginary
+      // parts (64-127); lanes 0-15 of quadrant q hold rows 16 q .. 16 q + 15
+      const uint32_t base = tmem + (uint32_t)(u & 1) * 128 + (warp < 4 ? 0u : 64u) + ((uint32_t)(32 * quad) << 16);
+      for (int c0 = 0; c0 < W; c0 += 16) {
+        uint32_t v[16];
+        tc_ld16(base + (uint32_t)c0, v);
+        tc_wait_ld();
+        if (lane < 16 && !fail) {
+          float2* g = G + (16 * quad + lane) * LDG + c0;
+          if (warp < 4) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) g[j].x += __uint_as_float(v[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) g[j].y += __uint_as_float(v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+    }
+    __syncthreads();
+  }
+  if (fail) goto cleanup;
+  // ---- 2. largest cosine of the fresh Gram (columns above the noise floor only)
+  {
+    const int ti = tid >> 4, tj = tid & 15;
+    float m = 0.f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = ti + 16 * p, j = tj + 16 * q;
+        const float di = G[i * LDG + i].x, dj = G[j * LDG + j].x;
+        if (i != j && di > floor2 && dj > floor2) {
+          const float gg = sqrtf(abs2(G[i * LDG + j]));
+          m = fmaxf(m, gg / (sqrtf(di) * sqrtf(dj)));
+        }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) offw[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+      float tt = 0.f;
+      for (int w = 0; w < 8; ++w) tt = fmaxf(tt, offw[w]);
+      if (tt > 0.f) atomicMax(d.off, __float_as_uint(tt));
+      skip = tt <= tol_out;            // the pair is already orthogonal
+    }
+    __syncthreads();
+    if (skip) goto cleanup;
+  }
+  // ---- 3. cyclic two-sided Jacobi on G, V <- V J for every rotation J (as in k_jacobi_blk)
+  for (int e = tid; e < W * W; e += 256) {
+    const int i = e / W, j = e - i * W;
+    V[i * LDG + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  if (tid == 0) any_s = 0;
+  __syncthreads();
+  for (int sw = 0; sw < max_inner; ++sw) {
+    for (int ir = 0; ir < W - 1; ++ir) {
+      if (tid < W / 2) {
+        int a, b;
+        rr_pair(tid, ir, W, a, b);
+        const float al = G[a * LDG + a].x, be = G[b * LDG + b].x;
+        const float2 ga = G[a * LDG + b];
+        const float g = sqrtf(abs2(ga));
+        int act = 0;
+        if (al > floor2 && be > floor2 && g > 0.f && g / (sqrtf(al) * sqrtf(be)) > tol) {
+          const float zeta = (be - al) / (2.f * g);
+          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = 1.f / sqrtf(1.f + tt * tt);
+          const float sn = c * tt;
+          rc[tid] = c;
+          rse[tid] = make_float2(sn * ga.x / g, sn * ga.y / g);
+          act = 1;
+          any_s = 1;
+        }
+        ract[tid] = act;
+      }
+      __syncthreads();
+      for (int e = tid; e < 2 * (W / 2) * W; e += 256) {
+        const int which = e / ((W / 2) * W), rest = e - which * ((W / 2) * W);
+        const int p = rest / W, i = rest - p * W;
+        if (!ract[p]) continue;
+        int a, b;
+        rr_pair(p, ir, W, a, b);
+        float2* Mx = which ? V : G;
+        const float c = rc[p];
+        const float2 se = rse[p], sec = conj(se);
+        const float2 x = Mx[i * LDG + a], y = Mx[i * LDG + b];
+        Mx[i * LDG + a] = c * x - sec * y;
+        Mx[i * LDG + b] = se * x + c * y;
+      }
+      __syncthreads();
+      for (int e = tid; e < (W / 2) * W; e += 256) {
+        const int p = e / W, j = e - p * W;
+        if (!ract[p]) continue;
+        int a, b;
+        rr_pair(p, ir, W, a, b);
+        const float c = rc[p];
+        const float2 se = rse[p], sec = conj(se);
+        const float2 x = G[a * LDG + j], y = G[b * LDG + j];
+        G[a * LDG + j] = c * x - se * y;
+        G[b * LDG + j] = sec * x + c * y;
+      }
+      __syncthreads();
+      if (tid < W / 2 && ract[tid]) {
+        int a, b;
+        rr_pair(tid, ir, W, a, b);
+        G[a * LDG + b] = make_float2(0.f, 0.f);
+        G[b * LDG + a] = make_float2(0.f, 0.f);
+        G[a * LDG + a].y = 0.f;
+        G[b * LDG + b].y = 0.f;
+      }
+      __syncthreads();
+    }
+    const int more = any_s;
+    __syncthreads();
+    if (!more) break;
+    if (tid == 0) any_s = 0;
+    __syncthreads();
+  }
+  // ---- 4. X_P <- X_P V.  B = V^T planes in buffer 1: B(n, k) = V(k, n)
+  for (int e = tid; e < W * (W / 4); e += 256) {
+    const int n = e >> 4, kq = e & 15;
+    float2 v4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v4[i] = V[(4 * kq + i) * LDG + n];
+    jt_store4(buf[1], tc_kmajor(n, 4 * kq, JT_SBO), v4);
+  }
+  {
+    // A: thread t stages rows m = e % 64, columns 4 (e / 64)..+3, e = t + 256 q
+    auto load_upd = [&](int t) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q, m = e & 63, cq = e >> 6, row = t * JT_CH + m;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int col = cidx[4 * cq + i];
+          pf[q][i] = (col >= 0 && row < d.r) ? d.X[(size_t)row + (size_t)col * d.ld] : make_float2(0.f, 0.f);
+        }
+      }
+    };
+    load_upd(0);
+    for (int t = 0; t < nch; ++t) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q;
+        jt_store4(buf[0], tc_kmajor(e & 63, 4 * (e >> 6), JT_SBO), pf[q]);
+      }
+      tc_fence_async_smem();
+      __syncthreads();
+      if (tid == 0 && !fail) {
+        tc_fence_after();
+        const uint32_t a = tc_smem_u32(buf[0]), b = tc_smem_u32(buf[1]);
+#pragma unroll
+        for (int ks = 0; ks < W / 8; ++ks) jt_mma12(tmem, tmem + 64, a, b, (uint32_t)ks * 256, ks == 0 ? 0u : 1u, false);
+        tc_commit(&mbar[2]);
+      }
+      if (t + 1 < nch) load_upd(t + 1);   // rows of the next chunk: disjoint from the ones written below
+      if (!fail && !tc_wait(&mbar[2], (uint32_t)(t & 1))) atomicExch(&fail, 1);
+      tc_fence_after();
+      // warps 0-3 write output columns 0-31, warps 4-7 columns 32-63; lanes 0-15 of quadrant q own
+      // rows 16 q + lane of the chunk
+      const int n0 = warp < 4 ? 0 : 32;
+      for (int c0 = 0; c0 < 32; c0 += 16) {
+        uint32_t vr[16], vi[16];
+        const uint32_t la = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(n0 + c0);
+        tc_ld16(la, vr);
+        tc_ld16(la + 64, vi);
+        tc_wait_ld();
+        const int row = t * JT_CH + 16 * quad + lane;
+        if (lane < 16 && row < d.r && !fail) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = cidx[n0 + c0 + j];
+            if (col >= 0) d.X[(size_t)row + (size_t)col * d.ld] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && !fail) atomicAdd(rows_updated, (unsigned long long)d.r);
+cleanup:
+  if (tid == 0) {
+    if (fail) atomicExch(&g_jac_error, 1);
+    tc_commit(&mbar[3]);                // MMAs still in flight after a failed wait finish first
+    tc_wait(&mbar[3], 0u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 256);
+}
+
+int jacobi_tc_error(bool reset) {
+  int v = 0;
+  NH_CK(cudaMemcpyFromSymbol(&v, g_jac_error, sizeof(int)));
+  if (reset && v) {
+    const int z = 0;
+    NH_CK(cudaMemcpyToSymbol(g_jac_error, &z, sizeof(int)));
+  }
+  return v;
+}
+
 // sigma_j = ||x_j||; rank positions by counting (descending, ties by index); count retained.
 template <typename R> struct SortD {
   const cplx<R>* X; int ld, r, k;
@@ -2144,7 +2490,12 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     const size_t jsmem = (size_t)32 * rpc * sizeof(cplx<R>);
     if (jmode == J_CLUSTER && jsmem > (size_t)200 * 1024) jmode = J_SCALAR;
     const bool use_cluster = jmode == J_CLUSTER;
-    if (jmode == J_BLOCK)
+    // FP32 blocked steps run their Gram and update products on the tensor cores
+    bool jtc = false;
+    if constexpr (sizeof(R) == 4) jtc = jmode == J_BLOCK && gemm_tc_enabled();
+    if (jtc)
+      NH_CK(cudaFuncSetAttribute(k_jacobi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JT_SMEM));
+    else if (jmode == J_BLOCK)
       NH_CK(cudaFuncSetAttribute(k_jacobi_blk<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JbCfg<R>::smem));
     if (use_cluster) {
       NH_CK(cudaFuncSetAttribute(k_jacobi_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2175,7 +2526,12 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
       for (int rd = 0; rd < maxblk - 1; ++rd) {
         if (jmode == J_BLOCK) {
           dim3 grid(maxblk / 2, (unsigned)jd.size());
-          k_jacobi_blk<R><<<grid, 256, JbCfg<R>::smem, st_>>>(djd, rd, tol, tol_out, negl2, 16, rows_upd);
+          if constexpr (sizeof(R) == 4) {
+            if (jtc) k_jacobi_tc<<<grid, 256, JT_SMEM, st_>>>(djd, rd, tol, tol_out, negl2, 16, rows_upd);
+            else k_jacobi_blk<R><<<grid, 256, JbCfg<R>::smem, st_>>>(djd, rd, tol, tol_out, negl2, 16, rows_upd);
+          } else {
+            k_jacobi_blk<R><<<grid, 256, JbCfg<R>::smem, st_>>>(djd, rd, tol, tol_out, negl2, 16, rows_upd);
+          }
           NH_LAUNCH_CK();
         } else if (use_cluster) {
           cudaLaunchConfig_t cfg = {};
@@ -2214,6 +2570,10 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         break;
       }
     }
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (jmode == J_BLOCK && !jd.empty() && gemm_tc_enabled() && jacobi_tc_error(true))
+      throw Error(ST_ETIMEOUT, "tsvd: a bounded wait of the tensor-core Jacobi step ran out");
   }
   if (prof.on && jmode == J_BLOCK && !jd.empty()) {   // X_P V of the block pairs that rotated
     unsigned long long ru = 0;

@@ -112,6 +112,8 @@ bool gemm_tc_enabled();
 int gemm_tc_run(const std::vector<GemmD<float>>& d, int cls, Arena& ar, cudaStream_t st,
                 void* (*stage)(void*, const void*, size_t), void* ctx);
 int gemm_tc_error(bool reset);
+// Flag of the tensor-core Jacobi step's bounded waits (read, optionally cleared).
+int jacobi_tc_error(bool reset);
 // Number of shape classes the GEMM autotuner has measured in this process.
 int gemm_tune_entries();
 

@@ -114,3 +114,43 @@ def test_autograd_matches_oracle_and_finite_differences(nh):
         xm[j] -= h
         fd = (L(np.mod(xp, 1.0), y) - L(np.mod(xm, 1.0), y)) / (2 * h)
         assert abs(fd - gx[j]) < 1e-4 * max(1.0, np.max(np.abs(gx)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpointed_factors_are_recomputed(nh, prec):
+    """Per-level checkpointing: handing back the top two levels' factors frees their memory, and
+    the next solve / gradient factors them again from the kept levels, giving the same results."""
+    w, x, y, f, g = _case("fp64_n32", 2, 91)
+    eps = 1e-10 if prec == "fp64" else 1e-6
+    h = nh.NudftHSS(torch.from_numpy(x), torch.from_numpy(y), w.nx, w.ny, eps=eps, levels=3, prec=prec,
+                    refine_tol=1e-12, refine_max=20).factor()
+    fc, gc = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    c0 = to_np(h.solve(fc))
+    gf0, gx0, gy0 = (to_np(t) for t in h.grad(fc, torch.from_numpy(c0).cuda(), gc))
+    bytes0 = h.info()["device_bytes"]
+    h.checkpoint(2)
+    info = h.info()
+    assert info["checkpointed_levels"] == 2 and info["device_bytes"] < bytes0
+    c1 = to_np(h.solve(fc))
+    assert h.info()["checkpointed_levels"] == 0
+    gf1, gx1, gy1 = (to_np(t) for t in h.grad(fc, torch.from_numpy(c1).cuda(), gc))
+    h.close()
+    assert _rel(c1, c0) < 1e-12
+    assert _rel(gf1, gf0) < 1e-12 and _rel(gx1, gx0) < 1e-12 and _rel(gy1, gy0) < 1e-12
+
+
+def test_autograd_with_checkpointed_levels(nh):
+    """lstsq(..., checkpoint_levels=2): the backward pass refactors the handed-back levels and
+    returns the gradients of the run without checkpointing."""
+    w, x, y, f, _ = _case("fp64_n32", 2, 93)
+    ct = torch.from_numpy(complex_normal((w.N, 2), 94)).cuda()
+    grads = []
+    for ck in (0, 2):
+        xt = torch.from_numpy(x).cuda().requires_grad_(True)
+        yt = torch.from_numpy(y).cuda().requires_grad_(True)
+        ft = torch.from_numpy(f).cuda().requires_grad_(True)
+        c = nh.lstsq(ft, xt, yt, w.nx, w.ny, eps=1e-10, levels=3, checkpoint_levels=ck)
+        torch.sum(torch.abs(c - ct) ** 2).backward()
+        grads.append((to_np(ft.grad), to_np(xt.grad), to_np(yt.grad)))
+    for a, b in zip(*grads):
+        assert _rel(b, a) < 1e-12

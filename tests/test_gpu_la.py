@@ -69,9 +69,14 @@ def test_tsvd_fp64(nh, monkeypatch, jacobi, r, w, kind):
     assert np.linalg.norm(resid, 2) <= 2 * eps * s_ref[0] + 1e-13 * s_ref[0]
 
 
-@pytest.mark.parametrize("jacobi", ["block", "scalar"])
+@pytest.mark.parametrize("jacobi", ["block", "block_cuda_cores", "scalar"])
 @pytest.mark.parametrize("r,w", [(300, 120), (1577, 3000), (2600, 2100)])
 def test_tsvd_fp32(nh, monkeypatch, jacobi, r, w):
+    """FP32 truncated SVD.  "block": the blocked Jacobi step with its Gram and update products on
+    the tensor cores (the default); "block_cuda_cores": the same step on CUDA cores."""
+    if jacobi == "block_cuda_cores":
+        monkeypatch.setenv("NH_GEMM_TC", "0")
+        jacobi = "block"
     monkeypatch.setenv("NH_JACOBI_MODE", jacobi)
     C = make_matrix(r, w, "graded", 5).astype(np.complex64)
     eps = 1e-5
