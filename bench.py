@@ -414,8 +414,8 @@ def run_batched(args):
     units = sum(p["c_true"].shape[1] for p in ps)
 
     def step():
-        hs = nh.build_batched(ps, threads=16)
-        cs = nh.solve_batched(hs, fs, threads=16)
+        hs = nh.build_batched(ps, threads=8)
+        cs = nh.solve_batched(hs, fs, threads=8)
         for h in hs:
             h.close()
         return cs
@@ -445,8 +445,8 @@ def run_batched(args):
     t0 = time.perf_counter()
     pd = [dict(p, x=a.to(dev, non_blocking=True), y=b.to(dev, non_blocking=True)) for p, a, b in zip(ps, hx, hy)]
     fd = [f.to(dev, non_blocking=True) for f in hf]
-    hs = nh.build_batched(pd, threads=16)
-    out = [c.cpu() for c in nh.solve_batched(hs, fd, threads=16)]
+    hs = nh.build_batched(pd, threads=8)
+    out = [c.cpu() for c in nh.solve_batched(hs, fd, threads=8)]
     for h in hs:
         h.close()
     t_e2e = time.perf_counter() - t0
@@ -458,11 +458,54 @@ def run_batched(args):
             "config": {"workload": "batched_uneven", "problems": len(ps), "sum_N": sum(p["nx"] * p["ny"] for p in ps),
                        "sum_M": sum(p["x"].size for p in ps), "nrhs_each": 8, "eps": 1e-6, "precision": "mixed",
                        "sizes": "nx, ny uniform in {32,48,64,96,128,192,256}; M/N ~ U[1.5,4]; theta ~ U[-0.25,0.35]",
-                       "concurrency": "one stream per problem, 16 host threads", "parallelism": "replicas x1"},
+                       "concurrency": "one stream per problem, 8 host threads", "parallelism": "replicas x1"},
             "rel_err_vs_c_true": err,
             "e2e": {"value": units / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ kernel mode
+def run_gemm(args):
+    """One complex64 GEMM C = A B (m x k times k x n, NN, beta = 0) through nudft2_la_gemm, the
+    library's batched GEMM (tensor cores when the shape qualifies): device time per call with CUDA
+    events after args.warmup calls, and the rate with 8 m n k flops per product.  Used for kernel
+    profiles; not the solver benchmark."""
+    import ctypes
+
+    import torch
+
+    from paper_2607_00928_b300.binding import MIXED, _check, _stream, lib
+    parts = [int(v) for v in args.gemm.split(",")]
+    m, n, k = parts[:3]
+    batch = parts[3] if len(parts) > 3 else 1
+    g = torch.Generator(device="cuda").manual_seed(1)
+    # (batch, cols, rows) contiguous = column-major rows x cols per item: no layout copies per call
+    A = torch.randn((batch, k, m), dtype=torch.complex64, device="cuda", generator=g)
+    B = torch.randn((batch, n, k), dtype=torch.complex64, device="cuda", generator=g)
+    C = torch.zeros((batch, n, m), dtype=torch.complex64, device="cuda")
+
+    def call():
+        _check(lib().nudft2_la_gemm(MIXED, 0, 0, m, n, k, 1.0, ctypes.c_void_p(A.data_ptr()), m, m * k,
+                                    ctypes.c_void_p(B.data_ptr()), k, k * n, 0.0, ctypes.c_void_p(C.data_ptr()), m,
+                                    m * n, batch, _stream()))
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        call()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    print(json.dumps({"metric": "complex64 GEMM rate (8 m n k flops)", "value": 8.0 * m * n * k * batch / ms / 1e9,
+                      "unit": "TFLOP/s", "ms": ms, "m": m, "n": n, "k": k, "batch": batch, "steps": args.steps,
+                      "warmup": args.warmup}), flush=True)
 
 
 def main():
@@ -474,7 +517,11 @@ def main():
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gemm", default=None, help="m,n,k[,batch]: time one library GEMM instead of the solver")
     args = ap.parse_args()
+    if args.gemm:
+        run_gemm(args)
+        return
     if args.workload == "batched_uneven":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the single-problem "

@@ -67,7 +67,10 @@ typedef struct {
   int prec;            /* nudft2_prec                                                             */
   double refine_tol;   /* MIXED: stop when max relative residual ||f - A c||/||f|| <= refine_tol    */
   int refine_max;      /* MIXED: maximum refinement steps                                          */
-  unsigned flags;      /* reserved, 0                                                              */
+  unsigned flags;      /* NUDFT2_FLAG_* bits                                                      */
+  int levels_y;        /* depth of T^y when > 0 (then `levels` is the depth of T^x): an unbalanced
+                          product tree (Def. 3.3 (2), (3)) with leaves (nx >> levels) x
+                          (ny >> levels_y); 0 = both trees have depth `levels`                     */
 } nudft2_opts;
 
 /* opts.flags bits */

@@ -23,7 +23,8 @@ FAST_FWD, FAST_ADJ, EXACT_FWD, EXACT_ADJ, PINV, PINV_ADJ = range(6)
 
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("levels", ctypes.c_int), ("leaf", ctypes.c_int), ("prec", ctypes.c_int),
-                ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("levels_y", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -210,7 +211,7 @@ class NudftHSS:
 
     def __init__(self, x, y, nx: int, ny: int, eps: float = 1e-10, levels: int = 0, leaf: int = 64,
                  prec: str = "fp64", refine_tol: float = 1e-8, refine_max: int = 8, stream=None,
-                 profile: bool = False, fp64_residuals: bool = False):
+                 profile: bool = False, fp64_residuals: bool = False, levels_y: int = 0):
         self._h = ctypes.c_void_p()
         self.x = torch.as_tensor(x).to(device="cuda", dtype=torch.float64).contiguous()
         self.y = torch.as_tensor(y).to(device="cuda", dtype=torch.float64).contiguous()
@@ -218,7 +219,7 @@ class NudftHSS:
         self.nx, self.ny, self.N = nx, ny, nx * ny
         self.stream = stream
         o = Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
-                 (FLAG_PROFILE if profile else 0) | (FLAG_FP64_RESIDUALS if fp64_residuals else 0))
+                 (FLAG_PROFILE if profile else 0) | (FLAG_FP64_RESIDUALS if fp64_residuals else 0), levels_y)
         _check(lib().nudft2_hss_build(ctypes.c_void_p(self.x.data_ptr()), ctypes.c_void_p(self.y.data_ptr()),
                                       self.M, nx, ny, ctypes.byref(o), _stream(stream), ctypes.byref(self._h)))
 
@@ -314,9 +315,10 @@ class NudftHSS:
             pass
 
 
-def _opts(eps=1e-10, levels=0, leaf=64, prec="fp64", refine_tol=1e-8, refine_max=8, profile=False) -> Opts:
+def _opts(eps=1e-10, levels=0, leaf=64, prec="fp64", refine_tol=1e-8, refine_max=8, profile=False,
+          levels_y=0) -> Opts:
     return Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
-                FLAG_PROFILE if profile else 0)
+                FLAG_PROFILE if profile else 0, levels_y)
 
 
 def build_batched(problems, factor: bool = True, threads: int = 8, stream=None):
@@ -326,7 +328,7 @@ def build_batched(problems, factor: bool = True, threads: int = 8, stream=None):
     n = len(problems)
     xs = [torch.as_tensor(p["x"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
     ys = [torch.as_tensor(p["y"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
-    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max")
+    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max", "levels_y")
     opts = (Opts * n)(*[_opts(**{k: p[k] for k in keys if k in p}) for p in problems])
     px = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
     py = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ys])

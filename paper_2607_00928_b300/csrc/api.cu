@@ -38,7 +38,7 @@ struct nudft2_hss_s {
   cudaEvent_t join = nullptr;
   std::map<int, std::unique_ptr<SolveGraph<double>>> g64;
   std::map<int, std::unique_ptr<SolveGraph<float>>> g32;
-  Arena keep{(size_t)64 << 20};
+  Arena keep{(size_t)64 << 20, true};
   Arena scr{(size_t)256 << 20};
   Plan pl;
   std::unique_ptr<Hss<double>> h64;
@@ -682,7 +682,7 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     NH_REQUIRE(nx >= 1 && ny >= 1 && (int64_t)nx * ny <= (1LL << 26), ST_EINVAL, "bad frequency grid");
     NH_REQUIRE(M >= (int64_t)nx * ny, ST_EINVAL, "least squares needs M >= N = nx*ny");
     NH_REQUIRE(M < (1LL << 31), ST_EINVAL, "M too large");
-    nudft2_opts opt{1e-10, 0, 64, NUDFT2_FP64, 1e-8, 8, 0};
+    nudft2_opts opt{1e-10, 0, 64, NUDFT2_FP64, 1e-8, 8, 0, 0};
     if (o) opt = *o;
     NH_REQUIRE(opt.eps > 0 && opt.eps < 1, ST_EINVAL, "eps must lie in (0,1)");
     NH_REQUIRE(opt.prec == NUDFT2_FP64 || opt.prec == NUDFT2_MIXED, ST_EINVAL, "unknown precision");
@@ -693,8 +693,9 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
       L = 1;
       while (L < 12 && (int64_t)(nx >> L) * (ny >> L) > leaf && (nx >> (L + 1)) >= 1 && (ny >> (L + 1)) >= 1) ++L;
     }
-    NH_REQUIRE(L >= 1 && L <= 12 && (nx >> L) >= 1 && (ny >> L) >= 1, ST_EINVAL,
-               "levels must satisfy 1 <= L and 2^L <= min(nx, ny)");
+    const int Lx = L, Ly = opt.levels_y > 0 ? opt.levels_y : L;
+    NH_REQUIRE(Lx >= 1 && Lx <= 12 && Ly >= 1 && Ly <= 12 && (nx >> Lx) >= 1 && (ny >> Ly) >= 1, ST_EINVAL,
+               "levels must satisfy 1 <= L and 2^Lx <= nx, 2^Ly <= ny");
     // validate points on the host: finite and in [0, 1)
     {
       std::vector<double> hx(M), hy(M);
@@ -706,7 +707,7 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     }
     h = new nudft2_hss_s();
     h->opt = opt;
-    h->M = (int)M; h->nx = nx; h->ny = ny; h->L = L; h->N = nx * ny;
+    h->M = (int)M; h->nx = nx; h->ny = ny; h->L = std::max(Lx, Ly); h->N = nx * ny;
     NH_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
     NH_CK(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     enter(h, stream);
@@ -714,7 +715,7 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     h->scr.set_stream(h->st);
     h->ops.reset(new Ops<double>(h->st, &h->scr));
     const double t0 = now_ms();
-    make_plan(h->st, h->keep, h->scr, d_x, d_y, (int)M, nx, ny, L, h->pl);
+    make_plan(h->st, h->keep, h->scr, d_x, d_y, (int)M, nx, ny, Lx, Ly, h->pl);
     h->Ax = h->keep.arr<double2>((size_t)M * nx);
     h->Ay = h->keep.arr<double2>((size_t)M * ny);
     twiddle_table(h->st, h->pl.x, (int)M, nx, h->Ax);

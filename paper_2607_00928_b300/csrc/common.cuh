@@ -106,7 +106,11 @@ template <typename R> struct Mat {
 // pointers with 256-byte alignment.  mark()/release() give stack-like scratch lifetimes.
 class Arena {
  public:
-  explicit Arena(size_t chunk = (size_t)256 << 20) : chunk_(chunk) {}
+  // dedicated_large: an arena that is never marked or released (long-lived storage) gives every
+  // allocation of at least a quarter chunk its own device block, so that large blocks do not
+  // leave the unused tails of partly filled chunks behind.
+  explicit Arena(size_t chunk = (size_t)256 << 20, bool dedicated_large = false)
+      : chunk_(chunk), dedicated_(dedicated_large) {}
   ~Arena() { free_all(); }
   void set_stream(cudaStream_t s) { st_ = s; }
   // While frozen (during CUDA-graph capture) the arena may only reuse chunks it already owns.
@@ -114,6 +118,14 @@ class Arena {
   void* alloc(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
+    if (dedicated_ && bytes >= chunk_ / 4) {
+      if (frozen_) throw Error(ST_ENOMEM, "arena is frozen during graph capture and has no room left");
+      void* p = nullptr;
+      NH_CK(cudaMallocAsync(&p, bytes, st_));
+      big_.push_back({p, bytes});
+      total_ += bytes;
+      return p;
+    }
     if (cur_ < chunks_.size()) {
       // try current chunk, then later (already allocated) chunks
       while (cur_ < chunks_.size()) {
@@ -170,6 +182,8 @@ class Arena {
   }
   void free_all() {
     for (auto& c : chunks_) cudaFreeAsync(c.p, st_);
+    for (auto& b : big_) cudaFreeAsync(b.first, st_);
+    big_.clear();
     chunks_.clear();
     cur_ = 0;
     total_ = 0;
@@ -177,6 +191,7 @@ class Arena {
   size_t reserved() const {
     size_t s = 0;
     for (auto& c : chunks_) s += c.size;
+    for (auto& b : big_) s += b.second;
     return s;
   }
   size_t used() const { return total_; }
@@ -184,7 +199,9 @@ class Arena {
  private:
   struct Chunk { void* p; size_t size; size_t used; };
   std::vector<Chunk> chunks_;
+  std::vector<std::pair<void*, size_t>> big_;   // dedicated blocks (dedicated_large arenas)
   size_t cur_ = 0, chunk_, total_ = 0;
+  bool dedicated_ = false;
   cudaStream_t st_ = 0;
   bool frozen_ = false;
 };

@@ -17,17 +17,6 @@
 
 namespace nh {
 
-static inline int morton_x(int p, int l) {
-  int ix = 0;
-  for (int b = 0; b < l; ++b) ix |= ((p >> (2 * b + 1)) & 1) << b;
-  return ix;
-}
-static inline int morton_y(int p, int l) {
-  int iy = 0;
-  for (int b = 0; b < l; ++b) iy |= ((p >> (2 * b)) & 1) << b;
-  return iy;
-}
-
 // =============================================================================== plan
 static void make_tree(Tree1D& t, int n, int L) {
   t.n = n;
@@ -51,11 +40,33 @@ static void make_tree(Tree1D& t, int n, int L) {
 }
 
 void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, const double* d_y, int M, int nx, int ny,
-               int L, Plan& pl) {
+               int Lx, int Ly, Plan& pl) {
+  const int L = std::max(Lx, Ly);
   pl.M = M; pl.nx = nx; pl.ny = ny; pl.L = L; pl.N = nx * ny;
-  make_tree(pl.tx, nx, L);
-  make_tree(pl.ty, ny, L);
-  const int nleaf = 1 << (2 * L);
+  pl.Lx = Lx; pl.Ly = Ly;
+  make_tree(pl.tx, nx, Lx);
+  make_tree(pl.ty, ny, Ly);
+  // product tree (Def. 3.3): fan-out per level, node -> (T^x node, T^y node)
+  pl.fan.assign(L + 1, 0);
+  pl.nn.assign(L + 1, 1);
+  pl.ix.assign(L + 1, {});
+  pl.iy.assign(L + 1, {});
+  pl.ix[0] = {0};
+  pl.iy[0] = {0};
+  for (int l = 0; l < L; ++l) {
+    const int F = (pl.splitx(l) ? 2 : 1) * (pl.splity(l) ? 2 : 1);
+    pl.fan[l] = F;
+    pl.nn[l + 1] = pl.nn[l] * F;
+    for (int p = 0; p < pl.nn[l]; ++p)
+      for (int c = 0; c < F; ++c) {
+        pl.ix[l + 1].push_back(pl.splitx(l) ? 2 * pl.ix[l][p] + pl.cxi(l, c) : pl.ix[l][p]);
+        pl.iy[l + 1].push_back(pl.splity(l) ? 2 * pl.iy[l][p] + pl.cyj(l, c) : pl.iy[l][p]);
+      }
+  }
+  const int nleaf = pl.nn[L];
+  const int nlx = 1 << Lx, nly = 1 << Ly;
+  std::vector<int> leafid((size_t)nlx * nly, 0);
+  for (int p = 0; p < nleaf; ++p) leafid[(size_t)pl.ix[L][p] * nly + pl.iy[L][p]] = p;
   pl.x = keep.arr<double>(M);
   pl.y = keep.arr<double>(M);
   NH_CK(cudaMemcpyAsync(pl.x, d_x, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -63,12 +74,14 @@ void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, cons
   auto mk = scr.mark();
   int* lfx = scr.arr<int>(nx);
   int* lfy = scr.arr<int>(ny);
+  int* lid = scr.arr<int>(leafid.size());
   NH_CK(cudaMemcpyAsync(lfx, pl.tx.leaf_of_col.data(), nx * sizeof(int), cudaMemcpyHostToDevice, st));
   NH_CK(cudaMemcpyAsync(lfy, pl.ty.leaf_of_col.data(), ny * sizeof(int), cudaMemcpyHostToDevice, st));
+  NH_CK(cudaMemcpyAsync(lid, leafid.data(), leafid.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   int* k2 = scr.arr<int>(M);
   int* kx = scr.arr<int>(M);
   int* ky = scr.arr<int>(M);
-  bin_points(st, pl.x, pl.y, M, nx, ny, lfx, lfy, L, k2, kx, ky);
+  bin_points(st, pl.x, pl.y, M, nx, ny, lfx, lfy, lid, nly, k2, kx, ky);
   pl.perm2 = keep.arr<int>(M);
   int* permx = scr.arr<int>(M);
   int* permy = scr.arr<int>(M);
@@ -102,9 +115,9 @@ void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, cons
   auto rows1d = [&](Tree1D& t, const std::vector<int>& cnt) {
     std::vector<int> pre(t.n + 1, 0);
     for (int k = 0; k < t.n; ++k) pre[k + 1] = pre[k] + cnt[k];
-    t.r0.assign(L + 1, {});
-    t.m.assign(L + 1, {});
-    for (int l = 0; l <= L; ++l)
+    t.r0.assign(t.L + 1, {});
+    t.m.assign(t.L + 1, {});
+    for (int l = 0; l <= t.L; ++l)
       for (size_t i = 0; i < t.c0[l].size(); ++i) {
         t.r0[l].push_back(pre[t.c0[l][i]]);
         t.m[l].push_back(pre[t.c1[l][i]] - pre[t.c0[l][i]]);
@@ -118,14 +131,14 @@ void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, cons
   pl.leaf_lx.assign(nleaf, 0);
   pl.leaf_ly.assign(nleaf, 0);
   for (int p = 0; p < nleaf; ++p) {
-    const int lx = morton_x(p, L), ly = morton_y(p, L);
+    const int lx = pl.ix[L][p], ly = pl.iy[L][p];
     pl.leaf_lx[p] = lx; pl.leaf_ly[p] = ly;
     rpre[p + 1] = rpre[p] + h2[p];
-    cpre[p + 1] = cpre[p] + (pl.tx.c1[L][lx] - pl.tx.c0[L][lx]) * (pl.ty.c1[L][ly] - pl.ty.c0[L][ly]);
+    cpre[p + 1] = cpre[p] + (pl.tx.c1[Lx][lx] - pl.tx.c0[Lx][lx]) * (pl.ty.c1[Ly][ly] - pl.ty.c0[Ly][ly]);
   }
   for (int l = 0; l <= L; ++l) {
-    const int span = 1 << (2 * (L - l));
-    for (int p = 0; p < (1 << (2 * l)); ++p) {
+    const int span = nleaf / pl.nn[l];
+    for (int p = 0; p < pl.nn[l]; ++p) {
       pl.r0[l].push_back(rpre[p * span]);
       pl.m[l].push_back(rpre[(p + 1) * span] - rpre[p * span]);
       pl.c0[l].push_back(cpre[p * span]);
@@ -135,7 +148,7 @@ void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, cons
   std::vector<int> cm(pl.N);
   for (int p = 0; p < nleaf; ++p) {
     const int lx = pl.leaf_lx[p], ly = pl.leaf_ly[p];
-    const int x0 = pl.tx.c0[L][lx], x1 = pl.tx.c1[L][lx], y0 = pl.ty.c0[L][ly], y1 = pl.ty.c1[L][ly];
+    const int x0 = pl.tx.c0[Lx][lx], x1 = pl.tx.c1[Lx][lx], y0 = pl.ty.c0[Ly][ly], y1 = pl.ty.c1[Ly][ly];
     const int dy = y1 - y0;
     for (int a = 0; a < x1 - x0; ++a)
       for (int b = 0; b < dy; ++b) cm[cpre[p] + a * dy + b] = (x0 + a) * ny + (y0 + b);
@@ -147,7 +160,7 @@ void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, cons
 
 // =============================================================================== Hss
 template <typename R>
-Hss<R>::Hss(cudaStream_t st, const Plan* pl) : st_(st), pl_(pl), keep_((size_t)512 << 20), scr_((size_t)64 << 20),
+Hss<R>::Hss(cudaStream_t st, const Plan* pl) : st_(st), pl_(pl), keep_((size_t)256 << 20, true), scr_((size_t)64 << 20),
                                                 tmp_((size_t)512 << 20), ops_(st, &scr_) {
   keep_.set_stream(st);
   scr_.set_stream(st);
@@ -303,17 +316,24 @@ void Hss<R>::build_1d(const Tree1D& t, const double* xo, double eps1, std::vecto
 //   B between siblings: diag(I (x) B^y, 0, 0) | diag(0, B^x (x) I, 0) | diag(0, 0, B^x (x) B^y)
 //   R = [[E_x (x) R^y, 0, 0], [0, R^x (x) E_y, 0], [(B^x V'^x*)_sel (x) R^y, R^x (x) (B^y V'^y*)_sel, R^x (x) R^y]]
 //   W = diag(E_x (x) W^y, W^x (x) E_y, W^x (x) W^y)
+// A dimension that does not split at a level (its 1D node is already a leaf: Def. 3.3 (2), (3))
+// keeps the parent's 1D node for every child: its selector E and transfer R (or W) are the
+// identity and it has no sibling terms (the same derivation with a single child in that
+// dimension), and siblings differ only in the other dimension.
 template <typename R> void Hss<R>::assemble_2d() {
   const Plan& pl = *pl_;
   const int L = pl.L;
   const Tree1D &tx = pl.tx, &ty = pl.ty;
+  auto gx = [&](int l, int p) -> const Gen1D<R>& { return gx_[pl.lvx(l)][pl.ix[l][p]]; };
+  auto gy = [&](int l, int p) -> const Gen1D<R>& { return gy_[pl.lvy(l)][pl.iy[l][p]]; };
+  auto dxo = [&](int l, int p) { const int i = pl.ix[l][p], lv = pl.lvx(l); return tx.c1[lv][i] - tx.c0[lv][i]; };
+  auto dyo = [&](int l, int p) { const int i = pl.iy[l][p], lv = pl.lvy(l); return ty.c1[lv][i] - ty.c0[lv][i]; };
   t_.assign(L + 1, {});
-  for (int l = 0; l <= L; ++l) t_[l].resize((size_t)1 << (2 * l));
+  for (int l = 0; l <= L; ++l) t_[l].resize((size_t)pl.nn[l]);
   for (int l = 1; l <= L; ++l)
-    for (int p = 0; p < (1 << (2 * l)); ++p) {
-      const int ix = morton_x(p, l), iy = morton_y(p, l);
-      const Gen1D<R>&ax = gx_[l][ix], &ay = gy_[l][iy];
-      const int dx = tx.c1[l][ix] - tx.c0[l][ix], dy = ty.c1[l][iy] - ty.c0[l][iy];
+    for (int p = 0; p < pl.nn[l]; ++p) {
+      const Gen1D<R>&ax = gx(l, p), &ay = gy(l, p);
+      const int dx = dxo(l, p), dy = dyo(l, p);
       Node2<R>& nd = t_[l][p];
       nd.ku = dx * ay.ru + ax.ru * dy + ax.ru * ay.ru;
       nd.kv = dx * ay.rv + ax.rv * dy + ax.rv * ay.rv;
@@ -326,19 +346,19 @@ template <typename R> void Hss<R>::assemble_2d() {
     std::vector<GatherD<R>> ga;
     std::vector<FaceD<R>> fc;
     std::vector<KronD<R>> kr;
-    const int nleaf = 1 << (2 * L);
-    for (int p = 0; p < nleaf; ++p) {
+    const int Lx = pl.Lx, Ly = pl.Ly;
+    for (int p = 0; p < pl.nn[L]; ++p) {
       const int ix = pl.leaf_lx[p], iy = pl.leaf_ly[p];
-      const Gen1D<R>&ax = gx_[L][ix], &ay = gy_[L][iy];
+      const Gen1D<R>&ax = gx_[Lx][ix], &ay = gy_[Ly][iy];
       const int r0 = pl.r0[L][p], m = pl.m[L][p];
-      const int dx = tx.c1[L][ix] - tx.c0[L][ix], dy = ty.c1[L][iy] - ty.c0[L][iy];
+      const int dx = tx.c1[Lx][ix] - tx.c0[Lx][ix], dy = ty.c1[Ly][iy] - ty.c0[Ly][iy];
       Node2<R>& nd = t_[L][p];
       Mat<R> Dx = tmp_.mat<R>(m, dx), Dy = tmp_.mat<R>(m, dy);
       Mat<R> Ux = tmp_.mat<R>(m, ax.ru), Uy = tmp_.mat<R>(m, ay.ru);
-      ps.push_back({pl.x2 + r0, m, tx.c0[L][ix], dx, pl.nx, Dx.p, Dx.ld});
-      ps.push_back({pl.y2 + r0, m, ty.c0[L][iy], dy, pl.ny, Dy.p, Dy.ld});
-      ga.push_back({ax.U.p, Ux.p, pl.posx + r0, m, ax.ru, ax.U.ld, Ux.ld, -tx.r0[L][ix]});
-      ga.push_back({ay.U.p, Uy.p, pl.posy + r0, m, ay.ru, ay.U.ld, Uy.ld, -ty.r0[L][iy]});
+      ps.push_back({pl.x2 + r0, m, tx.c0[Lx][ix], dx, pl.nx, Dx.p, Dx.ld});
+      ps.push_back({pl.y2 + r0, m, ty.c0[Ly][iy], dy, pl.ny, Dy.p, Dy.ld});
+      ga.push_back({ax.U.p, Ux.p, pl.posx + r0, m, ax.ru, ax.U.ld, Ux.ld, -tx.r0[Lx][ix]});
+      ga.push_back({ay.U.p, Uy.p, pl.posy + r0, m, ay.ru, ay.U.ld, Uy.ld, -ty.r0[Ly][iy]});
       nd.D = keep_.mat<R>(m, dx * dy);
       nd.U = keep_.mat<R>(m, nd.ku);
       nd.V = keep_.mat<R>(dx * dy, nd.kv);
@@ -366,27 +386,25 @@ template <typename R> void Hss<R>::assemble_2d() {
     std::vector<KronD<R>> kr;
     std::vector<Mat<R>> ids;
     std::vector<GemmD<R>> gm;
-    const int cl = l + 1;
-    for (int p = 0; p < (1 << (2 * l)); ++p) {
-      const int tix = morton_x(p, l), tiy = morton_y(p, l);
-      const Gen1D<R>&tX = gx_[l][tix], &tY = gy_[l][tiy];
-      const int dxt = tx.c1[l][tix] - tx.c0[l][tix], dyt = ty.c1[l][tiy] - ty.c0[l][tiy];
+    const int cl = l + 1, F = pl.fan[l];
+    const bool sx = pl.splitx(l), sy = pl.splity(l);
+    for (int p = 0; p < pl.nn[l]; ++p) {
+      const Gen1D<R>&tX = gx(l, p), &tY = gy(l, p);
+      const int dxt = dxo(l, p), dyt = dyo(l, p);
       Node2<R>& tau = t_[l][p];
-      for (int c = 0; c < 4; ++c) {
-        const int i = c >> 1, j = c & 1;
-        const int cx = 2 * tix + i, cy = 2 * tiy + j;
-        const Gen1D<R>&gxc = gx_[cl][cx], &gyc = gy_[cl][cy];
-        const int dxc = tx.c1[cl][cx] - tx.c0[cl][cx], dyc = ty.c1[cl][cy] - ty.c0[cl][cy];
-        Node2<R>& ch = t_[cl][4 * p + c];
+      for (int c = 0; c < F; ++c) {
+        const int q = F * p + c, i = pl.cxi(l, c), j = pl.cyj(l, c);
+        const Gen1D<R>&gxc = gx(cl, q), &gyc = gy(cl, q);
+        const int dxc = dxo(cl, q), dyc = dyo(cl, q);
+        Node2<R>& ch = t_[cl][q];
         const int r1 = dxc * gyc.ru, r2 = gxc.ru * dyc;
         // B_{c, c'}
-        for (int c2 = 0; c2 < 4; ++c2) {
+        for (int c2 = 0; c2 < F; ++c2) {
           if (c2 == c) continue;
-          const int i2 = c2 >> 1, j2 = c2 & 1;
-          const int cx2 = 2 * tix + i2, cy2 = 2 * tiy + j2;
-          const Gen1D<R>&gx2 = gx_[cl][cx2], &gy2 = gy_[cl][cy2];
-          const int dx2 = tx.c1[cl][cx2] - tx.c0[cl][cx2], dy2 = ty.c1[cl][cy2] - ty.c0[cl][cy2];
-          Node2<R>& sib = t_[cl][4 * p + c2];
+          const int q2 = F * p + c2, i2 = pl.cxi(l, c2), j2 = pl.cyj(l, c2);
+          const Gen1D<R>&gx2 = gx(cl, q2), &gy2 = gy(cl, q2);
+          const int dx2 = dxo(cl, q2), dy2 = dyo(cl, q2);
+          Node2<R>& sib = t_[cl][q2];
           Mat<R> B = keep_.mat<R>(ch.ku, sib.kv, true);
           ch.B[c2] = B;
           const int v1 = dx2 * gy2.rv, v2 = gx2.rv * dy2;
@@ -400,10 +418,9 @@ template <typename R> void Hss<R>::assemble_2d() {
           }
         }
         if (l == 0) continue;
-        // selectors and (B V'^*) blocks of the 1D siblings
-        const int sx = 2 * tix + (1 - i), sy = 2 * tiy + (1 - j);
-        const int offi = i ? (dxt - dxc) : 0, offi2 = i ? 0 : dxc;
-        const int offj = j ? (dyt - dyc) : 0, offj2 = j ? 0 : dyc;
+        // selectors and (B V'^*) blocks of the 1D siblings (only in a dimension that splits)
+        const int offi = sx ? (i ? (dxt - dxc) : 0) : 0, offi2 = i ? 0 : dxc;
+        const int offj = sy ? (j ? (dyt - dyc) : 0) : 0, offj2 = j ? 0 : dyc;
         const int dxs = dxt - dxc, dys = dyt - dyc;
         Mat<R> Ex = tmp_.mat<R>(dxc, dxt, true);
         Mat<R> Ey = tmp_.mat<R>(dyc, dyt, true);
@@ -411,29 +428,39 @@ template <typename R> void Hss<R>::assemble_2d() {
         ids.push_back(Ey.block(0, offj, dyc, dyc));
         Mat<R> BVx = tmp_.mat<R>(gxc.ru, dxt, true);
         Mat<R> BVy = tmp_.mat<R>(gyc.ru, dyt, true);
-        gm.push_back(gd<R>(gxc.Bs, OP_N, gx_[cl][sx].V, OP_C, BVx.block(0, offi2, gxc.ru, dxs)));
-        gm.push_back(gd<R>(gyc.Bs, OP_N, gy_[cl][sy].V, OP_C, BVy.block(0, offj2, gyc.ru, dys)));
+        if (sx) {
+          const int sxi = 2 * pl.ix[l][p] + (1 - i);
+          gm.push_back(gd<R>(gxc.Bs, OP_N, gx_[pl.lvx(cl)][sxi].V, OP_C, BVx.block(0, offi2, gxc.ru, dxs)));
+        }
+        if (sy) {
+          const int syj = 2 * pl.iy[l][p] + (1 - j);
+          gm.push_back(gd<R>(gyc.Bs, OP_N, gy_[pl.lvy(cl)][syj].V, OP_C, BVy.block(0, offj2, gyc.ru, dys)));
+        }
+        // 1D transfers of the children (identity, A == nullptr, in a dimension that does not split)
+        const cplx<R>* Rx = sx ? gxc.R_.p : nullptr;
+        const cplx<R>* Ry = sy ? gyc.R_.p : nullptr;
+        const cplx<R>* Wx = sx ? gxc.W.p : nullptr;
+        const cplx<R>* Wy = sy ? gyc.W.p : nullptr;
+        const int ldRx = sx ? gxc.R_.ld : 1, ldRy = sy ? gyc.R_.ld : 1, ldWx = sx ? gxc.W.ld : 1, ldWy = sy ? gyc.W.ld : 1;
         // R_c (ku_c x ku_tau)
         Mat<R> Rm = keep_.mat<R>(ch.ku, tau.ku, true);
         ch.R_ = Rm;
         const int c1 = dxt * tY.ru, c2 = tX.ru * dyt;
-        kr.push_back({Ex.p, gyc.R_.p, Rm.p, dxc, dxt, Ex.ld, gyc.ru, tY.ru, gyc.R_.ld, Rm.ld, R(1)});
-        kr.push_back({BVx.p, gyc.R_.p, Rm.at(r1 + r2, 0), gxc.ru, dxt, BVx.ld, gyc.ru, tY.ru, gyc.R_.ld, Rm.ld,
-                      R(1)});
-        kr.push_back({gxc.R_.p, Ey.p, Rm.at(r1, c1), gxc.ru, tX.ru, gxc.R_.ld, dyc, dyt, Ey.ld, Rm.ld, R(1)});
-        kr.push_back({gxc.R_.p, BVy.p, Rm.at(r1 + r2, c1), gxc.ru, tX.ru, gxc.R_.ld, gyc.ru, dyt, BVy.ld, Rm.ld,
-                      R(1)});
-        kr.push_back({gxc.R_.p, gyc.R_.p, Rm.at(r1 + r2, c1 + c2), gxc.ru, tX.ru, gxc.R_.ld, gyc.ru, tY.ru,
-                      gyc.R_.ld, Rm.ld, R(1)});
+        kr.push_back({Ex.p, Ry, Rm.p, dxc, dxt, Ex.ld, gyc.ru, tY.ru, ldRy, Rm.ld, R(1)});
+        if (sx)
+          kr.push_back({BVx.p, Ry, Rm.at(r1 + r2, 0), gxc.ru, dxt, BVx.ld, gyc.ru, tY.ru, ldRy, Rm.ld, R(1)});
+        kr.push_back({Rx, Ey.p, Rm.at(r1, c1), gxc.ru, tX.ru, ldRx, dyc, dyt, Ey.ld, Rm.ld, R(1)});
+        if (sy)
+          kr.push_back({Rx, BVy.p, Rm.at(r1 + r2, c1), gxc.ru, tX.ru, ldRx, gyc.ru, dyt, BVy.ld, Rm.ld, R(1)});
+        kr.push_back({Rx, Ry, Rm.at(r1 + r2, c1 + c2), gxc.ru, tX.ru, ldRx, gyc.ru, tY.ru, ldRy, Rm.ld, R(1)});
         // W_c (kv_c x kv_tau)
         Mat<R> Wm = keep_.mat<R>(ch.kv, tau.kv, true);
         ch.W = Wm;
         const int q1 = dxc * gyc.rv, q2 = gxc.rv * dyc;
         const int e1 = dxt * tY.rv, e2 = tX.rv * dyt;
-        kr.push_back({Ex.p, gyc.W.p, Wm.p, dxc, dxt, Ex.ld, gyc.rv, tY.rv, gyc.W.ld, Wm.ld, R(1)});
-        kr.push_back({gxc.W.p, Ey.p, Wm.at(q1, e1), gxc.rv, tX.rv, gxc.W.ld, dyc, dyt, Ey.ld, Wm.ld, R(1)});
-        kr.push_back({gxc.W.p, gyc.W.p, Wm.at(q1 + q2, e1 + e2), gxc.rv, tX.rv, gxc.W.ld, gyc.rv, tY.rv, gyc.W.ld,
-                      Wm.ld, R(1)});
+        kr.push_back({Ex.p, Wy, Wm.p, dxc, dxt, Ex.ld, gyc.rv, tY.rv, ldWy, Wm.ld, R(1)});
+        kr.push_back({Wx, Ey.p, Wm.at(q1, e1), gxc.rv, tX.rv, ldWx, dyc, dyt, Ey.ld, Wm.ld, R(1)});
+        kr.push_back({Wx, Wy, Wm.at(q1 + q2, e1 + e2), gxc.rv, tX.rv, ldWx, gyc.rv, tY.rv, ldWy, Wm.ld, R(1)});
       }
     }
     ops_.set_identity(ids);
@@ -488,14 +515,15 @@ template <typename R> void Hss<R>::recompress(double eps) {
     std::vector<GemmD<R>> gm;
     for (auto& tau : t_[l]) (void)tau;
     const int nn = (int)t_[l].size();
+    const int F = pl_->fan[l];
     for (int p = 0; p < nn; ++p) {
       Node2<R>& tau = t_[l][p];
       int su = 0, sv = 0;
-      for (int c = 0; c < 4; ++c) { su += t_[l + 1][4 * p + c].pu; sv += t_[l + 1][4 * p + c].pv; }
+      for (int c = 0; c < F; ++c) { su += t_[l + 1][F * p + c].pu; sv += t_[l + 1][F * p + c].pv; }
       Mat<R> S1 = tmp_.mat<R>(su, tau.ku), S2 = tmp_.mat<R>(sv, tau.kv);
       int ou = 0, ov = 0;
-      for (int c = 0; c < 4; ++c) {
-        Node2<R>& ch = t_[l + 1][4 * p + c];
+      for (int c = 0; c < F; ++c) {
+        Node2<R>& ch = t_[l + 1][F * p + c];
         gm.push_back(gd<R>(ch.F, OP_N, ch.R_, OP_N, S1.block(ou, 0, ch.pu, tau.ku)));
         gm.push_back(gd<R>(ch.G, OP_N, ch.W, OP_N, S2.block(ov, 0, ch.pv, tau.kv)));
         ou += ch.pu; ov += ch.pv;
@@ -528,8 +556,8 @@ template <typename R> void Hss<R>::recompress(double eps) {
       qf.push_back(Q[p]);
       qf.push_back(Q[nn + p]);
       int ou = 0, ov = 0;
-      for (int c = 0; c < 4; ++c) {
-        Node2<R>& ch = t_[l + 1][4 * p + c];
+      for (int c = 0; c < F; ++c) {
+        Node2<R>& ch = t_[l + 1][F * p + c];
         ch.R_ = Rs.block(ou, 0, ch.pu, tau.pu);
         ch.W = Ws.block(ov, 0, ch.pv, tau.pv);
         ou += ch.pu; ov += ch.pv;
@@ -545,12 +573,13 @@ template <typename R> void Hss<R>::recompress(double eps) {
     auto tk = tmp_.mark();
     std::vector<GemmD<R>> g1, g2;
     std::vector<Mat<R>> outs;
-    for (int p = 0; p < (1 << (2 * l)); ++p)
-      for (int c = 0; c < 4; ++c) {
-        Node2<R>& ch = t_[l + 1][4 * p + c];
-        for (int c2 = 0; c2 < 4; ++c2) {
+    const int F = pl_->fan[l];
+    for (int p = 0; p < pl_->nn[l]; ++p)
+      for (int c = 0; c < F; ++c) {
+        Node2<R>& ch = t_[l + 1][F * p + c];
+        for (int c2 = 0; c2 < F; ++c2) {
           if (c2 == c) continue;
-          Node2<R>& sb = t_[l + 1][4 * p + c2];
+          Node2<R>& sb = t_[l + 1][F * p + c2];
           Mat<R> T1 = tmp_.mat<R>(ch.ku, sb.pv);
           Mat<R> Bn = keep_.mat<R>(ch.pu, sb.pv);
           g1.push_back(gd<R>(ch.B[c2], OP_N, sb.G, OP_C, T1));
@@ -568,19 +597,20 @@ template <typename R> void Hss<R>::recompress(double eps) {
     auto mk = scr_.mark();
     auto tk = tmp_.mark();
     const int nn = (int)t_[l].size();
+    const int F = pl_->fan[l - 1];
     std::vector<Mat<R>> Ct;
     std::vector<CopyD<R>> cp;
     std::vector<R*> sdev;
     for (int q = 0; q < nn; ++q) {
-      const int p = q >> 2, c = q & 3;
+      const int p = q / F, c = q % F;
       Node2<R>& ch = t_[l][q];
       const Node2<R>& tau = t_[l - 1][p];
       int w = 0;
-      for (int c2 = 0; c2 < 4; ++c2) if (c2 != c) w += t_[l][4 * p + c2].pv;
+      for (int c2 = 0; c2 < F; ++c2) if (c2 != c) w += t_[l][F * p + c2].pv;
       const int rt = (l >= 2) ? (int)tau.SU.size() : 0;
       Mat<R> cu = tmp_.mat<R>(w + rt, ch.pu);
       int o = 0;
-      for (int c2 = 0; c2 < 4; ++c2) {
+      for (int c2 = 0; c2 < F; ++c2) {
         if (c2 == c) continue;
         const Mat<R>& B = ch.B[c2];
         cp.push_back({B.p, cu.at(o, 0), B.n, B.m, B.ld, cu.ld, OP_C, R(1), R(0)});
@@ -595,17 +625,17 @@ template <typename R> void Hss<R>::recompress(double eps) {
       Ct.push_back(cu);
     }
     for (int q = 0; q < nn; ++q) {
-      const int p = q >> 2, c = q & 3;
+      const int p = q / F, c = q % F;
       Node2<R>& ch = t_[l][q];
       const Node2<R>& tau = t_[l - 1][p];
       int w = 0;
-      for (int c2 = 0; c2 < 4; ++c2) if (c2 != c) w += t_[l][4 * p + c2].pu;
+      for (int c2 = 0; c2 < F; ++c2) if (c2 != c) w += t_[l][F * p + c2].pu;
       const int rt = (l >= 2) ? (int)tau.SV.size() : 0;
       Mat<R> cv = tmp_.mat<R>(w + rt, ch.pv);
       int o = 0;
-      for (int c2 = 0; c2 < 4; ++c2) {
+      for (int c2 = 0; c2 < F; ++c2) {
         if (c2 == c) continue;
-        const Mat<R>& B = t_[l][4 * p + c2].B[c];    // B_{c', c}: pu_{c'} x pv_c
+        const Mat<R>& B = t_[l][F * p + c2].B[c];    // B_{c', c}: pu_{c'} x pv_c
         cp.push_back({B.p, cv.at(o, 0), B.m, B.n, B.ld, cv.ld, OP_N, R(1), R(0)});
         o += B.m;
       }
@@ -630,12 +660,12 @@ template <typename R> void Hss<R>::recompress(double eps) {
       ch.SV = S[nn + q];
     }
     for (int q = 0; q < nn; ++q) {
-      const int p = q >> 2, c = q & 3;
+      const int p = q / F, c = q % F;
       Node2<R>& ch = t_[l][q];
       const Mat<R>& Pc = P[q];
-      for (int c2 = 0; c2 < 4; ++c2) {
+      for (int c2 = 0; c2 < F; ++c2) {
         if (c2 == c) continue;
-        const Mat<R>& Qc2 = P[nn + 4 * p + c2];
+        const Mat<R>& Qc2 = P[nn + F * p + c2];
         Mat<R> T1 = tmp_.mat<R>(ch.B[c2].m, Qc2.n);
         Mat<R> Bn = keep_.mat<R>(Pc.n, Qc2.n);
         g1.push_back(gd<R>(ch.B[c2], OP_N, Qc2, OP_N, T1));
@@ -657,8 +687,9 @@ template <typename R> void Hss<R>::recompress(double eps) {
         ch.U = Un;
         ch.V = Vn;
       } else {
-        for (int c3 = 0; c3 < 4; ++c3) {
-          Node2<R>& gc = t_[l + 1][4 * q + c3];
+        const int F1 = pl_->fan[l];
+        for (int c3 = 0; c3 < F1; ++c3) {
+          Node2<R>& gc = t_[l + 1][F1 * q + c3];
           Mat<R> Rn = keep_.mat<R>(gc.R_.m, Pc.n), Wn = keep_.mat<R>(gc.W.m, Qc.n);
           g1.push_back(gd<R>(gc.R_, OP_N, Pc, OP_N, Rn));
           g1.push_back(gd<R>(gc.W, OP_N, Qc, OP_N, Wn));
@@ -692,6 +723,7 @@ template <typename R> void Hss<R>::build(double eps) {
 template <typename R> void Hss<R>::factor_level(int l) {
   const int L = pl_->L;
   Arena& fa = *fac_[l];
+  const int F = l < L ? pl_->fan[l] : 0;
   auto mk = scr_.mark();
   auto tk = tmp_.mark();
   const int nn = (int)t_[l].size();
@@ -711,18 +743,18 @@ template <typename R> void Hss<R>::factor_level(int l) {
     } else {
       // merge the children (Sec. 2.3): D+ blocks, U+ = stack U2_c R_c, V+ = stack V2_c W_c
       int rows = 0, cols = 0;
-      for (int c = 0; c < 4; ++c) { rows += t_[l + 1][4 * p + c].rows2; cols += t_[l + 1][4 * p + c].kv; }
+      for (int c = 0; c < F; ++c) { rows += t_[l + 1][F * p + c].rows2; cols += t_[l + 1][F * p + c].kv; }
       nd.m = rows; nd.n = cols;
       nd.Wk = fa.template mat<R>(rows, nd.ku + cols);
       Vs[p] = tmp_.mat<R>(cols, nd.kv);
       int ro = 0;
-      for (int c = 0; c < 4; ++c) {
-        Node2<R>& a = t_[l + 1][4 * p + c];
+      for (int c = 0; c < F; ++c) {
+        Node2<R>& a = t_[l + 1][F * p + c];
         Mat<R> U2 = a.Wk.block(a.n1, 0, a.rows2, a.ku);
         gm.push_back(gd<R>(U2, OP_N, a.R_, OP_N, nd.Wk.block(ro, 0, a.rows2, nd.ku)));
         int co = nd.ku;
-        for (int c2 = 0; c2 < 4; ++c2) {
-          Node2<R>& b = t_[l + 1][4 * p + c2];
+        for (int c2 = 0; c2 < F; ++c2) {
+          Node2<R>& b = t_[l + 1][F * p + c2];
           Mat<R> dst = nd.Wk.block(ro, co, a.rows2, b.kv);
           if (c2 == c) {
             Mat<R> D22 = a.Wk.block(a.n1, a.ku, a.rows2, a.kv);
@@ -738,8 +770,8 @@ template <typename R> void Hss<R>::factor_level(int l) {
         ro += a.rows2;
       }
       int vo = 0;
-      for (int c = 0; c < 4; ++c) {
-        Node2<R>& a = t_[l + 1][4 * p + c];
+      for (int c = 0; c < F; ++c) {
+        Node2<R>& a = t_[l + 1][F * p + c];
         gm.push_back(gd<R>(a.V2, OP_N, a.W, OP_N, Vs[p].block(vo, 0, a.kv, nd.kv)));
         vo += a.kv;
       }
@@ -754,12 +786,12 @@ template <typename R> void Hss<R>::factor_level(int l) {
     for (int p = 0, gi = 0; p < nn; ++p) {
       Node2<R>& nd = t_[l][p];
       int ro = 0;
-      for (int c = 0; c < 4; ++c) {
-        Node2<R>& a = t_[l + 1][4 * p + c];
+      for (int c = 0; c < F; ++c) {
+        Node2<R>& a = t_[l + 1][F * p + c];
         gi++;   // U+ product
         int co = nd.ku;
-        for (int c2 = 0; c2 < 4; ++c2) {
-          Node2<R>& b = t_[l + 1][4 * p + c2];
+        for (int c2 = 0; c2 < F; ++c2) {
+          Node2<R>& b = t_[l + 1][F * p + c2];
           if (c2 != c) {
             const GemmD<R>& t1 = gm[gi++];
             Mat<R> T1;
@@ -840,22 +872,23 @@ template <typename R> void Hss<R>::factor_level(int l) {
 
 template <typename R> void Hss<R>::factor_root() {
   Arena& fa = *fac_[0];
+  const int F = pl_->fan[0];
   // root: D+ = P_root R_root
   {
     auto mk = scr_.mark();
     auto tk = tmp_.mark();
     int rows = 0, cols = 0;
-    for (int c = 0; c < 4; ++c) { rows += t_[1][c].rows2; cols += t_[1][c].kv; }
+    for (int c = 0; c < F; ++c) { rows += t_[1][c].rows2; cols += t_[1][c].kv; }
     NH_REQUIRE(rows >= cols, ST_ERANK, "root block has fewer rows than columns");
     root_rows_ = rows; root_cols_ = cols;
     Droot_ = fa.template mat<R>(rows, cols);
     std::vector<CopyD<R>> cp;
     std::vector<GemmD<R>> g1, g2;
     int ro = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < F; ++c) {
       Node2<R>& a = t_[1][c];
       int co = 0;
-      for (int c2 = 0; c2 < 4; ++c2) {
+      for (int c2 = 0; c2 < F; ++c2) {
         Node2<R>& b = t_[1][c2];
         if (c2 == c) {
           Mat<R> D22 = a.Wk.block(a.n1, a.ku, a.rows2, a.kv);
@@ -886,7 +919,7 @@ template <typename R> void Hss<R>::factor() {
   const int L = pl_->L;
   fac_.clear();
   for (int l = 0; l <= L; ++l) {
-    fac_.emplace_back(new Arena((size_t)64 << 20));
+    fac_.emplace_back(new Arena((size_t)64 << 20, true));
     fac_.back()->set_stream(st_);
   }
   for (int l = L; l >= 1; --l) factor_level(l);
@@ -961,11 +994,12 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
     ops_.apply_q_left(qp, cpm, true);
     if (l > 1) {
       std::vector<CopyD<R>> cp;
+      const int F = pl_->fan[l - 1];
       for (int p = 0; p < (int)t_[l - 1].size(); ++p) {
         int ro = 0;
-        for (int c = 0; c < 4; ++c) {
-          Node2<R>& a = t_[l][4 * p + c];
-          cp.push_back({Fl[l][4 * p + c].at(a.n1, 0), Fl[l - 1][p].at(ro, 0), a.rows2, s, Fl[l][4 * p + c].ld,
+        for (int c = 0; c < F; ++c) {
+          Node2<R>& a = t_[l][F * p + c];
+          cp.push_back({Fl[l][F * p + c].at(a.n1, 0), Fl[l - 1][p].at(ro, 0), a.rows2, s, Fl[l][F * p + c].ld,
                         Fl[l - 1][p].ld, OP_N, R(1), R(0)});
           ro += a.rows2;
         }
@@ -978,7 +1012,7 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
   {
     std::vector<CopyD<R>> cp;
     int ro = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < pl_->fan[0]; ++c) {
       Node2<R>& a = t_[1][c];
       cp.push_back({Fl[1][c].at(a.n1, 0), froot.at(ro, 0), a.rows2, s, Fl[1][c].ld, froot.ld, OP_N, R(1), R(0)});
       ro += a.rows2;
@@ -993,14 +1027,15 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
   std::vector<Mat<R>> parentC = {croot};
   for (int l = 1; l <= L; ++l) {
     const int nn = (int)t_[l].size();
+    const int F = pl_->fan[l - 1];
     Cl[l].resize(nn);
     Bl[l].resize(nn);
     std::vector<Mat<R>> Z(nn), C2(nn);
     std::vector<GemmD<R>> gz;
     for (int q = 0; q < nn; ++q) {
-      const int p = q >> 2, c = q & 3;
+      const int p = q / F, c = q % F;
       int off = 0;
-      for (int c2 = 0; c2 < c; ++c2) off += t_[l][4 * p + c2].kv;
+      for (int c2 = 0; c2 < c; ++c2) off += t_[l][F * p + c2].kv;
       const Mat<R>& pc = (l == 1) ? parentC[0] : Cl[l - 1][p];
       C2[q] = pc.block(off, 0, t_[l][q].kv, s);
       Z[q] = scr_.mat<R>(t_[l][q].kv, s);
@@ -1012,7 +1047,7 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
     {
       std::vector<GemmD<R>> g0;
       for (int q = 0; q < nn; ++q) {
-        const int p = q >> 2;
+        const int p = q / F;
         if (l >= 2) g0.push_back(gd<R>(t_[l][q].R_, OP_N, Bl[l - 1][p], OP_N, Bl[l][q]));
         else g0.push_back(gd<R>(t_[l][q].R_, OP_N, Bl[l][q], OP_N, Bl[l][q], R(0), R(0)));
       }
@@ -1021,11 +1056,11 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
         for (auto& g : g0) { g.k = 0; g.A = nullptr; g.B = nullptr; }
       }
       ops_.gemm(g0);
-      for (int j = 1; j < 4; ++j) {
+      for (int j = 1; j < F; ++j) {
         std::vector<GemmD<R>> gj;
         for (int q = 0; q < nn; ++q) {
-          const int p = q >> 2, c = q & 3, c2 = (c + j) & 3;
-          gj.push_back(gd<R>(t_[l][q].B[c2], OP_N, Z[4 * p + c2], OP_N, Bl[l][q], R(1), R(1)));
+          const int p = q / F, c = q % F, c2 = (c + j) % F;
+          gj.push_back(gd<R>(t_[l][q].B[c2], OP_N, Z[F * p + c2], OP_N, Bl[l][q], R(1), R(1)));
         }
         ops_.gemm(gj);
       }
@@ -1112,11 +1147,12 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
     std::vector<GemmD<R>> gf, gb, gc;
     std::vector<CopyD<R>> cp;
     Bb[l].resize(nn);
+    const int F = pl_->fan[l - 1];
     for (int q = 0; q < nn; ++q) {
-      const int p = q >> 2, c = q & 3;
+      const int p = q / F, c = q % F;
       Node2<R>& nd = t_[l][q];
       int off = 0;
-      for (int c2 = 0; c2 < c; ++c2) off += t_[l][4 * p + c2].kv;
+      for (int c2 = 0; c2 < c; ++c2) off += t_[l][F * p + c2].kv;
       const Mat<R>& dst = (l == 1) ? crootb : Yb[l - 1][p];
       C2b[q] = dst.block(off, 0, nd.kv, s);
       F1b[q] = Fb[l][q].block(0, 0, nd.n1, s);
@@ -1136,20 +1172,22 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
     }
     ops_.gemm(gb);
     ops_.gemm(gc);
-    if (l < L)
-      for (int c = 0; c < 4; ++c) {
+    if (l < L) {
+      const int F1 = pl_->fan[l];
+      for (int c = 0; c < F1; ++c) {
         std::vector<GemmD<R>> g;
         for (int q = 0; q < nn; ++q)
-          g.push_back(gd<R>(t_[l + 1][4 * q + c].R_, OP_C, Bb[l + 1][4 * q + c], OP_N, Bb[l][q], R(1), R(1)));
+          g.push_back(gd<R>(t_[l + 1][F1 * q + c].R_, OP_C, Bb[l + 1][F1 * q + c], OP_N, Bb[l][q], R(1), R(1)));
         ops_.gemm(g);
       }
+    }
     // b_q = ... + sum_{c2 != c} B_{q,c2} z_{c2}  =>  zb_{q2} = sum_{q != q2} B_{q,c2}^* bb_q ; z = V2^* C2  =>  C2b += V2 zb
     std::vector<Mat<R>> Zb(nn);
     for (int q = 0; q < nn; ++q) Zb[q] = scr_.mat<R>(std::max(t_[l][q].kv, 1), s);
-    for (int j = 1; j < 4; ++j) {
+    for (int j = 1; j < F; ++j) {
       std::vector<GemmD<R>> g;
       for (int q2 = 0; q2 < nn; ++q2) {
-        const int p = q2 >> 2, c2 = q2 & 3, c = (c2 + j) & 3, q = 4 * p + c;
+        const int p = q2 / F, c2 = q2 % F, c = (c2 + j) % F, q = F * p + c;
         g.push_back(gd<R>(t_[l][q].B[c2], OP_C, Bb[l][q], OP_N, Zb[q2], R(1), j == 1 ? R(0) : R(1)));
       }
       ops_.gemm(g);
@@ -1165,7 +1203,7 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
   {
     std::vector<CopyD<R>> cp;
     int ro = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < pl_->fan[0]; ++c) {
       Node2<R>& a = t_[1][c];
       cp.push_back({frootb.at(ro, 0), Fb[1][c].at(a.n1, 0), a.rows2, s, frootb.ld, Fb[1][c].ld, OP_N, R(1), R(0)});
       ro += a.rows2;
@@ -1187,12 +1225,13 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
     ops_.apply_q_left(qo, co, false);
     if (l < L) {
       std::vector<CopyD<R>> cp;
+      const int F1 = pl_->fan[l];
       for (int p = 0; p < nn; ++p) {
         int ro = 0;
-        for (int c = 0; c < 4; ++c) {
-          Node2<R>& a = t_[l + 1][4 * p + c];
-          cp.push_back({Fb[l][p].at(ro, 0), Fb[l + 1][4 * p + c].at(a.n1, 0), a.rows2, s, Fb[l][p].ld,
-                        Fb[l + 1][4 * p + c].ld, OP_N, R(1), R(0)});
+        for (int c = 0; c < F1; ++c) {
+          Node2<R>& a = t_[l + 1][F1 * p + c];
+          cp.push_back({Fb[l][p].at(ro, 0), Fb[l + 1][F1 * p + c].at(a.n1, 0), a.rows2, s, Fb[l][p].ld,
+                        Fb[l + 1][F1 * p + c].ld, OP_N, R(1), R(0)});
           ro += a.rows2;
         }
       }
@@ -1231,10 +1270,11 @@ template <typename R> void Hss<R>::matvec(const cplx<R>* x, int ldx, int s, cplx
   for (int l = L - 1; l >= 1; --l) {
     xh[l].resize(t_[l].size());
     for (int p = 0; p < (int)t_[l].size(); ++p) xh[l][p] = scr_.mat<R>(t_[l][p].kv, s);
-    for (int c = 0; c < 4; ++c) {
+    const int F = pl_->fan[l];
+    for (int c = 0; c < F; ++c) {
       std::vector<GemmD<R>> g;
       for (int p = 0; p < (int)t_[l].size(); ++p)
-        g.push_back(gd<R>(t_[l + 1][4 * p + c].W, OP_C, xh[l + 1][4 * p + c], OP_N, xh[l][p], R(1), c ? R(1) : R(0)));
+        g.push_back(gd<R>(t_[l + 1][F * p + c].W, OP_C, xh[l + 1][F * p + c], OP_N, xh[l][p], R(1), c ? R(1) : R(0)));
       ops_.gemm(g);
     }
   }
@@ -1243,10 +1283,11 @@ template <typename R> void Hss<R>::matvec(const cplx<R>* x, int ldx, int s, cplx
     const int nn = (int)t_[l].size();
     yh[l].resize(nn);
     for (int q = 0; q < nn; ++q) yh[l][q] = scr_.mat<R>(t_[l][q].ku, s);
-    for (int j = 0; j < 4; ++j) {
+    const int F = pl_->fan[l - 1];
+    for (int j = 0; j < F; ++j) {
       std::vector<GemmD<R>> g;
       for (int q = 0; q < nn; ++q) {
-        const int p = q >> 2, c = q & 3;
+        const int p = q / F, c = q % F;
         if (j == 0) {
           if (l >= 2) g.push_back(gd<R>(t_[l][q].R_, OP_N, yh[l - 1][p], OP_N, yh[l][q]));
           else {
@@ -1255,8 +1296,8 @@ template <typename R> void Hss<R>::matvec(const cplx<R>* x, int ldx, int s, cplx
             g.push_back(z);
           }
         } else {
-          const int c2 = (c + j) & 3;
-          g.push_back(gd<R>(t_[l][q].B[c2], OP_N, xh[l][4 * p + c2], OP_N, yh[l][q], R(1), R(1)));
+          const int c2 = (c + j) % F;
+          g.push_back(gd<R>(t_[l][q].B[c2], OP_N, xh[l][F * p + c2], OP_N, yh[l][q], R(1), R(1)));
         }
       }
       ops_.gemm(g);
@@ -1305,10 +1346,11 @@ template <typename R> void Hss<R>::matvec_adj(const cplx<R>* y, int ldy, int s, 
   for (int l = L - 1; l >= 1; --l) {
     zh[l].resize(t_[l].size());
     for (int p = 0; p < (int)t_[l].size(); ++p) zh[l][p] = scr_.mat<R>(t_[l][p].ku, s);
-    for (int c = 0; c < 4; ++c) {
+    const int F = pl_->fan[l];
+    for (int c = 0; c < F; ++c) {
       std::vector<GemmD<R>> g;
       for (int p = 0; p < (int)t_[l].size(); ++p)
-        g.push_back(gd<R>(t_[l + 1][4 * p + c].R_, OP_C, zh[l + 1][4 * p + c], OP_N, zh[l][p], R(1), c ? R(1) : R(0)));
+        g.push_back(gd<R>(t_[l + 1][F * p + c].R_, OP_C, zh[l + 1][F * p + c], OP_N, zh[l][p], R(1), c ? R(1) : R(0)));
       ops_.gemm(g);
     }
   }
@@ -1316,10 +1358,11 @@ template <typename R> void Hss<R>::matvec_adj(const cplx<R>* y, int ldy, int s, 
     const int nn = (int)t_[l].size();
     xh[l].resize(nn);
     for (int q = 0; q < nn; ++q) xh[l][q] = scr_.mat<R>(t_[l][q].kv, s);
-    for (int j = 0; j < 4; ++j) {
+    const int F = pl_->fan[l - 1];
+    for (int j = 0; j < F; ++j) {
       std::vector<GemmD<R>> g;
       for (int q = 0; q < nn; ++q) {
-        const int p = q >> 2, c = q & 3;
+        const int p = q / F, c = q % F;
         if (j == 0) {
           if (l >= 2) g.push_back(gd<R>(t_[l][q].W, OP_N, xh[l - 1][p], OP_N, xh[l][q]));
           else {
@@ -1328,8 +1371,8 @@ template <typename R> void Hss<R>::matvec_adj(const cplx<R>* y, int ldy, int s, 
             g.push_back(z);
           }
         } else {
-          const int c2 = (c + j) & 3;
-          g.push_back(gd<R>(t_[l][4 * p + c2].B[c], OP_C, zh[l][4 * p + c2], OP_N, xh[l][q], R(1), R(1)));
+          const int c2 = (c + j) % F;
+          g.push_back(gd<R>(t_[l][F * p + c2].B[c], OP_C, zh[l][F * p + c2], OP_N, xh[l][q], R(1), R(1)));
         }
       }
       ops_.gemm(g);

@@ -10,10 +10,13 @@
 namespace nh {
 
 // ---------------------------------------------------------------- trees and point order
-// Equal-depth 1D binary trees T^x, T^y over the column index sets (bisection of the periodic
-// interval, Sec. 2.4) and their face-splitting product, the quadtree T = T^x . T^y
-// (Def. 3.3); nodes of level l are numbered in Morton order, child c = 2*bx + by of node p
-// is 4p + c (children order (1,1),(1,2),(2,1),(2,2) of the proof of Thm. 3.5).
+// 1D binary trees T^x (depth Lx) and T^y (depth Ly) over the column index sets (bisection of the
+// periodic interval, Sec. 2.4) and their face-splitting product T = T^x . T^y (Def. 3.3), of
+// depth L = max(Lx, Ly).  A level-l node splits in x when l < Lx and in y when l < Ly: four
+// children when both split (Def. 3.3 (4)), two when only one does (Def. 3.3 (2), (3): the other
+// 1D node is already a leaf).  The fan-out is the same for every node of a level.  Child c of node
+// p of level l is node fan[l] * p + c of level l + 1; with both splits c = 2 i + j for the x child
+// i and the y child j (children order (1,1),(1,2),(2,1),(2,2) of the proof of Thm. 3.5).
 struct Tree1D {
   int n = 0, L = 0;
   std::vector<std::vector<int>> c0, c1;   // column range of node (l, i)
@@ -23,7 +26,18 @@ struct Tree1D {
 
 struct Plan {
   int M = 0, nx = 0, ny = 0, L = 0, N = 0;
+  int Lx = 0, Ly = 0;                     // depths of T^x and T^y; L = max(Lx, Ly)
   Tree1D tx, ty;
+  std::vector<int> fan;                   // fan[l]: children of every level-l node (l < L)
+  std::vector<int> nn;                    // nodes per level
+  std::vector<std::vector<int>> ix, iy;   // (l, p) -> node of T^x at level lvx(l), of T^y at lvy(l)
+  int lvx(int l) const { return l < Lx ? l : Lx; }
+  int lvy(int l) const { return l < Ly ? l : Ly; }
+  bool splitx(int l) const { return l < Lx; }
+  bool splity(int l) const { return l < Ly; }
+  // x child and y child (0 or 1; 0 when that dimension does not split) of child c of a level-l node
+  int cxi(int l, int c) const { return splitx(l) ? (splity(l) ? c >> 1 : c) : 0; }
+  int cyj(int l, int c) const { return splity(l) ? (splitx(l) ? c & 1 : c) : 0; }
   // 2D: per level l, per node p: rows [r0, r0+m) in 2D order, columns [c0, c0+nc) in tree order
   std::vector<std::vector<int>> r0, m, c0, nc;
   std::vector<int> leaf_lx, leaf_ly;      // per leaf p: 1D leaf indices
@@ -39,7 +53,7 @@ struct Plan {
 // Build the plan: bins points on the device, sorts them (stable counting sort) into the
 // three orders and reads the per-bin counts back to size the trees.
 void make_plan(cudaStream_t st, Arena& keep, Arena& scr, const double* d_x, const double* d_y, int M, int nx, int ny,
-               int L, Plan& pl);
+               int Lx, int Ly, Plan& pl);
 
 // ---------------------------------------------------------------- HSS generators and URV factors
 template <typename R> struct Gen1D {    // one node of a 1D HSS (Sec. 2.2, Def. 2.2)

@@ -199,25 +199,22 @@ template void dft_matrix<float>(cudaStream_t, int, int, double, float2*);
 
 // ---------------------------------------------------------------- binning (Sec. 3.2 product tree)
 __global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y, int M, int nx, int ny,
-                      const int* __restrict__ leafx, const int* __restrict__ leafy, int L, int* key2d, int* keyx,
-                      int* keyy) {
+                      const int* __restrict__ leafx, const int* __restrict__ leafy, const int* __restrict__ leafid,
+                      int nly, int* key2d, int* keyx, int* keyy) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   int bx = (int)floor(x[j] * (double)nx);
   int by = (int)floor(y[j] * (double)ny);
   bx = min(max(bx, 0), nx - 1);
   by = min(max(by, 0), ny - 1);
-  const int lx = leafx[bx], ly = leafy[by];
-  int p = 0;
-  for (int b = 0; b < L; ++b) p |= ((((lx >> b) & 1) << 1) | ((ly >> b) & 1)) << (2 * b);
-  key2d[j] = p;
+  key2d[j] = leafid[leafx[bx] * nly + leafy[by]];
   keyx[j] = bx;
   keyy[j] = by;
 }
 
 void bin_points(cudaStream_t st, const double* x, const double* y, int M, int nx, int ny, const int* leafx,
-                const int* leafy, int L, int* key2d, int* keyx, int* keyy) {
-  k_bin<<<(M + 255) / 256, 256, 0, st>>>(x, y, M, nx, ny, leafx, leafy, L, key2d, keyx, keyy);
+                const int* leafy, const int* leafid, int nly, int* key2d, int* keyx, int* keyy) {
+  k_bin<<<(M + 255) / 256, 256, 0, st>>>(x, y, M, nx, ny, leafx, leafy, leafid, nly, key2d, keyx, keyy);
   NH_LAUNCH_CK();
 }
 

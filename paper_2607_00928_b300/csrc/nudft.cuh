@@ -34,9 +34,10 @@ template <typename R> void dft_matrix(cudaStream_t st, int n, int sign, double s
 
 // Stable counting sort of keys[0..M) in [0, nkeys): perm[pos] = j, counts[key] (device).
 void counting_sort(cudaStream_t st, Arena& ar, const int* keys, int M, int nkeys, int* perm, int* counts);
-// keys: key2d (Morton leaf), keyx (x bin), keyy (y bin)
+// keys: key2d (product-tree leaf: leafid[lx * nly + ly] for the 1D leaves lx, ly of the point's
+// bins), keyx (x bin), keyy (y bin)
 void bin_points(cudaStream_t st, const double* x, const double* y, int M, int nx, int ny, const int* leafx,
-                const int* leafy, int L, int* key2d, int* keyx, int* keyy);
+                const int* leafy, const int* leafid, int nly, int* key2d, int* keyx, int* keyy);
 // out[i] = in[perm[i]] (double), out_pos[i] = inv[perm[i]]
 void permute_double(cudaStream_t st, const double* in, const int* perm, int M, double* out);
 void inverse_perm(cudaStream_t st, const int* perm, int M, int* inv);

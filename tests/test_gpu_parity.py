@@ -272,3 +272,41 @@ def test_mixed_refinement_incremental_residual(nh):
         assert info["refine_relres"] <= 1e-11
     fp64_ms = {full: sum(v["ms"] for k, v in out[full][2].items() if k.endswith("_fp64")) for full in (False, True)}
     assert fp64_ms[False] < fp64_ms[True]
+
+
+# ------------------------------------------------------------------ unbalanced product trees (Def. 3.3 (2), (3))
+@pytest.mark.parametrize("nx,ny,mx,my,lx,ly,seed", [
+    (16, 16, 32, 16, 1, 2, 1),      # config 1 with 8 x 4 product leaves ("leaf 32")
+    (16, 64, 32, 64, 2, 4, 7),      # ny = 4 nx: square 4 x 4 leaves instead of equal-depth 4 x 16
+    (64, 16, 128, 16, 4, 2, 8),     # the other way round
+    (32, 32, 64, 32, 3, 1, 9),      # x split three times, y once: leaves 4 x 16
+])
+def test_unbalanced_tree_solve_matches_oracle(nh, nx, ny, mx, my, lx, ly, seed):
+    """T^x of depth lx and T^y of depth ly: below min(lx, ly) levels only the deeper tree splits
+    (binary product-tree levels).  The HSS forward map stays within the Thm. 3.7 bound of the
+    exact A, and the FP64 solve matches the dense oracle's least-squares solution to 1e-8."""
+    x, y = jittered_grid(mx, my, -0.25, 0.25, seed)
+    ct = complex_normal((nx * ny, 2), seed + 50)
+    f = orc.forward(x, y, ct, nx, ny)
+    h = nh.NudftHSS(x, y, nx, ny, eps=1e-10, levels=lx, levels_y=ly).factor()
+    info = h.info()
+    assert info["levels"] == max(lx, ly)
+    fa = to_np(h.apply(nh.FAST_FWD, torch.from_numpy(ct)))
+    assert relerr_cols(fa, f) < 100 * 1e-10
+    c = to_np(h.solve(torch.from_numpy(f)))
+    h.close()
+    cref, _, _ = orc.lstsq(orc.nudft_matrix(x, y, nx, ny), f)
+    assert relerr_cols(c, cref) < 1e-8
+
+
+def test_unbalanced_tree_mixed_refined(nh):
+    """Mixed precision on an unbalanced tree, refined with the FP64 residual to 1e-10."""
+    nx, ny = 32, 64
+    x, y = jittered_grid(64, 64, -0.3, 0.3, 12)
+    ct = complex_normal((nx * ny, 3), 13)
+    f = orc.forward(x, y, ct, nx, ny)
+    h = nh.NudftHSS(x, y, nx, ny, eps=1e-6, levels=2, levels_y=3, prec="mixed", refine_tol=1e-10,
+                    refine_max=12).factor()
+    c = to_np(h.solve(torch.from_numpy(f)))
+    h.close()
+    assert relerr_cols(c, ct) < 1e-8

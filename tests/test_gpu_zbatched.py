@@ -90,8 +90,8 @@ def test_config4_full_size_batch(nh):
     idx = np.random.default_rng(4).choice(ps[big]["x"].size, 16, replace=False)
     ref = orc.forward(ps[big]["x"][idx], ps[big]["y"][idx], ps[big]["c_true"], ps[big]["nx"], ps[big]["ny"])
     assert np.max(np.abs(fs[big].cpu().numpy()[idx] - ref)) < 1e-10 * np.max(np.abs(ref))
-    hs = nh.build_batched(ps, threads=16)
-    cs = nh.solve_batched(hs, fs, threads=16)
+    hs = nh.build_batched(ps, threads=8)
+    cs = nh.solve_batched(hs, fs, threads=8)
     for p, c in zip(ps, cs):
         assert _relcols(c.cpu().numpy(), p["c_true"]) < 1e-8
     for h in hs:
