@@ -250,6 +250,14 @@ nudft2_status nudft2_la_tsvd(int prec, void* d_ct, int64_t w, int64_t r, int64_t
 nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_q, int64_t ldq,
                            int grouped, void* stream);
 
+/* nudft2_la_qr_apply: Householder QR of A (m x n, ld lda) in place as in nudft2_la_qr, then
+ * C <- Q^* C (conj = 1) or C <- Q C (conj = 0) for C (m x s, ld ldc) by the streaming
+ * reflector kernels that the URV solve sweeps use (Sec. 2.3), with the 32-column panel factors
+ * (grouped = 0) or the merged 256-column blocks (grouped = 1).  s >= 0 (columns are taken in
+ * chunks of up to 16).  Synchronises the stream.  Errors: EINVAL. */
+nudft2_status nudft2_la_qr_apply(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_c, int64_t s,
+                                 int64_t ldc, int conj, int grouped, void* stream);
+
 /* nudft2_la_gemm: the batched complex GEMM behind every generator product of the construction,
  * factorization and solve:  C_b = alpha op_a(A_b) op_b(B_b) + beta C_b  for b < batch, with
  * X_b = X + b * stride_x (elements).  op: 0 = none, 1 = transpose, 2 = conjugate transpose.

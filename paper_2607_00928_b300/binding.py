@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_la_tsvd.argtypes = [ci, vp, i64, i64, i64, ctypes.c_double, vp, i64, ctypes.POINTER(ci),
                                  ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, ci, vp]
+    L.nudft2_la_qr_apply.argtypes = [ci, vp, i64, i64, i64, vp, i64, i64, ci, ci, vp]
     L.nudft2_la_gemm.argtypes = [ci, ci, ci, i64, i64, i64, ctypes.c_double, vp, i64, i64, vp, i64, i64,
                                  ctypes.c_double, vp, i64, i64, ci, vp]
     L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
@@ -93,7 +94,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
               "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_plsqr",
-              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_gemm", "nudft2_exact_apply",
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
@@ -175,6 +176,20 @@ def la_qr(A: torch.Tensor, grouped: bool = False):
     _check(lib().nudft2_la_qr(prec, ctypes.c_void_p(a.data_ptr()), m, n, m, ctypes.c_void_p(q.data_ptr()), m,
                               int(grouped), _stream()))
     return q.t(), torch.triu(a.t())
+
+
+def la_qr_apply(A: torch.Tensor, C: torch.Tensor, conj: bool, grouped: bool = False):
+    """Householder QR of A (m x n) by the library, then Q^* C (conj) or Q C for C (m x s) by the
+    streaming reflector kernels of the solve sweeps: (result m x s, R m x n)."""
+    m, n = A.shape
+    s = C.shape[1]
+    dt = A.dtype
+    prec = FP64 if dt == torch.complex128 else MIXED
+    a = A.t().contiguous()                          # column major
+    c = C.to(dt).t().contiguous()
+    _check(lib().nudft2_la_qr_apply(prec, ctypes.c_void_p(a.data_ptr()), m, n, m, ctypes.c_void_p(c.data_ptr()), s,
+                                    m, int(conj), int(grouped), _stream()))
+    return c.t(), torch.triu(a.t())
 
 
 _OPS = {"N": 0, "T": 1, "C": 2}

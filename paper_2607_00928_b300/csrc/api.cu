@@ -331,6 +331,23 @@ static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, int grou
 }
 
 template <typename R>
+static void la_qr_apply(void* d_a, int m, int n, int lda, void* d_c, int s, int ldc, bool conj, int grouped,
+                        cudaStream_t st) {
+  Arena scr, keep;
+  scr.set_stream(st);
+  keep.set_stream(st);
+  Ops<R> ops(st, &scr);
+  Mat<R> A;
+  A.p = (cplx<R>*)d_a; A.m = m; A.n = n; A.ld = lda;
+  auto Q = ops.qr({A}, keep);
+  if (grouped) ops.group_wy(Q, keep);
+  Mat<R> C;
+  C.p = (cplx<R>*)d_c; C.m = m; C.n = s; C.ld = ldc;
+  ops.apply_q_stream(Q, {C}, conj);
+  NH_CK(cudaStreamSynchronize(st));
+}
+
+template <typename R>
 static void la_gemm(int opa, int opb, int m, int n, int k, double alpha, const void* A, int lda, int64_t sa,
                     const void* B, int ldb, int64_t sb, double beta, void* C, int ldc, int64_t sc, int batch,
                     cudaStream_t st) {
@@ -1126,6 +1143,21 @@ nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t ld
       la_qr<double>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, grouped, (cudaStream_t)stream);
     else
       la_qr<float>(d_a, (int)m, (int)n, (int)lda, d_q, (int)ldq, grouped, (cudaStream_t)stream);
+  });
+}
+
+nudft2_status nudft2_la_qr_apply(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_c, int64_t s,
+                                 int64_t ldc, int conj, int grouped, void* stream) {
+  return guard([&] {
+    NH_REQUIRE(d_a && m >= 1 && n >= 1 && lda >= m && s >= 0 && (s == 0 || (d_c && ldc >= m)) && m < (1LL << 31) &&
+                   n < (1LL << 31) && s < (1LL << 31),
+               ST_EINVAL, "la_qr_apply: bad arguments");
+    if (prec == NUDFT2_FP64)
+      la_qr_apply<double>(d_a, (int)m, (int)n, (int)lda, d_c, (int)s, (int)ldc, conj != 0, grouped,
+                          (cudaStream_t)stream);
+    else
+      la_qr_apply<float>(d_a, (int)m, (int)n, (int)lda, d_c, (int)s, (int)ldc, conj != 0, grouped,
+                         (cudaStream_t)stream);
   });
 }
 

@@ -803,7 +803,7 @@ template <typename R> void Hss<R>::factor_level(int l) {
         }
         ro += a.rows2;
       }
-      gi += 4;   // V+ products
+      gi += F;   // V+ products
     }
     ops_.gemm(g2);
   }
@@ -990,8 +990,8 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
       qp.push_back(nd.P);
       cpm.push_back(Fl[l][p].block(0, 0, nd.mc, s));
     }
-    ops_.apply_q_left(qo, co, true);
-    ops_.apply_q_left(qp, cpm, true);
+    ops_.apply_q_sweep(qo, co, true);
+    ops_.apply_q_sweep(qp, cpm, true);
     if (l > 1) {
       std::vector<CopyD<R>> cp;
       const int F = pl_->fan[l - 1];
@@ -1018,7 +1018,7 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
       ro += a.rows2;
     }
     ops_.copy(cp);
-    ops_.apply_q_left({Proot_}, {froot}, true);
+    ops_.apply_q_sweep({Proot_}, {froot}, true);
   }
   Mat<R> croot = scr_.mat<R>(root_cols_, s);
   ops_.gemm({gd<R>(Rinv_, OP_N, froot.block(0, 0, root_cols_, s), OP_N, croot)});
@@ -1089,7 +1089,7 @@ template <typename R> void Hss<R>::solve(const cplx<R>* f2, int ldf, int s, cplx
         qv.push_back(t_[l][q].Qv);
       }
       ops_.copy(cp);
-      ops_.apply_q_left(qv, Y, false);
+      ops_.apply_q_sweep(qv, Y, false);
     }
     Cl[l] = Y;
   }
@@ -1136,7 +1136,7 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
     {
       std::vector<QFac<R>> qv;
       for (int q = 0; q < nn; ++q) qv.push_back(t_[l][q].Qv);
-      ops_.apply_q_left(qv, Yb[l], true);                        // Y <- Q_v^* Y
+      ops_.apply_q_sweep(qv, Yb[l], true);                        // Y <- Q_v^* Y
     }
     // destination of the C2 adjoints: the parent's Y adjoint (or the root's c adjoint)
     if (l >= 2) {
@@ -1199,7 +1199,7 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
   // ---- root: croot = R^{-1} (P_root^* froot)[0:cols]  =>  frootb = P_root [R^{-*} crootb; 0]
   Mat<R> frootb = scr_.mat<R>(std::max(root_rows_, 1), s, true);
   ops_.gemm({gd<R>(Rinv_, OP_C, crootb.block(0, 0, root_cols_, s), OP_N, frootb.block(0, 0, root_cols_, s))});
-  ops_.apply_q_left({Proot_}, {frootb}, false);
+  ops_.apply_q_sweep({Proot_}, {frootb}, false);
   {
     std::vector<CopyD<R>> cp;
     int ro = 0;
@@ -1221,8 +1221,8 @@ template <typename R> void Hss<R>::solve_adj(const cplx<R>* ytree, int ldy, int 
       cpm.push_back(Fb[l][p].block(0, 0, nd.mc, s));
       if (nd.omega) { qo.push_back(nd.Om); co.push_back(Fb[l][p].block(0, 0, nd.m, s)); }
     }
-    ops_.apply_q_left(qp, cpm, false);
-    ops_.apply_q_left(qo, co, false);
+    ops_.apply_q_sweep(qp, cpm, false);
+    ops_.apply_q_sweep(qo, co, false);
     if (l < L) {
       std::vector<CopyD<R>> cp;
       const int F1 = pl_->fan[l];
@@ -1396,17 +1396,19 @@ template <typename R> void Hss<R>::matvec_adj(const cplx<R>* y, int ldy, int s, 
 }
 
 template <typename R> double Hss<R>::solve_entries() const {
+  // Householder vectors: the lower trapezoid (unit diagonal included) of each m x k factor
+  auto trap = [](const QFac<R>& q) { return (double)q.m * q.k - 0.5 * (double)q.k * (q.k - 1); };
   double e = 0;
   const int L = pl_->L;
   for (int l = 1; l <= L; ++l)
     for (const Node2<R>& nd : t_[l]) {
-      if (nd.omega) e += (double)nd.Om.m * nd.Om.k;
-      e += (double)nd.P.m * nd.P.k + (double)nd.Qv.m * nd.Qv.k;
+      if (nd.omega) e += trap(nd.Om);
+      e += trap(nd.P) + trap(nd.Qv);
       e += (double)nd.n1 * nd.n1 + (double)nd.n1 * (nd.kv + nd.ku) + (double)nd.kv * nd.kv;
       for (int c = 0; c < 4; ++c) e += (double)nd.B[c].m * nd.B[c].n;
       if (l >= 2) e += (double)nd.R_.m * nd.R_.n;
     }
-  e += (double)Proot_.m * Proot_.k + (double)root_cols_ * root_cols_;
+  e += trap(Proot_) + (double)root_cols_ * root_cols_;
   return e;
 }
 

@@ -139,6 +139,11 @@ template <typename R> class Ops {
   void group_wy(std::vector<QFac<R>>& Q, Arena& keep);
   // C <- Q C (conj=false) or Q^* C (conj=true), from the left.  C has Q.m rows.
   void apply_q_left(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
+  // The same product by streaming kernels (one pass over each block of reflectors per chunk of
+  // up to 16 columns of C, no GEMM tiles): the form the solve sweeps use for few right-hand sides.
+  void apply_q_stream(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
+  // apply_q_stream, or apply_q_left when NH_SWEEP_STREAM=0 (for comparison runs)
+  void apply_q_sweep(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
   // C <- C Q (conj=false) or C Q^*, from the right.  C has Q.m columns.
   void apply_q_right(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
   // X <- inverse of the upper triangle of A (square); X must not alias A.
@@ -165,6 +170,7 @@ template <typename R> class Ops {
   void gemm_class(const std::vector<GemmD<R>>& d, int cls);   // one operand-layout class
   int gemm_pick(const std::vector<GemmD<R>>& d, int cls);     // kernel kind: static rule or autotuner
   void gemm_run(const std::vector<GemmD<R>>& d, int cls, int kind);
+  template <int S> void apply_q_stream_s(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
   template <typename D> D* upload(const std::vector<D>& v);
   void* stage(const void* src, size_t bytes);
   cudaStream_t st_;

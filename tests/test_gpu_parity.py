@@ -310,3 +310,31 @@ def test_unbalanced_tree_mixed_refined(nh):
     c = to_np(h.solve(torch.from_numpy(f)))
     h.close()
     assert relerr_cols(c, ct) < 1e-8
+
+
+@pytest.mark.parametrize("prec,s", [("fp64", 20), ("fp64", 1), ("mixed", 16), ("mixed", 5)])
+def test_streaming_sweeps_match_gemm_sweeps(nh, monkeypatch, prec, s):
+    """The URV solve and its adjoint with the streaming reflector kernels (the default) and with the
+    generic blocked-GEMM application (NH_SWEEP_STREAM=0) give the same c to rounding, and both
+    match the dense oracle's least-squares solution; s = 20 takes a 16 + 4 column split."""
+    w = WORKLOADS["fp64_n32"]
+    x, y, _ = make_workload(w)
+    c0 = complex_normal((w.N, s), 321)
+    f = orc.forward(x, y, c0, w.nx, w.ny)
+    f = f + noise_like(f, 1e-6, 322)
+    cref = _dense_ref(w, f)
+    opts = dict(eps=w.eps, levels=w.levels) if prec == "fp64" else dict(eps=1e-6, levels=w.levels, prec="mixed",
+                                                                         refine_tol=1e-10, refine_max=10)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("NH_SWEEP_STREAM", mode)
+        h = nh.NudftHSS(x, y, w.nx, w.ny, **opts).factor()
+        c = to_np(h.solve(torch.from_numpy(f)))
+        g = to_np(h.apply(nh.PINV_ADJ, torch.from_numpy(c0)))
+        h.close()
+        out[mode] = (c, g)
+    assert relerr_cols(out["1"][0], cref) < 1e-8
+    assert relerr_cols(out["0"][0], cref) < 1e-8
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert relerr_cols(out["1"][0], out["0"][0]) < max(tol, 1e-9)
+    assert relerr_cols(out["1"][1], out["0"][1]) < tol
