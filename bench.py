@@ -9,8 +9,10 @@ the FP64 iterative refinement with the exact apply), Algorithm 1 of Li & Liu.
 Prints ONE JSON line (rank 0).  value = right-hand sides solved per second over whole steps
 (offline stage included), summed over ranks; the paper-style split t_c / t_f / t_s and the
 online solve rate are reported alongside.  Multi-GPU runs are independent replicas (the path
-has no exchange step).  --impl reference times the FP64 CPU oracle (dense Householder least
-squares) on a bounded sample of the same workload family and scales it to the workload.
+has no exchange step).  --impl reference times the FP64 CPU oracle (CGLS with its direct
+O(MN) applies) on a bounded sample of the same workload: two iterations, scaled by the measured
+iteration count to a 1e-8 residual.  --workload batched_uneven runs the 64-problem batch;
+--gemm, --sweep and --one-step are kernel and launch-list profiling modes, not bench lines.
 """
 from __future__ import annotations
 
@@ -239,6 +241,14 @@ def run_ours(args, w):
             h.solve(f1)                 # each call synchronises its stream before returning
         s1["ms"] = (time.perf_counter() - t0) * 1e3 / reps
 
+    if args.one_step:           # launch lists under a profiler: exactly one step, nothing else
+        torch.cuda.synchronize()
+        c, inf = step()
+        rel = float(torch.max(torch.linalg.norm(c - ctt, dim=0) / torch.linalg.norm(ctt, dim=0)).item())
+        print(json.dumps({"mode": "one-step", "config": config_of(w, args), "launches": inf["launches"],
+                          "t_build_ms": inf["t_build_ms"], "t_factor_ms": inf["t_factor_ms"],
+                          "t_solve_ms": inf["t_solve_ms"], "rel_err_vs_c_true": rel}), flush=True)
+        return
     for i in range(args.warmup):
         c, inf = step(time_one_rhs if i == args.warmup - 1 else None)
     torch.cuda.synchronize()
@@ -326,15 +336,16 @@ TF32_OVER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rates of B300
 def class_pipe(name: str, mixed: bool, pipes: dict):
     """(bound, peak, unit, source) of the pipe a kernel class runs on.
 
-    gemm_tc: the tcgen05 3xTF32 complex GEMM, against the useful complex-FP32 rate of the TF32
-    tensor pipe (TF32 rate / 3, the TF32 rate taken as the measured BF16 burst rate times the
+    gemm_tc, jacobi_tc (the blocked Jacobi step whose Gram and update products run on the tensor
+    cores; its flops count those products only): the tcgen05 3xTF32 complex products, against the
+    useful complex-FP32 rate of the TF32 tensor pipe (TF32 rate / 3, the TF32 rate taken as the measured BF16 burst rate times the
     nominal TF32/BF16 ratio).  sweep: one URV solve replayed from its graph, against the measured
     HBM copy bandwidth.  FP64 classes (all classes of an FP64 run, the "_fp64" ones of a mixed run)
     against the measured DFMA rate; the other mixed-run classes (CUDA-core GEMM, QR, Jacobi)
     against the measured FFMA rate."""
     if name == "sweep" or name == "sweep_fp64":
         return "hbm", pipes["hbm_gbs"], "GB/s", pipes["hbm_src"]
-    if name == "gemm_tc":
+    if name in ("gemm_tc", "jacobi_tc"):
         return ("tensor", pipes["bf16"] * TF32_OVER_BF16 / 3.0, "TFLOP/s",
                 f"3xTF32 useful rate = bf16 {pipes['bf16']:.0f} TFLOP/s ({pipes['bf16_src']}) x 1.1/2.25 / 3")
     if name.endswith("_fp64") or not mixed:
@@ -508,6 +519,34 @@ def run_gemm(args):
                       "warmup": args.warmup}), flush=True)
 
 
+def run_sweep(args):
+    """One call of nudft2_la_qr_apply: blocked Householder QR of a random m x k complex64 matrix
+    (merged 256-column blocks), then Q^* C for a random m x s C by the streaming kernels (partial
+    V^* C over row slabs, ordered sum, T product, row update).  Prints the wall time per call
+    (QR included) and the reflector bytes one application streams; used for kernel profiles of the
+    sweep kernels, not as a benchmark line."""
+    import torch
+
+    import paper_2607_00928_b300 as nh
+    m, k, s = [int(v) for v in args.sweep.split(",")]
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn((m, k), dtype=torch.complex64, device="cuda", generator=g)
+    C = torch.randn((m, s), dtype=torch.complex64, device="cuda", generator=g)
+    for _ in range(args.warmup):
+        nh.la_qr_apply(A, C, conj=True, grouped=True)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out, _ = nh.la_qr_apply(A, C, conj=True, grouped=True)
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    kk = min(m, k)
+    print(json.dumps({"mode": "sweep", "m": m, "k": k, "s": s, "ms_per_call_with_qr": statistics.median(ts),
+                      "reflector_bytes": (m * kk - kk * (kk - 1) / 2) * 8, "steps": args.steps,
+                      "warmup": args.warmup}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,9 +557,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gemm", default=None, help="m,n,k[,batch]: time one library GEMM instead of the solver")
+    ap.add_argument("--sweep", default=None,
+                    help="m,k,s: Householder QR of a random m x k complex64 matrix, then Q^* C (m x s) by the "
+                         "streaming reflector kernels of the solve sweeps (for kernel profiles)")
+    ap.add_argument("--one-step", action="store_true",
+                    help="profiling mode: one build + factor + solve of the workload, no warm-up, end-to-end or CPU "
+                         "legs; prints the stage times only")
     args = ap.parse_args()
     if args.gemm:
         run_gemm(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.workload == "batched_uneven":
         if args.impl == "reference":

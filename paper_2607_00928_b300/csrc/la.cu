@@ -59,7 +59,7 @@ template <typename R> int* Ops<R>::upload_ints(const std::vector<int>& v) {
 
 // =============================================================================== profiling
 const char* kclass_name(int c) {
-  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other", "qrcp", "sweep", "gemm_tc"};
+  static const char* n[] = {"gemm", "qr_panel", "jacobi", "other", "qrcp", "sweep", "gemm_tc", "jacobi_tc"};
   return (c >= 0 && c < K_NCLASS) ? n[c] : "?";
 }
 Prof::~Prof() {
@@ -2474,6 +2474,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     maxblk = std::max(maxblk, nb);
   }
   unsigned long long* rows_upd = ar_->template arr<unsigned long long>(1, true);
+  bool jtc = false;   // FP32 blocked steps run their Gram and update products on the tensor cores
   const double u = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
   if (!jd.empty()) {
     auto djd = upload(jd);
@@ -2490,8 +2491,6 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     const size_t jsmem = (size_t)32 * rpc * sizeof(cplx<R>);
     if (jmode == J_CLUSTER && jsmem > (size_t)200 * 1024) jmode = J_SCALAR;
     const bool use_cluster = jmode == J_CLUSTER;
-    // FP32 blocked steps run their Gram and update products on the tensor cores
-    bool jtc = false;
     if constexpr (sizeof(R) == 4) jtc = jmode == J_BLOCK && gemm_tc_enabled();
     if (jtc)
       NH_CK(cudaFuncSetAttribute(k_jacobi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JT_SMEM));
@@ -2554,7 +2553,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         }
         count();
       }
-      prof.end(st_, K_JACOBI, fl, 0);
+      prof.end(st_, jtc ? K_JACOBI_TC : K_JACOBI, fl, 0);
       NH_CK(cudaMemcpyAsync(hoff.data(), offs, nm * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
       NH_CK(cudaStreamSynchronize(st_));
       bool all = true;
@@ -2579,7 +2578,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     unsigned long long ru = 0;
     NH_CK(cudaMemcpyAsync(&ru, rows_upd, sizeof(ru), cudaMemcpyDeviceToHost, st_));
     NH_CK(cudaStreamSynchronize(st_));
-    prof.add_flops(K_JACOBI, 8.0 * JbCfg<R>::W * JbCfg<R>::W * (double)ru);
+    prof.add_flops(jtc ? K_JACOBI_TC : K_JACOBI, 8.0 * JbCfg<R>::W * JbCfg<R>::W * (double)ru);
   }
   // 4. sort + count
   std::vector<SortD<R>> sd;

@@ -73,8 +73,9 @@ template <typename R> struct QFac {
 // K_SWEEP: one whole URV solve (Sec. 2.3 sweeps) replayed from its CUDA graph, with the bytes of
 // the factors it streams.
 // K_GEMM_TC: the tensor-core complex GEMM (operand packing included); K_GEMM: the CUDA-core one.
+// K_JACOBI_TC: the blocked Jacobi step with its Gram and update products on the tensor cores.
 enum KClass { K_GEMM = 0, K_QR_PANEL = 1, K_JACOBI = 2, K_OTHER = 3, K_QRCP = 4, K_SWEEP = 5, K_GEMM_TC = 6,
-              K_NCLASS = 7 };
+              K_JACOBI_TC = 7, K_NCLASS = 8 };
 struct KStat { double ms = 0, flops = 0, bytes = 0; int launches = 0; };
 const char* kclass_name(int c);
 

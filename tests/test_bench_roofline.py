@@ -38,3 +38,15 @@ def test_tensor_core_gemm_and_sweep_use_their_own_pipes():
     sw = {c["kernel"]: c for c in r["classes"]}["sweep"]
     assert sw["bound"] == "hbm" and sw["unit"] == "GB/s" and abs(sw["achieved"] - 3000.0) < 1e-9
     assert abs(sw["frac"] - 0.5) < 1e-12
+
+
+def test_tensor_core_jacobi_uses_the_tensor_pipe():
+    """The blocked Jacobi step whose Gram and update products run on tcgen05 is divided by the
+    3xTF32 useful rate, the CUDA-core one by the FFMA rate."""
+    kst = {"jacobi_tc": {"ms": 2000.0, "flops": 2.0e14, "bytes": 0.0, "launches": 20},
+           "jacobi": {"ms": 1000.0, "flops": 2.0e13, "bytes": 0.0, "launches": 5}}
+    r = bench.roofline(kst, WORKLOADS["mixed_n256"], PIPES)
+    assert r["kernel"] == "jacobi_tc" and r["bound"] == "tensor"
+    assert abs(r["frac"] - 100.0 / (1500.0 * 1.1 / 2.25 / 3.0)) < 1e-12
+    jb = {c["kernel"]: c for c in r["classes"]}["jacobi"]
+    assert jb["bound"] == "alu" and jb["peak"] == bench.FFMA_TFLOPS_NOMINAL
