@@ -246,6 +246,7 @@ def run_ours(args, w):
         c, inf = step()
         rel = float(torch.max(torch.linalg.norm(c - ctt, dim=0) / torch.linalg.norm(ctt, dim=0)).item())
         print(json.dumps({"mode": "one-step", "config": config_of(w, args), "launches": inf["launches"],
+                          "device_bytes": inf.get("device_bytes"),
                           "t_build_ms": inf["t_build_ms"], "t_factor_ms": inf["t_factor_ms"],
                           "t_solve_ms": inf["t_solve_ms"], "rel_err_vs_c_true": rel}), flush=True)
         return
@@ -320,6 +321,7 @@ def run_ours(args, w):
                 "online_solves_per_s_one_rhs": (1e3 / s1["ms"]) if s1.get("ms") else None,
                 "rel_err_vs_c_true": rel, "max_rank": infos[-1]["max_rank"],
                 "level_rank": infos[-1]["level_rank"], "refine_iters": infos[-1]["refine_iters"],
+                "device_bytes": infos[-1].get("device_bytes"),
                 "refine_relres": infos[-1]["refine_relres"],
                 "e2e": {"value": world * w.nrhs / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},

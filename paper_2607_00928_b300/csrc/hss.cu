@@ -712,8 +712,43 @@ template <typename R> void Hss<R>::build(double eps) {
   build_1d(pl_->ty, pl_->yo, eps / 10.0, gy_, Gy_);
   assemble_2d();
   recompress(eps);
-  NH_CK(cudaStreamSynchronize(st_));
+  compact_generators();
   tmp_.free_all();
+}
+
+// The construction leaves every intermediate version of the generators in keep_ (the 1D HSS
+// and dense 1D kernel matrices, the face-split generators before recompression, the thin-QR
+// factors F, G, the truncated-SVD bases).  Only the final D, U, V (leaves), B, R and W are read
+// afterwards (factorization, matvecs, recomputation of checkpointed levels): they are copied into
+// a fresh arena and keep_ is handed back.
+template <typename R> void Hss<R>::compact_generators() {
+  auto gen = std::make_unique<Arena>((size_t)256 << 20, true);
+  gen->set_stream(st_);
+  std::vector<CopyD<R>> cp;
+  auto move = [&](Mat<R>& a) {
+    if (!a.p || a.m <= 0 || a.n <= 0) return;   // empty blocks are never dereferenced
+    Mat<R> b = gen->template mat<R>(a.m, a.n);
+    cp.push_back({a.p, b.p, a.m, a.n, a.ld, b.ld, OP_N, R(1), R(0)});
+    a = b;
+  };
+  const int L = pl_->L;
+  for (int l = 1; l <= L; ++l)
+    for (Node2<R>& nd : t_[l]) {
+      if (l == L) { move(nd.D); move(nd.U); move(nd.V); }
+      for (int c = 0; c < 4; ++c) move(nd.B[c]);
+      move(nd.R_);
+      move(nd.W);
+      nd.F = Mat<R>();
+      nd.G = Mat<R>();
+    }
+  ops_.copy(cp);
+  NH_CK(cudaStreamSynchronize(st_));
+  keep_.free_all();
+  gen_ = std::move(gen);
+  gx_.clear();
+  gy_.clear();
+  Gx_ = Mat<R>();
+  Gy_ = Mat<R>();
 }
 
 // ------------------------------------------------------------------------------- URV factorization (Sec. 2.3)

@@ -104,7 +104,7 @@ template <typename R> class Hss {
   int max_rank() const;
   std::vector<int> level_ranks() const;
   size_t bytes() const {
-    size_t b = keep_.reserved();
+    size_t b = keep_.reserved() + (gen_ ? gen_->reserved() : 0);
     for (auto& a : fac_) b += a->reserved();
     return b;
   }
@@ -120,6 +120,7 @@ template <typename R> class Hss {
   void recompress(double eps);
   void factor_level(int l);
   void factor_root();
+  void compact_generators();
   cudaStream_t st_;
   const Plan* pl_;
   Arena keep_, scr_, tmp_;
@@ -127,6 +128,7 @@ template <typename R> class Hss {
   std::vector<std::vector<Gen1D<R>>> gx_, gy_;
   Mat<R> Gx_, Gy_;
   std::vector<std::vector<Node2<R>>> t_;
+  std::unique_ptr<Arena> gen_;                 // the final generators (after build)
   std::vector<std::unique_ptr<Arena>> fac_;   // factor storage per level (0 = root)
   int dropped_ = 0;                            // top levels whose factors were handed back
   // root factor

@@ -1281,6 +1281,98 @@ __device__ __forceinline__ void rr_pair(int p, int r, int n, int& a, int& b) {
   else { a = 1 + (r + p) % (n - 1); b = 1 + (r - p + n - 1) % (n - 1); }
 }
 
+// Cyclic two-sided Jacobi on the Hermitian W x W Gram G in shared memory (leading dimension ldg),
+// accumulating V <- V J for every rotation J, until a sweep rotates nothing or max_inner sweeps.
+// A round rotates W / 2 disjoint column pairs (round-robin order) with the one-sided rotation
+// formula evaluated on Gram entries; pairs whose cosine is at most tol, or with a column below the
+// noise floor, are left alone.  G <- J^* G J is applied block by block: output 2 x 2 block (P, Q)
+// depends only on input block (P, Q), so one thread updates it in place -- two barriers per round.
+// Shared scratch: rc, rse, ract, pa, pb (W / 2 entries each) and *any_s.  Called by all 256
+// threads of the CTA.
+template <typename R, int W>
+__device__ void jac_inner(cplx<R>* G, cplx<R>* V, int ldg, R floor2, R tol, int max_inner, R* rc, cplx<R>* rse,
+                          int* ract, int* pa, int* pb, int* any_s) {
+  constexpr int NP = W / 2;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < W * W; e += 256) {
+    const int i = e / W, j = e - i * W;
+    V[i * ldg + j] = mkc(R(i == j ? 1 : 0), R(0));
+  }
+  if (tid == 0) *any_s = 0;
+  __syncthreads();
+  for (int sw = 0; sw < max_inner; ++sw) {
+    for (int ir = 0; ir < W - 1; ++ir) {
+      if (tid < NP) {
+        int a, b;
+        rr_pair(tid, ir, W, a, b);
+        pa[tid] = a;
+        pb[tid] = b;
+        const R al = G[a * ldg + a].x, be = G[b * ldg + b].x;
+        const cplx<R> ga = G[a * ldg + b];
+        const R g = sqrt(abs2(ga));
+        int act = 0;
+        R c = R(1);
+        cplx<R> se = czero<R>();
+        if (al > floor2 && be > floor2 && g > R(0) && g / (sqrt(al) * sqrt(be)) > tol) {
+          const R zeta = (be - al) / (R(2) * g);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          c = R(1) / sqrt(R(1) + t * t);
+          const R sn = c * t;
+          se = mkc(sn * ga.x / g, sn * ga.y / g);
+          act = 1;
+          *any_s = 1;
+        }
+        rc[tid] = c;
+        rse[tid] = se;
+        ract[tid] = act;
+      }
+      __syncthreads();
+      // J of pair P: columns (a, b) -> (c x_a - conj(se) x_b, se x_a + c x_b); identity when inactive
+      for (int e = tid; e < NP * NP; e += 256) {
+        const int P = e / NP, Q = e - P * NP;
+        const int aP = ract[P], aQ = ract[Q];
+        if (!aP && !aQ) continue;
+        const int ra = pa[P], rb = pb[P], ca = pa[Q], cb = pb[Q];
+        const R cp = rc[P], cq = rc[Q];
+        const cplx<R> sp = rse[P], sq = rse[Q];
+        const cplx<R> g00 = G[ra * ldg + ca], g01 = G[ra * ldg + cb], g10 = G[rb * ldg + ca], g11 = G[rb * ldg + cb];
+        // T = g J_Q
+        const cplx<R> t00 = cq * g00 - conj(sq) * g01, t01 = sq * g00 + cq * g01;
+        const cplx<R> t10 = cq * g10 - conj(sq) * g11, t11 = sq * g10 + cq * g11;
+        // J_P^* T
+        cplx<R> n00 = cp * t00 - sp * t10, n01 = cp * t01 - sp * t11;
+        cplx<R> n10 = conj(sp) * t00 + cp * t10, n11 = conj(sp) * t01 + cp * t11;
+        if (P == Q) {   // the rotated pair: off-diagonal zero, real diagonal
+          n01 = czero<R>();
+          n10 = czero<R>();
+          n00.y = R(0);
+          n11.y = R(0);
+        }
+        G[ra * ldg + ca] = n00;
+        G[ra * ldg + cb] = n01;
+        G[rb * ldg + ca] = n10;
+        G[rb * ldg + cb] = n11;
+      }
+      for (int e = tid; e < W * NP; e += 256) {
+        const int i = e / NP, Q = e - i * NP;
+        if (!ract[Q]) continue;
+        const int ca = pa[Q], cb = pb[Q];
+        const R c = rc[Q];
+        const cplx<R> se = rse[Q];
+        const cplx<R> x = V[i * ldg + ca], y = V[i * ldg + cb];
+        V[i * ldg + ca] = c * x - conj(se) * y;
+        V[i * ldg + cb] = se * x + c * y;
+      }
+      __syncthreads();
+    }
+    const int more = *any_s;
+    __syncthreads();
+    if (!more) break;
+    if (tid == 0) *any_s = 0;
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __device__ void jac_rotate(cplx<R>* xa, cplx<R>* xb, int r, R tol, unsigned* off, R floor2) {
   const int lane = threadIdx.x & 31;
@@ -1513,7 +1605,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   __shared__ int cidx[W];
   __shared__ R rc[W / 2];
   __shared__ cplx<R> rse[W / 2];
-  __shared__ int ract[W / 2];
+  __shared__ int ract[W / 2], rpa[W / 2], rpb[W / 2];
   __shared__ int any_s;
   __shared__ float offw[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1586,79 +1678,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     __syncthreads();
     if ((R)offw[0] <= tol_out) return;   // uniform: the pair is already orthogonal
   }
-  // ---- 3. cyclic two-sided Jacobi on G, V <- V J for every rotation J
-  for (int e = tid; e < W * W; e += 256) {
-    const int i = e / W, j = e - i * W;
-    V[i * LDG + j] = mkc(R(i == j ? 1 : 0), R(0));
-  }
-  if (tid == 0) any_s = 0;
-  __syncthreads();
-  for (int sw = 0; sw < max_inner; ++sw) {
-    for (int ir = 0; ir < W - 1; ++ir) {
-      if (tid < W / 2) {
-        int a, b;
-        rr_pair(tid, ir, W, a, b);
-        const R al = G[a * LDG + a].x, be = G[b * LDG + b].x;
-        const cplx<R> ga = G[a * LDG + b];
-        const R g = sqrt(abs2(ga));
-        int act = 0;
-        if (al > floor2 && be > floor2 && g > R(0) && g / (sqrt(al) * sqrt(be)) > tol) {
-          const R zeta = (be - al) / (R(2) * g);
-          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-          const R c = R(1) / sqrt(R(1) + t * t);
-          const R s = c * t;
-          rc[tid] = c;
-          rse[tid] = mkc(s * ga.x / g, s * ga.y / g);
-          act = 1;
-          any_s = 1;
-        }
-        ract[tid] = act;
-      }
-      __syncthreads();
-      // columns a, b of G and of V: (x_a, x_b) <- (c x_a - conj(se) x_b, se x_a + c x_b)
-      for (int e = tid; e < 2 * (W / 2) * W; e += 256) {
-        const int which = e / ((W / 2) * W), rest = e - which * ((W / 2) * W);
-        const int p = rest / W, i = rest - p * W;
-        if (!ract[p]) continue;
-        int a, b;
-        rr_pair(p, ir, W, a, b);
-        cplx<R>* M = which ? V : G;
-        const R c = rc[p];
-        const cplx<R> se = rse[p], sec = conj(se);
-        const cplx<R> x = M[i * LDG + a], y = M[i * LDG + b];
-        M[i * LDG + a] = c * x - sec * y;
-        M[i * LDG + b] = se * x + c * y;
-      }
-      __syncthreads();
-      // rows a, b of G (the conjugate transformation from the left)
-      for (int e = tid; e < (W / 2) * W; e += 256) {
-        const int p = e / W, j = e - p * W;
-        if (!ract[p]) continue;
-        int a, b;
-        rr_pair(p, ir, W, a, b);
-        const R c = rc[p];
-        const cplx<R> se = rse[p], sec = conj(se);
-        const cplx<R> x = G[a * LDG + j], y = G[b * LDG + j];
-        G[a * LDG + j] = c * x - se * y;
-        G[b * LDG + j] = sec * x + c * y;
-      }
-      __syncthreads();
-      if (tid < W / 2 && ract[tid]) {
-        int a, b;
-        rr_pair(tid, ir, W, a, b);
-        G[a * LDG + b] = czero<R>();
-        G[b * LDG + a] = czero<R>();
-        G[a * LDG + a].y = R(0);
-        G[b * LDG + b].y = R(0);
-      }
-      __syncthreads();
-    }
-    const int more = any_s;
-    __syncthreads();                   // every thread has read the flag before it is reset
-    if (!more) break;
-    if (tid == 0) any_s = 0;
-    __syncthreads();
-  }
+  // ---- 3. two-sided Jacobi on G, V <- V J for every rotation J
+  jac_inner<R, W>(G, V, LDG, floor2, tol, max_inner, rc, rse, ract, rpa, rpb, &any_s);
   // ---- 4. X_P <- X_P V, chunk by chunk (in place; each chunk's rows are read before written)
   const int tk = ti;
   cplx<R> pf[C::PF];
@@ -1702,53 +1723,49 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 
 // =============================================================================== blocked Jacobi on tensor cores
 // The FP32 blocked Jacobi step of k_jacobi_blk with both of its products on the tensor cores
-// (tcgen05 kind::tf32, 3xTF32 split, M = N = 64), one CTA per block pair:
-//  1. Gram G = X_P^* X_P, X_P = the pair's 64 columns.  Chunks of 64 rows are split into TF32
-//     planes in shared memory (two buffers; the next chunk's loads are in flight while the current
-//     chunk's 96 MMAs run).  Each chunk accumulates in one of two tensor-memory accumulators, and
-//     the previous chunk's accumulator is added (FP32, round to nearest) into G in shared memory,
-//     so no tensor-core accumulation runs longer than 64 rows (its truncation stays at ~1e-6).
-//     With M = 64 the accumulator row i sits in tensor-memory lane 32 (i / 16) + i % 16.
+// (tcgen05 kind::tf32, 3xTF32 split), one CTA per block pair:
+//  1. Gram G = X_P^* X_P, X_P = the pair's 64 columns, as the real Gram of the stacked operand
+//     S = [Re X_P, Im X_P]^T (128 x rows): D = S S^T holds Re^T Re, Re^T Im, Im^T Re, Im^T Im, and
+//     G = (Re^T Re + Im^T Im) + i (Re^T Im - Im^T Re).  One M = N = 128 MMA per k = 8 step and split
+//     term: 3 MMAs, against 12 of M = N = 64 for the complex form, at the full-width tensor rate.
+//     Chunks of 64 rows are split into TF32 hi/lo planes in shared memory (two buffers; loads run
+//     two chunks ahead in registers).  Each chunk accumulates in one of two tensor-memory
+//     accumulators; the previous chunk's is added (FP32, round to nearest) into two partial Grams in
+//     shared memory -- every warp owns one quarter of D and one real component of one partial, so
+//     the adds need no ordering -- and no tensor-core accumulation runs longer than 64 rows.
 //  2. The largest cosine and the two-sided Jacobi on G -> V, exactly as in k_jacobi_blk.
-//  3. X_P <- X_P V over chunks of 64 rows: A = the chunk (K-major along the 64 columns), B = the
-//     planes of V^T, the product in tensor memory, written back in place.
+//  3. X_P <- X_P V over chunks of 64 rows: A = the chunk (complex planes, double-buffered), B = the
+//     planes of V^T, 12 MMAs of M = N = 64 per k = 8 step into one of two accumulators; the
+//     previous chunk's product is written back in place while the next chunk's MMAs run.
 // Every wait is bounded: one that runs out sets g_jac_error, and the CTA leaves X untouched.
 namespace {
 constexpr int JT_W = 64, JT_CH = 64;             // pair width, rows per chunk
 constexpr uint32_t JT_SBO = (JT_CH / 4) * 128;   // 8-row group stride of a 64-deep K-major plane
-constexpr int JT_PLANE = JT_W * JT_CH * 4;       // 16 KB
-constexpr int JT_BUF = 4 * JT_PLANE;             // re hi, re lo, im hi, im lo
+constexpr int JT_PLANE = JT_W * JT_CH * 4;       // 16 KB: one real plane of a 64 x 64 operand
+constexpr int JT_REGION = 4 * JT_PLANE;          // 64 KB: re hi, re lo, im hi, im lo (or hi, lo of 128 rows)
 constexpr int JT_LDG = JT_W + 1;
-constexpr size_t JT_SMEM = 2 * (size_t)JT_BUF + 2 * (size_t)JT_W * JT_LDG * sizeof(float2) + 1024;
+constexpr size_t JT_PART = (size_t)JT_W * JT_LDG * sizeof(float2);
+constexpr size_t JT_SMEM = 2 * (size_t)JT_REGION + 2 * JT_PART + 1024;
 }  // namespace
 
 __device__ int g_jac_error;
 
 // the 12 MMAs of one k = 8 step of a complex product D = A B^T given as TF32 planes
-// (negA: the A-negate descriptor for the -Ai Bi terms; the conjugated Gram passes its own order)
-__device__ __forceinline__ void jt_mma12(uint32_t dr, uint32_t di, uint32_t a, uint32_t b, uint32_t ko, uint32_t f,
-                                         bool gram) {
+__device__ __forceinline__ void jt_mma12(uint32_t dr, uint32_t di, uint32_t a, uint32_t b, uint32_t ko, uint32_t f) {
   const uint32_t idp = tc_idesc(64, 64, false), idn = tc_idesc(64, 64, true);
   const uint64_t arh = tc_desc(a + ko, JT_SBO), arl = tc_desc(a + JT_PLANE + ko, JT_SBO),
                  aih = tc_desc(a + 2 * JT_PLANE + ko, JT_SBO), ail = tc_desc(a + 3 * JT_PLANE + ko, JT_SBO);
   const uint64_t brh = tc_desc(b + ko, JT_SBO), brl = tc_desc(b + JT_PLANE + ko, JT_SBO),
                  bih = tc_desc(b + 2 * JT_PLANE + ko, JT_SBO), bil = tc_desc(b + 3 * JT_PLANE + ko, JT_SBO);
-  if (gram) {
-    // G = X^* X: Gr = Xr Xr + Xi Xi, Gi = Xr Xi - Xi Xr (A and B are the same planes)
-    tc_mma(dr, arh, brh, idp, f); tc_mma(dr, arh, brl, idp, 1u); tc_mma(dr, arl, brh, idp, 1u);
-    tc_mma(dr, aih, bih, idp, 1u); tc_mma(dr, aih, bil, idp, 1u); tc_mma(dr, ail, bih, idp, 1u);
-    tc_mma(di, arh, bih, idp, f); tc_mma(di, arh, bil, idp, 1u); tc_mma(di, arl, bih, idp, 1u);
-    tc_mma(di, aih, brh, idn, 1u); tc_mma(di, aih, brl, idn, 1u); tc_mma(di, ail, brh, idn, 1u);
-  } else {
-    // D = A B: Dr = Ar Br - Ai Bi, Di = Ar Bi + Ai Br
-    tc_mma(dr, arh, brh, idp, f); tc_mma(dr, arh, brl, idp, 1u); tc_mma(dr, arl, brh, idp, 1u);
-    tc_mma(dr, aih, bih, idn, 1u); tc_mma(dr, aih, bil, idn, 1u); tc_mma(dr, ail, bih, idn, 1u);
-    tc_mma(di, arh, bih, idp, f); tc_mma(di, arh, bil, idp, 1u); tc_mma(di, arl, bih, idp, 1u);
-    tc_mma(di, aih, brh, idp, 1u); tc_mma(di, aih, brl, idp, 1u); tc_mma(di, ail, brh, idp, 1u);
-  }
+  // D = A B: Dr = Ar Br - Ai Bi, Di = Ar Bi + Ai Br
+  tc_mma(dr, arh, brh, idp, f); tc_mma(dr, arh, brl, idp, 1u); tc_mma(dr, arl, brh, idp, 1u);
+  tc_mma(dr, aih, bih, idn, 1u); tc_mma(dr, aih, bil, idn, 1u); tc_mma(dr, ail, bih, idn, 1u);
+  tc_mma(di, arh, bih, idp, f); tc_mma(di, arh, bil, idp, 1u); tc_mma(di, arl, bih, idp, 1u);
+  tc_mma(di, aih, brh, idp, 1u); tc_mma(di, aih, brl, idp, 1u); tc_mma(di, ail, brh, idp, 1u);
 }
 
-// four consecutive values along k of one operand row, split into the four planes at byte offset off
+// four consecutive values along k of one complex operand row, split into the four planes at byte
+// offset off
 __device__ __forceinline__ void jt_store4(unsigned char* buf, uint32_t off, const float2 (&v)[4]) {
   uint32_t p[4][4];
 #pragma unroll
@@ -1771,16 +1788,20 @@ __global__ void __launch_bounds__(256, 1)
   extern __shared__ unsigned char jt_raw[];
   const uint32_t raw_s = tc_smem_u32(jt_raw);
   unsigned char* sm = jt_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
-  unsigned char* buf[2] = {sm, sm + JT_BUF};
-  float2* G = reinterpret_cast<float2*>(sm + 2 * JT_BUF);   // G[i * LDG + j] = x_i^* x_j
+  // shared memory: regions 0 and 1 (64 KB each), then two 64 x 65 complex arrays.  Gram: the two
+  // chunk buffers and the two partial Grams (G, P2).  Jacobi: G and V.  Update: B = V^T planes in
+  // region 0, A chunk buffers in region 1 and over G/V.
+  unsigned char* reg0 = sm;
+  unsigned char* reg1 = sm + JT_REGION;
+  float2* G = reinterpret_cast<float2*>(sm + 2 * JT_REGION);   // G[i * LDG + j] = x_i^* x_j
   float2* V = G + W * LDG;
   __shared__ int cidx[W];
   __shared__ float rc[W / 2];
   __shared__ float2 rse[W / 2];
-  __shared__ int ract[W / 2];
+  __shared__ int ract[W / 2], rpa[W / 2], rpb[W / 2];
   __shared__ int any_s, fail, skip;
   __shared__ float offw[8];
-  __shared__ uint64_t mbar[4];
+  __shared__ uint64_t mbar[5];
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quad = warp & 3;
   int I, J;
@@ -1791,12 +1812,12 @@ __global__ void __launch_bounds__(256, 1)
   }
   if (warp == 0) tc_alloc(&tslot, 256);
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) tc_bar_init(&mbar[i], 1);
+    for (int i = 0; i < 5; ++i) tc_bar_init(&mbar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fail = 0;
     skip = 0;
   }
-  for (int e = tid; e < W * LDG; e += 256) G[e] = make_float2(0.f, 0.f);
+  for (int e = tid; e < 2 * W * LDG; e += 256) G[e] = make_float2(0.f, 0.f);   // G and P2 (= V)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1804,60 +1825,101 @@ __global__ void __launch_bounds__(256, 1)
   const float floor2 = negl2 * (*d.amax);
   const int nch = (d.r + JT_CH - 1) / JT_CH;
 
-  // ---- 1. Gram.  Thread t stages 4 quads: quad e = t + 256 q -> column c = e / 16, rows 4 (e % 16)..+3
-  float2 pf[4][4];
-  auto load_gram = [&](int t) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q, c = e >> 4, r0 = t * JT_CH + 4 * (e & 15), col = cidx[c];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        pf[q][i] = (col >= 0 && r0 + i < d.r) ? d.X[(size_t)(r0 + i) + (size_t)col * d.ld] : make_float2(0.f, 0.f);
-    }
-  };
-  load_gram(0);
-  for (int t = 0; t <= nch; ++t) {
-    if (t < nch) {
-      unsigned char* b = buf[t & 1];   // last read by chunk t - 2, whose MMAs completed before its drain
+  // ---- 1. Gram.  Unit e = tid + 256 q: column c = 8 (e >> 7) + (e & 7), chunk rows 4 kq .. 4 kq + 3
+  //      with kq = (e >> 3) & 15 -- eight lanes fill one 8-row x 16-byte core matrix, so a warp's
+  //      16-byte stores cover 512 contiguous bytes.  Re parts go to stacked rows c, Im to 64 + c.
+  {
+    float2 pa[4][4], pb[4][4];
+    auto load_g = [&](int t, float2 (&pf)[4][4]) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int e = tid + 256 * q;
-        jt_store4(b, tc_kmajor(e >> 4, 4 * (e & 15), JT_SBO), pf[q]);
+        const int e = tid + 256 * q, c = 8 * (e >> 7) + (e & 7), r0 = t * JT_CH + 4 * ((e >> 3) & 15);
+        const int col = cidx[c];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          pf[q][i] = (col >= 0 && r0 + i < d.r) ? d.X[(size_t)(r0 + i) + (size_t)col * d.ld] : make_float2(0.f, 0.f);
       }
-      tc_fence_async_smem();
-      __syncthreads();
+    };
+    auto store_g = [&](unsigned char* b, const float2 (&pf)[4][4]) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q, c = 8 * (e >> 7) + (e & 7), kq = (e >> 3) & 15;
+        uint32_t h[2][4], l[2][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          tc_split(pf[q][i].x, h[0][i], l[0][i]);
+          tc_split(pf[q][i].y, h[1][i], l[1][i]);
+        }
+        const uint32_t ore = tc_kmajor(c, 4 * kq, JT_SBO), oim = tc_kmajor(64 + c, 4 * kq, JT_SBO);
+        *reinterpret_cast<uint4*>(b + ore) = make_uint4(h[0][0], h[0][1], h[0][2], h[0][3]);
+        *reinterpret_cast<uint4*>(b + 2 * JT_PLANE + ore) = make_uint4(l[0][0], l[0][1], l[0][2], l[0][3]);
+        *reinterpret_cast<uint4*>(b + oim) = make_uint4(h[1][0], h[1][1], h[1][2], h[1][3]);
+        *reinterpret_cast<uint4*>(b + 2 * JT_PLANE + oim) = make_uint4(l[1][0], l[1][1], l[1][2], l[1][3]);
+      }
+    };
+    // hi plane of the 128 stacked rows at +0, lo plane at +2 JT_PLANE (32 KB each)
+    auto mma_g = [&](unsigned char* b, int t) {
       if (tid == 0 && !fail) {
         tc_fence_after();
-        const uint32_t a = tc_smem_u32(b), dr = tmem + (uint32_t)(t & 1) * 128, di = dr + 64;
+        const uint32_t hi = tc_smem_u32(b), lo = hi + 2 * JT_PLANE, dd = tmem + (uint32_t)(t & 1) * 128;
+        const uint32_t id = tc_idesc(128, 128, false);
 #pragma unroll
-        for (int ks = 0; ks < JT_CH / 8; ++ks) jt_mma12(dr, di, a, a, (uint32_t)ks * 256, ks == 0 ? 0u : 1u, true);
+        for (int ks = 0; ks < JT_CH / 8; ++ks) {
+          const uint64_t h = tc_desc(hi + (uint32_t)ks * 256, JT_SBO), l = tc_desc(lo + (uint32_t)ks * 256, JT_SBO);
+          tc_mma(dd, h, h, id, ks == 0 ? 0u : 1u);
+          tc_mma(dd, h, l, id, 1u);
+          tc_mma(dd, l, h, id, 1u);
+        }
         tc_commit(&mbar[t & 1]);
       }
-      if (t + 1 < nch) load_gram(t + 1);
-    }
-    if (t >= 1) {
-      const int u = t - 1;
+    };
+    // warp (quad, h = warp >> 2) adds rows 32 quad .. + 31, columns 64 h .. + 63 of chunk u's D:
+    // quad < 2: Re^T Re -> G.x (h = 0), Re^T Im -> G.y (h = 1); quad >= 2: Im^T Re -> P2.y (h = 0),
+    // Im^T Im -> P2.x (h = 1).  Afterwards G += conj-combined P2.
+    auto drain_g = [&](int u) {
       if (!fail && !tc_wait(&mbar[u & 1], (uint32_t)((u >> 1) & 1))) atomicExch(&fail, 1);
       tc_fence_after();
-      // warps 0-3 add the real parts (columns 0-63 of the accumulator), warps 4-7 the imaginary
-      // parts (64-127); lanes 0-15 of quadrant q hold rows 16 q .. 16 q + 15
-      const uint32_t base = tmem + (uint32_t)(u & 1) * 128 + (warp < 4 ? 0u : 64u) + ((uint32_t)(32 * quad) << 16);
+      const int h = warp >> 2, i = (32 * quad + lane) & 63;
+      const bool re = (quad < 2) == (h == 0);
+      // this warp's real component of row i (4-byte accesses: the other component belongs to
+      // another warp)
+      float* dst = reinterpret_cast<float*>((quad < 2 ? G : V) + i * LDG) + (re ? 0 : 1);
+      const uint32_t base = tmem + (uint32_t)(u & 1) * 128 + (uint32_t)(64 * h) + ((uint32_t)(32 * quad) << 16);
       for (int c0 = 0; c0 < W; c0 += 16) {
         uint32_t v[16];
         tc_ld16(base + (uint32_t)c0, v);
         tc_wait_ld();
-        if (lane < 16 && !fail) {
-          float2* g = G + (16 * quad + lane) * LDG + c0;
-          if (warp < 4) {
+        if (!fail) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) g[j].x += __uint_as_float(v[j]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) g[j].y += __uint_as_float(v[j]);
-          }
+          for (int j = 0; j < 16; ++j) dst[2 * (c0 + j)] += __uint_as_float(v[j]);
         }
       }
       tc_fence_before();
+    };
+    auto step_g = [&](int t, float2 (&pf)[4][4]) {
+      if (t < nch) {
+        unsigned char* b = (t & 1) ? reg1 : reg0;   // last read by chunk t - 2, drained before
+        store_g(b, pf);
+        if (t + 2 < nch) load_g(t + 2, pf);
+        tc_fence_async_smem();
+        __syncthreads();
+        mma_g(b, t);
+      }
+      if (t >= 1) drain_g(t - 1);
+      __syncthreads();
+    };
+    load_g(0, pa);
+    if (nch > 1) load_g(1, pb);
+    for (int t = 0; t <= nch; t += 2) {
+      step_g(t, pa);
+      if (t + 1 <= nch) step_g(t + 1, pb);
+    }
+    // G = (Re^T Re + Im^T Im) + i (Re^T Im - Im^T Re)
+    for (int e = tid; e < W * W; e += 256) {
+      const int i = e / W, j = e - i * W;
+      const float2 p = V[i * LDG + j];
+      G[i * LDG + j].x += p.x;
+      G[i * LDG + j].y -= p.y;
     }
     __syncthreads();
   }
@@ -1890,88 +1952,22 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     if (skip) goto cleanup;
   }
-  // ---- 3. cyclic two-sided Jacobi on G, V <- V J for every rotation J (as in k_jacobi_blk)
-  for (int e = tid; e < W * W; e += 256) {
-    const int i = e / W, j = e - i * W;
-    V[i * LDG + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-  }
-  if (tid == 0) any_s = 0;
-  __syncthreads();
-  for (int sw = 0; sw < max_inner; ++sw) {
-    for (int ir = 0; ir < W - 1; ++ir) {
-      if (tid < W / 2) {
-        int a, b;
-        rr_pair(tid, ir, W, a, b);
-        const float al = G[a * LDG + a].x, be = G[b * LDG + b].x;
-        const float2 ga = G[a * LDG + b];
-        const float g = sqrtf(abs2(ga));
-        int act = 0;
-        if (al > floor2 && be > floor2 && g > 0.f && g / (sqrtf(al) * sqrtf(be)) > tol) {
-          const float zeta = (be - al) / (2.f * g);
-          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float c = 1.f / sqrtf(1.f + tt * tt);
-          const float sn = c * tt;
-          rc[tid] = c;
-          rse[tid] = make_float2(sn * ga.x / g, sn * ga.y / g);
-          act = 1;
-          any_s = 1;
-        }
-        ract[tid] = act;
-      }
-      __syncthreads();
-      for (int e = tid; e < 2 * (W / 2) * W; e += 256) {
-        const int which = e / ((W / 2) * W), rest = e - which * ((W / 2) * W);
-        const int p = rest / W, i = rest - p * W;
-        if (!ract[p]) continue;
-        int a, b;
-        rr_pair(p, ir, W, a, b);
-        float2* Mx = which ? V : G;
-        const float c = rc[p];
-        const float2 se = rse[p], sec = conj(se);
-        const float2 x = Mx[i * LDG + a], y = Mx[i * LDG + b];
-        Mx[i * LDG + a] = c * x - sec * y;
-        Mx[i * LDG + b] = se * x + c * y;
-      }
-      __syncthreads();
-      for (int e = tid; e < (W / 2) * W; e += 256) {
-        const int p = e / W, j = e - p * W;
-        if (!ract[p]) continue;
-        int a, b;
-        rr_pair(p, ir, W, a, b);
-        const float c = rc[p];
-        const float2 se = rse[p], sec = conj(se);
-        const float2 x = G[a * LDG + j], y = G[b * LDG + j];
-        G[a * LDG + j] = c * x - se * y;
-        G[b * LDG + j] = sec * x + c * y;
-      }
-      __syncthreads();
-      if (tid < W / 2 && ract[tid]) {
-        int a, b;
-        rr_pair(tid, ir, W, a, b);
-        G[a * LDG + b] = make_float2(0.f, 0.f);
-        G[b * LDG + a] = make_float2(0.f, 0.f);
-        G[a * LDG + a].y = 0.f;
-        G[b * LDG + b].y = 0.f;
-      }
-      __syncthreads();
-    }
-    const int more = any_s;
-    __syncthreads();
-    if (!more) break;
-    if (tid == 0) any_s = 0;
-    __syncthreads();
-  }
-  // ---- 4. X_P <- X_P V.  B = V^T planes in buffer 1: B(n, k) = V(k, n)
+  // ---- 3. two-sided Jacobi on G, V <- V J for every rotation J
+  jac_inner<float, W>(G, V, LDG, floor2, tol, max_inner, rc, rse, ract, rpa, rpb, &any_s);
+  // ---- 4. X_P <- X_P V.  B = V^T planes in region 0: B(n, k) = V(k, n)
   for (int e = tid; e < W * (W / 4); e += 256) {
     const int n = e >> 4, kq = e & 15;
     float2 v4[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) v4[i] = V[(4 * kq + i) * LDG + n];
-    jt_store4(buf[1], tc_kmajor(n, 4 * kq, JT_SBO), v4);
+    jt_store4(reg0, tc_kmajor(n, 4 * kq, JT_SBO), v4);
   }
+  __syncthreads();   // V is read: its region now takes the second A buffer
   {
-    // A: thread t stages rows m = e % 64, columns 4 (e / 64)..+3, e = t + 256 q
-    auto load_upd = [&](int t) {
+    unsigned char* abuf[2] = {reg1, sm + 2 * JT_REGION};
+    float2 pa[4][4], pb[4][4];
+    // A: unit e = tid + 256 q stages row m = e % 64 of the chunk, columns 4 (e / 64) .. + 3
+    auto load_u = [&](int t, float2 (&pf)[4][4]) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int e = tid + 256 * q, m = e & 63, cq = e >> 6, row = t * JT_CH + m;
@@ -1982,35 +1978,35 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
     };
-    load_upd(0);
-    for (int t = 0; t < nch; ++t) {
+    auto store_u = [&](unsigned char* b, const float2 (&pf)[4][4]) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int e = tid + 256 * q;
-        jt_store4(buf[0], tc_kmajor(e & 63, 4 * (e >> 6), JT_SBO), pf[q]);
+        jt_store4(b, tc_kmajor(e & 63, 4 * (e >> 6), JT_SBO), pf[q]);
       }
-      tc_fence_async_smem();
-      __syncthreads();
+    };
+    auto mma_u = [&](unsigned char* b, int t) {
       if (tid == 0 && !fail) {
         tc_fence_after();
-        const uint32_t a = tc_smem_u32(buf[0]), b = tc_smem_u32(buf[1]);
+        const uint32_t a = tc_smem_u32(b), bb = tc_smem_u32(reg0), dd = tmem + (uint32_t)(t & 1) * 128;
 #pragma unroll
-        for (int ks = 0; ks < W / 8; ++ks) jt_mma12(tmem, tmem + 64, a, b, (uint32_t)ks * 256, ks == 0 ? 0u : 1u, false);
-        tc_commit(&mbar[2]);
+        for (int ks = 0; ks < W / 8; ++ks) jt_mma12(dd, dd + 64, a, bb, (uint32_t)ks * 256, ks == 0 ? 0u : 1u);
+        tc_commit(&mbar[2 + (t & 1)]);
       }
-      if (t + 1 < nch) load_upd(t + 1);   // rows of the next chunk: disjoint from the ones written below
-      if (!fail && !tc_wait(&mbar[2], (uint32_t)(t & 1))) atomicExch(&fail, 1);
+    };
+    // warps 0-3 write output columns 0-31, warps 4-7 columns 32-63; lanes 0-15 of quadrant q own
+    // rows 16 q + lane of the chunk (M = 64 accumulator layout)
+    auto drain_u = [&](int u) {
+      if (!fail && !tc_wait(&mbar[2 + (u & 1)], (uint32_t)((u >> 1) & 1))) atomicExch(&fail, 1);
       tc_fence_after();
-      // warps 0-3 write output columns 0-31, warps 4-7 columns 32-63; lanes 0-15 of quadrant q own
-      // rows 16 q + lane of the chunk
       const int n0 = warp < 4 ? 0 : 32;
       for (int c0 = 0; c0 < 32; c0 += 16) {
         uint32_t vr[16], vi[16];
-        const uint32_t la = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(n0 + c0);
+        const uint32_t la = tmem + (uint32_t)(u & 1) * 128 + ((uint32_t)(32 * quad) << 16) + (uint32_t)(n0 + c0);
         tc_ld16(la, vr);
         tc_ld16(la + 64, vi);
         tc_wait_ld();
-        const int row = t * JT_CH + 16 * quad + lane;
+        const int row = u * JT_CH + 16 * quad + lane;
         if (lane < 16 && row < d.r && !fail) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
@@ -2020,15 +2016,33 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
       tc_fence_before();
+    };
+    // chunk t + 2 is loaded while chunk t - 1 is written back: disjoint rows
+    auto step_u = [&](int t, float2 (&pf)[4][4]) {
+      if (t < nch) {
+        unsigned char* b = abuf[t & 1];   // last read by chunk t - 2's MMAs, drained before
+        store_u(b, pf);
+        if (t + 2 < nch) load_u(t + 2, pf);
+        tc_fence_async_smem();
+        __syncthreads();
+        mma_u(b, t);
+      }
+      if (t >= 1) drain_u(t - 1);
       __syncthreads();
+    };
+    load_u(0, pa);
+    if (nch > 1) load_u(1, pb);
+    for (int t = 0; t <= nch; t += 2) {
+      step_u(t, pa);
+      if (t + 1 <= nch) step_u(t + 1, pb);
     }
   }
   if (tid == 0 && !fail) atomicAdd(rows_updated, (unsigned long long)d.r);
 cleanup:
   if (tid == 0) {
     if (fail) atomicExch(&g_jac_error, 1);
-    tc_commit(&mbar[3]);                // MMAs still in flight after a failed wait finish first
-    tc_wait(&mbar[3], 0u);
+    tc_commit(&mbar[4]);                // MMAs still in flight after a failed wait finish first
+    tc_wait(&mbar[4], 0u);
   }
   tc_fence_before();
   __syncthreads();
