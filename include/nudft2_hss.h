@@ -179,6 +179,22 @@ nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const v
                                        const int* nrhs, void* const* d_c, const int64_t* ldc, int threads,
                                        void* stream, nudft2_status* status);
 
+/* build + factor + solve + free for each problem of a batch, the problems run to completion
+ * concurrently on `threads` host threads (each on its own stream; largest problems start first),
+ * so that at most `threads` handles hold device memory at a time: the batched offline/online
+ * stages of Sec. 4.1 when the factorizations need not outlive the solve.  Problem i: points
+ * d_x[i], d_y[i] (M[i]), sizes nx[i] x ny[i], options opts[i] (opts may be NULL), data d_f[i]
+ * (M[i] x nrhs[i], ld ldf[i], complex128), solution d_c[i] (N_i x nrhs[i], ld ldc[i], complex128,
+ * lexicographic order as for nudft2_hss_solve).  A problem that runs out of device memory while
+ * others hold theirs waits for one of them to finish and starts again; alone on the device its
+ * ENOMEM stands.  status[i] (may be NULL) receives each problem's code.  Returns OK or the first
+ * failing problem's code (nudft2_last_error names it).  Errors: EINVAL, and those of build, factor
+ * and solve per problem. */
+nudft2_status nudft2_hss_run_batched(int count, const double* const* d_x, const double* const* d_y,
+                                     const int64_t* M, const int* nx, const int* ny, const nudft2_opts* opts,
+                                     const void* const* d_f, const int64_t* ldf, const int* nrhs, void* const* d_c,
+                                     const int64_t* ldc, int threads, void* stream, nudft2_status* status);
+
 /* plsqr: the direct solver as a preconditioner for LSQR (Sec. 4.1, Sec. 5): LSQR (Paige &
  * Saunders) on B c = P f with B = P A and P = F^{-1} G~_hss^+ (one URV solve + 2D inverse DFT, no
  * refinement), B^* = A^* P^* (2D DFT + adjoint URV solve).  A and A^* are the exact FP64 apply of

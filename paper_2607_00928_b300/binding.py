@@ -77,6 +77,9 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(Opts), ci, ci, vp, pp, ctypes.POINTER(ci)]
     L.nudft2_hss_solve_batched.argtypes = [ci, pp, pp, ctypes.POINTER(i64), ctypes.POINTER(ci), pp,
                                            ctypes.POINTER(i64), ci, vp, ctypes.POINTER(ci)]
+    L.nudft2_hss_run_batched.argtypes = [ci, pp, pp, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                         ctypes.POINTER(Opts), pp, ctypes.POINTER(i64), ctypes.POINTER(ci), pp,
+                                         ctypes.POINTER(i64), ci, vp, ctypes.POINTER(ci)]
     L.nudft2_hss_free.argtypes = [vp]
     L.nudft2_hss_free.restype = None
     L.nudft2_psi_eval.argtypes = [vp, i64, ci, vp, vp]
@@ -93,7 +96,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_hss_checkpoint.argtypes = [vp, ci, vp]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
-              "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_plsqr",
+              "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_run_batched", "nudft2_hss_plsqr",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint"):
         getattr(L, f).restype = ctypes.c_int
@@ -383,6 +386,29 @@ def solve_batched(handles, fs, threads: int = 8, stream=None):
     ldc = (ctypes.c_int64 * n)(*[h.N for h in handles])
     nr = (ctypes.c_int * n)(*[fc.shape[0] for fc in fcs])
     _check(lib().nudft2_hss_solve_batched(n, hp, pf, ldf, nr, pc, ldc, threads, _stream(stream), None))
+    return [c[0] if f.dim() == 1 else c.t() for c, f in zip(cs, fs)]
+
+
+def run_batched(problems, fs, threads: int = 8, stream=None):
+    """Build, factor and solve every problem of a batch, each run to completion and freed
+    (nudft2_hss_run_batched): at most `threads` factorizations hold device memory at a time.
+    problems: dicts as for build_batched; fs[i]: (M_i,) or (M_i, s_i) complex128 CUDA.  Returns
+    the list of c (N_i,) or (N_i, s_i)."""
+    n = len(problems)
+    xs = [torch.as_tensor(p["x"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
+    ys = [torch.as_tensor(p["y"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
+    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max", "levels_y")
+    opts = (Opts * n)(*[_opts(**{k: p[k] for k in keys if k in p}) for p in problems])
+    Ns = [int(p["nx"]) * int(p["ny"]) for p in problems]
+    fcs = [_colmajor(f, x.numel()) for f, x in zip(fs, xs)]
+    cs = [torch.empty((fc.shape[0], N), dtype=torch.complex128, device="cuda") for fc, N in zip(fcs, Ns)]
+    vpa = ctypes.c_void_p * n
+    _check(lib().nudft2_hss_run_batched(
+        n, vpa(*[t.data_ptr() for t in xs]), vpa(*[t.data_ptr() for t in ys]),
+        (ctypes.c_int64 * n)(*[t.numel() for t in xs]), (ctypes.c_int * n)(*[int(p["nx"]) for p in problems]),
+        (ctypes.c_int * n)(*[int(p["ny"]) for p in problems]), opts, vpa(*[fc.data_ptr() for fc in fcs]),
+        (ctypes.c_int64 * n)(*[x.numel() for x in xs]), (ctypes.c_int * n)(*[fc.shape[0] for fc in fcs]),
+        vpa(*[c.data_ptr() for c in cs]), (ctypes.c_int64 * n)(*Ns), threads, _stream(stream), None))
     return [c[0] if f.dim() == 1 else c.t() for c, f in zip(cs, fs)]
 
 

@@ -4,9 +4,11 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -1229,6 +1231,66 @@ nudft2_status nudft2_hss_solve_batched(int count, const nudft2_hss_t* h, const v
   if (r != NUDFT2_OK) return r;
   if (status)
     for (int i = 0; i < count; ++i) status[i] = st[i];
+  return batch_result(st, msg);
+}
+
+nudft2_status nudft2_hss_run_batched(int count, const double* const* d_x, const double* const* d_y,
+                                     const int64_t* M, const int* nx, const int* ny, const nudft2_opts* opts,
+                                     const void* const* d_f, const int64_t* ldf, const int* nrhs, void* const* d_c,
+                                     const int64_t* ldc, int threads, void* stream, nudft2_status* status) {
+  if (count < 1 || !d_x || !d_y || !M || !nx || !ny || !d_f || !ldf || !nrhs || !d_c || !ldc) {
+    g_err = "run_batched: bad arguments";
+    return NUDFT2_EINVAL;
+  }
+  // largest problems first, so that the last ones to start are the short ones
+  std::vector<int> order((size_t)count);
+  for (int i = 0; i < count; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)M[a] * std::sqrt((double)nx[a] * ny[a]) > (double)M[b] * std::sqrt((double)nx[b] * ny[b]);
+  });
+  std::vector<nudft2_status> st((size_t)count, NUDFT2_OK);
+  std::vector<std::string> msg((size_t)count);
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0;
+  long finished = 0;
+  auto r = guard([&] {
+    run_pool(count, threads, [&](int k) {
+      const int i = order[(size_t)k];
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        active++;
+      }
+      nudft2_status s = NUDFT2_OK;
+      for (;;) {
+        nudft2_hss_t h = nullptr;
+        s = nudft2_hss_build(d_x[i], d_y[i], M[i], nx[i], ny[i], opts ? &opts[i] : nullptr, stream, &h);
+        if (s == NUDFT2_OK) s = nudft2_hss_factor(h, stream);
+        if (s == NUDFT2_OK) s = nudft2_hss_solve(h, d_f[i], ldf[i], nrhs[i], d_c[i], ldc[i], stream);
+        if (s != NUDFT2_OK) msg[(size_t)i] = nudft2_last_error();
+        if (h) nudft2_hss_free(h);
+        if (s != NUDFT2_ENOMEM) break;
+        // out of device memory while other problems hold theirs: wait for one of them to finish,
+        // then start this one again; alone on the device, the failure stands
+        std::unique_lock<std::mutex> lk(mu);
+        if (active <= 1) break;
+        const long seen = finished;
+        active--;
+        cv.wait(lk, [&] { return finished > seen || active == 0; });
+        active++;
+      }
+      st[(size_t)i] = s;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        active--;
+        finished++;
+      }
+      cv.notify_all();
+    });
+  });
+  if (r != NUDFT2_OK) return r;
+  if (status)
+    for (int i = 0; i < count; ++i) status[i] = st[(size_t)i];
   return batch_result(st, msg);
 }
 

@@ -63,6 +63,27 @@ def test_batched_mixed_precision_refines(nh):
         h.close()
 
 
+def test_run_batched_matches_build_and_solve(nh):
+    """nudft2_hss_run_batched (each problem built, factored, solved and freed by the pool) gives the
+    same c as build_batched + solve_batched, for more problems than threads, with the failing
+    problem named."""
+    ps = _problems(7, 200, eps=1e-10)
+    fs = [torch.from_numpy(p["f"]).cuda() for p in ps]
+    cs = [c.cpu().numpy() for c in nh.run_batched(ps, fs, threads=3)]
+    hs = nh.build_batched(ps, threads=3)
+    cs2 = [c.cpu().numpy() for c in nh.solve_batched(hs, fs, threads=3)]
+    for h in hs:
+        h.close()
+    for p, a, b in zip(ps, cs, cs2):
+        assert _relcols(a, b) < 1e-12
+        assert _relcols(a, p["c_true"]) < 1e-8
+    ps[4]["x"] = ps[4]["x"].copy()
+    ps[4]["x"][3] = -0.25
+    with pytest.raises(nh.NudftError) as e:
+        nh.run_batched(ps, fs, threads=3)
+    assert "problem 4" in str(e.value)
+
+
 def test_batched_names_the_failing_problem(nh):
     ps = _problems(3, 170, eps=1e-10)
     ps[1]["x"] = ps[1]["x"].copy()
@@ -75,7 +96,7 @@ def test_batched_names_the_failing_problem(nh):
 def test_config4_full_size_batch(nh):
     """The batched workload at its full size: 64 problems, n_x, n_y in {32, ..., 256}, M/N in
     [1.5, 4], 8 right-hand sides each, built, factored and solved together in mixed precision
-    refined to 1e-8.  Every problem recovers its c_true (consistent data) to the 1e-8 target, and
+    refined to 1e-8 (nudft2_hss_run_batched: at most 8 factorizations alive at a time).  Every problem recovers its c_true (consistent data) to the 1e-8 target, and
     the oracle's direct sum confirms the data of the largest problem at sampled points."""
     from synthetic import batched_uneven
     ps = batched_uneven()
@@ -90,9 +111,6 @@ def test_config4_full_size_batch(nh):
     idx = np.random.default_rng(4).choice(ps[big]["x"].size, 16, replace=False)
     ref = orc.forward(ps[big]["x"][idx], ps[big]["y"][idx], ps[big]["c_true"], ps[big]["nx"], ps[big]["ny"])
     assert np.max(np.abs(fs[big].cpu().numpy()[idx] - ref)) < 1e-10 * np.max(np.abs(ref))
-    hs = nh.build_batched(ps, threads=8)
-    cs = nh.solve_batched(hs, fs, threads=8)
+    cs = nh.run_batched(ps, fs, threads=8)   # each problem built, factored, solved and freed
     for p, c in zip(ps, cs):
         assert _relcols(c.cpu().numpy(), p["c_true"]) < 1e-8
-    for h in hs:
-        h.close()
