@@ -325,6 +325,7 @@ static void la_qr(void* d_a, int m, int n, int lda, void* d_q, int ldq, int grou
   A.p = (cplx<R>*)d_a; A.m = m; A.n = n; A.ld = lda;
   auto Q = ops.qr({A}, keep);
   if (grouped) ops.group_wy(Q, keep);
+  else Q[0].Tg = nullptr;   // apply panel by panel
   Mat<R> Qm;
   Qm.p = (cplx<R>*)d_q; Qm.m = m; Qm.n = m; Qm.ld = ldq;
   ops.set_identity({Qm});
@@ -343,6 +344,7 @@ static void la_qr_apply(void* d_a, int m, int n, int lda, void* d_c, int s, int 
   A.p = (cplx<R>*)d_a; A.m = m; A.n = n; A.ld = lda;
   auto Q = ops.qr({A}, keep);
   if (grouped) ops.group_wy(Q, keep);
+  else Q[0].Tg = nullptr;   // apply panel by panel
   Mat<R> C;
   C.p = (cplx<R>*)d_c; C.m = m; C.n = s; C.ld = ldc;
   ops.apply_q_stream(Q, {C}, conj);

@@ -948,6 +948,22 @@ __global__ void __launch_bounds__(256) k_qr_panel_cl(const QRD<R>* __restrict__ 
   }
 }
 
+// S = strictly-upper(Y) + diag(1/tau), tau read from the diagonal of the panel T blocks.
+template <typename R> struct GrpD { cplx<R>* Y; const cplx<R>* Tp; int w, g0, ldy; };
+template <typename R> __global__ void k_group_s(const GrpD<R>* __restrict__ ds, int nb) {
+  const GrpD<R> d = ds[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.w * d.w) return;
+  const int i = e % d.w, j = e / d.w;
+  cplx<R>& y = d.Y[(size_t)i + (size_t)j * d.ldy];
+  if (i > j) y = czero<R>();
+  else if (i == j) {
+    const int c = d.g0 + i, p = c / nb, o = c % nb;
+    const R tau = d.Tp[(size_t)p * nb * nb + o + (size_t)o * nb].x;
+    y = mkc(R(1) / tau, R(0));
+  }
+}
+
 template <typename R>
 std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   std::vector<QFac<R>> out(A.size());
@@ -971,7 +987,8 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
     q.V = f.V; q.ldv = f.ldv;
     q.tau = (R*)ar_->alloc(std::max(k, 1) * sizeof(R));
     q.Tp = f.Tp;
-    q.W = (cplx<R>*)ar_->alloc((size_t)2 * NB * std::max(a.n, 1) * sizeof(cplx<R>));
+    q.W = (cplx<R>*)ar_->alloc((size_t)2 * (k > GW ? GW : NB) * std::max(a.n, 1) * sizeof(cplx<R>));
+    if (k > GW) f.Tg = (cplx<R>*)keep.alloc((size_t)((k + GW - 1) / GW) * GW * GW * sizeof(cplx<R>));
     kmax = std::max(kmax, k);
   }
   if (kmax == 0) { ar_->release(mk); return out; }
@@ -981,7 +998,13 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   for (auto& q : d) mmax = std::max(mmax, q.m);
   int qcs = 1;
   while (qcs < 8 && (long long)qcs * 1024 < mmax) qcs *= 2;
-  for (int j0 = 0; j0 < kmax; j0 += NB) {
+  // Two-level blocking for k > GW: the 32-column panels of one group of GW columns update only
+  // the group's own columns; then the group's merged compact-WY factor (T_g from the UT identity,
+  // as in group_wy) updates the rest of the matrix with GEMMs of depth GW.  Matrices with k <= GW
+  // update their whole trailing matrix panel by panel.
+  for (int J0 = 0; J0 < kmax; J0 += GW) {
+  const int J1 = J0 + GW;
+  for (int j0 = J0; j0 < std::min(J1, kmax); j0 += NB) {
     double fl = 0;
     if (prof.on)
       for (const auto& q : d) {
@@ -1017,7 +1040,8 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
       const int k = std::min(q.m, q.n);
       if (j0 >= k) continue;
       const int b = std::min(NB, k - j0);
-      const int n2 = q.n - j0 - b;
+      const int cend = k > GW ? std::min(J1, q.n) : q.n;   // columns this panel updates
+      const int n2 = cend - j0 - b;
       if (n2 <= 0) continue;
       const int mm = q.m - j0;
       cplx<R>* Vp = q.V + (size_t)j0 + (size_t)j0 * q.ldv;
@@ -1033,24 +1057,53 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
     gemm(g2);
     gemm(g3);
   }
+  // the group's T_g = (striu(V_g^* V_g) + diag(1 / tau))^{-1}, then the rest of the matrix
+  {
+    auto mg = ar_->mark();
+    std::vector<GemmD<R>> gs, g1, g2, g3;
+    std::vector<GrpD<R>> gd;
+    std::vector<Mat<R>> S, T;
+    int wmax = 0;
+    for (size_t i = 0; i < d.size(); ++i) {
+      const QRD<R>& q = d[i];
+      const int k = std::min(q.m, q.n);
+      if (k <= GW || J0 >= k) continue;
+      const int w = std::min(GW, k - J0), mm = q.m - J0;
+      const cplx<R>* Vg = q.V + (size_t)J0 + (size_t)J0 * q.ldv;
+      Mat<R> Sm = ar_->template mat<R>(w, w);
+      gs.push_back({Vg, Vg, Sm.p, w, w, mm, q.ldv, q.ldv, Sm.ld, OP_C, OP_N, R(1), R(0)});
+      gd.push_back({Sm.p, q.Tp, w, J0, Sm.ld});
+      S.push_back(Sm);
+      Mat<R> Tm;
+      Tm.p = out[i].Tg + (size_t)(J0 / GW) * GW * GW; Tm.m = w; Tm.n = w; Tm.ld = GW;
+      T.push_back(Tm);
+      wmax = std::max(wmax, w);
+      const int n2 = q.n - J1;
+      if (n2 <= 0) continue;
+      cplx<R>* A2 = q.A + (size_t)J0 + (size_t)J1 * q.lda;
+      cplx<R>* W1 = q.W;
+      cplx<R>* W2 = q.W + (size_t)GW * std::max(q.n, 1);
+      g1.push_back({Vg, A2, W1, w, n2, mm, q.ldv, q.lda, GW, OP_C, OP_N, R(1), R(0)});
+      g2.push_back({Tm.p, W1, W2, w, n2, w, GW, GW, GW, OP_C, OP_N, R(1), R(0)});
+      g3.push_back({Vg, W2, A2, mm, n2, w, q.ldv, GW, q.lda, OP_N, OP_N, R(-1), R(1)});
+    }
+    if (!gs.empty()) {
+      gemm(gs);
+      auto dg = upload(gd);
+      dim3 grid((wmax * wmax + 255) / 256, (unsigned)gd.size());
+      k_group_s<R><<<grid, 256, 0, st_>>>(dg, NB);
+      NH_LAUNCH_CK();
+      count();
+      trinv(S, T);
+      gemm(g1);
+      gemm(g2);
+      gemm(g3);
+    }
+    ar_->release(mg);
+  }
+  }
   ar_->release(mk);
   return out;
-}
-
-// S = strictly-upper(Y) + diag(1/tau), tau read from the diagonal of the panel T blocks.
-template <typename R> struct GrpD { cplx<R>* Y; const cplx<R>* Tp; int w, g0, ldy; };
-template <typename R> __global__ void k_group_s(const GrpD<R>* __restrict__ ds, int nb) {
-  const GrpD<R> d = ds[blockIdx.y];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.w * d.w) return;
-  const int i = e % d.w, j = e / d.w;
-  cplx<R>& y = d.Y[(size_t)i + (size_t)j * d.ldy];
-  if (i > j) y = czero<R>();
-  else if (i == j) {
-    const int c = d.g0 + i, p = c / nb, o = c % nb;
-    const R tau = d.Tp[(size_t)p * nb * nb + o + (size_t)o * nb].x;
-    y = mkc(R(1) / tau, R(0));
-  }
 }
 
 template <typename R> void Ops<R>::group_wy(std::vector<QFac<R>>& Q, Arena& keep) {
@@ -1060,7 +1113,7 @@ template <typename R> void Ops<R>::group_wy(std::vector<QFac<R>>& Q, Arena& keep
   std::vector<Mat<R>> S, T;
   int wmax = 0;
   for (auto& q : Q) {
-    if (q.k <= NB) continue;                      // a single panel is already one block
+    if (q.k <= NB || q.Tg) continue;              // a single panel is one block; qr() merged k > GW
     const int ng = (q.k + GW - 1) / GW;
     q.Tg = (cplx<R>*)keep.alloc((size_t)ng * GW * GW * sizeof(cplx<R>));
     for (int gi = 0; gi < ng; ++gi) {

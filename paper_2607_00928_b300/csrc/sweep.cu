@@ -10,10 +10,11 @@
 //   1. k_wy_part:   partial V_b^* C over one slab of rows per CTA; thread t owns reflector column
 //                   t; V and C tiles are double-buffered in shared memory with cp.async.  A node
 //                   with a single slab writes W1 = V_b^* C directly;
-//   2. k_wy_reduce: W1 = the sum of a node's partials, in slab order (deterministic), one
-//                   element per thread;
+//   2. k_wy_reduce: W1 = the sum of a node's partials in a fixed order (deterministic), four
+//                   lanes per element;
 //   3. k_wy_tmul:   W2 = T^* W1 (Q^* C) or T W1 (Q C); a few CTAs per node, one slice of rows each;
-//   4. k_wy_update: C -= V_b W2; thread t owns one row, W2 sits in shared memory.
+//   4. k_wy_update: C -= V_b W2; two threads per row (one per half of the reflectors), W2 in
+//                   shared memory.
 // Blocks are applied in increasing order for Q^* C and in decreasing order for Q C.  Every node of
 // a level (and every chunk of S columns of its right-hand sides) shares the same four launches
 // per block step.  Rows above a block's first reflector are untouched (the vectors are zero
@@ -130,18 +131,34 @@ __global__ void __launch_bounds__(WY_T) k_wy_part(const WyD<R>* __restrict__ ds,
   }
 }
 
-// W1 = sum of the node's partials in slab order, one element of W1 per thread
+// W1 = sum of the node's partials, 64 elements of W1 per CTA: four lanes per element each sum the
+// slabs p = lane (mod 4) (several loads in flight), then the four lane sums are added in a fixed
+// order -- deterministic
 template <typename R, int S>
 __global__ void __launch_bounds__(WY_T) k_wy_reduce(const WyD<R>* __restrict__ ds, int nd,
                                                    const cplx<R>* __restrict__ part, cplx<R>* __restrict__ w1) {
   const int di = wy_find<R, 2>(ds, nd, blockIdx.x);
   const WyD<R> d = ds[di];
-  const int e = (blockIdx.x - d.pre_r) * WY_T + threadIdx.x;
-  if (e >= d.b * S) return;
-  const cplx<R>* pp = part + (size_t)d.part0 * WY_T * S + e;
+  const int el = threadIdx.x & 63, pl = threadIdx.x >> 6;
+  const int e = (blockIdx.x - d.pre_r) * 64 + el;
+  __shared__ cplx<R> acc4[4][64];
   cplx<R> sum = czero<R>();
-  for (int p = 0; p < d.nparts; ++p) sum = sum + pp[(size_t)p * WY_T * S];
-  w1[(size_t)di * WY_T * S + e] = sum;
+  if (e < d.b * S) {
+    const cplx<R>* pp = part + (size_t)d.part0 * WY_T * S + e;
+    int p = pl;
+    for (; p + 12 < d.nparts; p += 16) {
+      const cplx<R> a0 = pp[(size_t)p * WY_T * S], a1 = pp[(size_t)(p + 4) * WY_T * S];
+      const cplx<R> a2 = pp[(size_t)(p + 8) * WY_T * S], a3 = pp[(size_t)(p + 12) * WY_T * S];
+      sum = sum + a0;
+      sum = sum + a1;
+      sum = sum + a2;
+      sum = sum + a3;
+    }
+    for (; p < d.nparts; p += 4) sum = sum + pp[(size_t)p * WY_T * S];
+  }
+  acc4[pl][el] = sum;
+  __syncthreads();
+  if (pl == 0 && e < d.b * S) w1[(size_t)di * WY_T * S + e] = ((acc4[0][el] + acc4[1][el]) + acc4[2][el]) + acc4[3][el];
 }
 
 // W2 rows of slice blockIdx.x % WY_MID of node blockIdx.x / WY_MID: op(T) W1, op = ^* (conj) or none
@@ -170,44 +187,56 @@ __global__ void __launch_bounds__(WY_T) k_wy_tmul(const WyD<R>* __restrict__ ds,
   }
 }
 
-// C(r, :) -= V(r, :) W2, one row per thread
+// C(r, :) -= V(r, :) W2 for 128 rows per CTA: thread t takes row t % 128 and half t / 128 of the
+// reflector columns (eight loads in flight); the halves are added through shared memory.
 template <typename R, int S>
 __global__ void __launch_bounds__(WY_T) k_wy_update(const WyD<R>* __restrict__ ds, int nd,
                                                    const cplx<R>* __restrict__ w2) {
   const int di = wy_find<R, 1>(ds, nd, blockIdx.x);
   const WyD<R> d = ds[di];
-  const int r = (blockIdx.x - d.pre_u) * WY_T + threadIdx.x;
+  const int rl = threadIdx.x & 127, half = threadIdx.x >> 7;
+  const int r = (blockIdx.x - d.pre_u) * 128 + rl;
   extern __shared__ __align__(16) unsigned char wy_raw[];
   cplx<R>* W2 = reinterpret_cast<cplx<R>*>(wy_raw);   // b x S
+  cplx<R>* Hs = W2 + WY_T * S;                       // 128 x S: the second half's sums
   const cplx<R>* src = w2 + (size_t)di * WY_T * S;
   for (int e = threadIdx.x; e < d.b * S; e += WY_T) W2[e] = src[e];
   __syncthreads();
-  if (r >= d.m) return;
   cplx<R> acc[S];
 #pragma unroll
   for (int q = 0; q < S; ++q) acc[q] = czero<R>();
-  const cplx<R>* v = d.V + r;
-  int i = 0;
-  for (; i + 4 <= d.b; i += 4) {
-    cplx<R> x[4];
+  const int hb = (d.b + 1) / 2, i0 = half * hb, i1 = min(d.b, i0 + hb);
+  if (r < d.m) {
+    const cplx<R>* v = d.V + r;
+    int i = i0;
+    for (; i + 8 <= i1; i += 8) {
+      cplx<R> x[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = v[(size_t)(i + u) * d.ldv];
+      for (int u = 0; u < 8; ++u) x[u] = v[(size_t)(i + u) * d.ldv];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int q = 0; q < S; ++q) cfma(acc[q], x[u], W2[(i + u) * S + q]);
-  }
-  for (; i < d.b; ++i) {
-    const cplx<R> x = v[(size_t)i * d.ldv];
-#pragma unroll
-    for (int q = 0; q < S; ++q) cfma(acc[q], x, W2[i * S + q]);
-  }
-#pragma unroll
-  for (int q = 0; q < S; ++q)
-    if (q < d.s) {
-      cplx<R>& c = d.C[(size_t)r + (size_t)q * d.ldc];
-      c = c - acc[q];
+        for (int q = 0; q < S; ++q) cfma(acc[q], x[u], W2[(i + u) * S + q]);
     }
+    for (; i < i1; ++i) {
+      const cplx<R> x = v[(size_t)i * d.ldv];
+#pragma unroll
+      for (int q = 0; q < S; ++q) cfma(acc[q], x, W2[i * S + q]);
+    }
+  }
+  if (half == 1) {
+#pragma unroll
+    for (int q = 0; q < S; ++q) Hs[rl * S + q] = acc[q];
+  }
+  __syncthreads();
+  if (half == 0 && r < d.m) {
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      if (q < d.s) {
+        cplx<R>& c = d.C[(size_t)r + (size_t)q * d.ldc];
+        c = c - (acc[q] + Hs[rl * S + q]);
+      }
+  }
 }
 
 template <typename R>
@@ -252,15 +281,15 @@ void Ops<R>::apply_q_stream_s(const std::vector<QFac<R>>& Q, const std::vector<M
       w.C = C[jb.i].p + j0 + (size_t)jb.c0 * C[jb.i].ld;
       w.ldv = q.ldv; w.ldt = B; w.ldc = C[jb.i].ld;
       w.m = mm; w.b = std::min(B, q.k - j0); w.s = jb.s;
-      // at most 64 slabs per node keeps the final sum short
-      w.rows = std::max(rows_all, ((mm + 63) / 64 + TR - 1) / TR * TR);
+      // at most 256 slabs per node keeps the partial sums small next to V
+      w.rows = std::max(rows_all, ((mm + 255) / 256 + TR - 1) / TR * TR);
       w.nparts = (mm + w.rows - 1) / w.rows;
       w.pre_p = p_cta; w.pre_u = u_cta; w.pre_r = r_cta; w.part0 = slot;
       p_cta += w.nparts;
-      u_cta += (mm + WY_T - 1) / WY_T;
+      u_cta += (mm + 127) / 128;
       if (w.nparts > 1) {
         slot += w.nparts;
-        r_cta += (w.b * S + WY_T - 1) / WY_T;
+        r_cta += (w.b * S + 63) / 64;
       }
       steps[st].push_back(w);
     }
@@ -273,7 +302,7 @@ void Ops<R>::apply_q_stream_s(const std::vector<QFac<R>>& Q, const std::vector<M
   cplx<R>* w1 = (cplx<R>*)ar_->alloc(jobs.size() * per);
   cplx<R>* w2 = (cplx<R>*)ar_->alloc(jobs.size() * per);
   const size_t smem_p = (2 * (size_t)WY_T * (TR + 1) + 2 * (size_t)TR * S) * sizeof(cplx<R>);
-  const size_t smem_u = per;
+  const size_t smem_u = per + (size_t)128 * S * sizeof(cplx<R>);
   static const bool attr = [&] {   // once per template instance (thread-safe static initialisation)
     NH_CK(cudaFuncSetAttribute(k_wy_part<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p));
     NH_CK(cudaFuncSetAttribute(k_wy_tmul<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u));
