@@ -171,6 +171,11 @@ template <typename R> class Ops {
   void gemm_class(const std::vector<GemmD<R>>& d, int cls);   // one operand-layout class
   int gemm_pick(const std::vector<GemmD<R>>& d, int cls);     // kernel kind: static rule or autotuner
   void gemm_run(const std::vector<GemmD<R>>& d, int cls, int kind);
+  // rank-revealing column-pivoted QR of every A (in place: R in the upper trapezoid of the first
+  // peff rows, zero below its diagonal) with pivots chosen blockwise on random sketches; perm[i]
+  // (A[i].n entries, device) receives the column order; stops at the rank the truncated SVD at
+  // eps can use (every remaining column norm <= 0.01 eps max column norm).
+  void qrcp_sketch(const std::vector<Mat<R>>& A, const std::vector<int*>& perm, double eps, std::vector<int>& peff);
   template <int S> void apply_q_stream_s(const std::vector<QFac<R>>& Q, const std::vector<Mat<R>>& C, bool conj);
   template <typename D> D* upload(const std::vector<D>& v);
   void* stage(const void* src, size_t bytes);

@@ -64,9 +64,10 @@ def test_exact_apply_forward_and_adjoint(nh, nx, ny, mx, my, s):
 
 
 # ------------------------------------------------------------------ HSS approximation (Thm. 3.7)
-@pytest.mark.parametrize("name", ["fp64_n16", "fp64_n32"])
+@pytest.mark.parametrize("name", ["fp64_n16", "fp64_n32", "fp64_n64", "fp64_n128"])
 def test_hss_forward_map_error_bound(nh, name):
-    """FAST_FWD applies A_fast = G~_hss F; ||A_fast - A|| / ||A|| stays within (1+C) eps."""
+    """FAST_FWD applies A_fast = G~_hss F; ||A_fast - A|| / ||A|| stays within (1+C) eps, up to
+    the n = 128 FP64 workload (three and four tree levels)."""
     w = WORKLOADS[name]
     x, y, _ = make_workload(w)
     h = nh.NudftHSS(x, y, w.nx, w.ny, eps=w.eps, levels=w.levels)

@@ -398,3 +398,20 @@ def test_matrix_free_gradient_matches_dense_gradient():
     assert np.max(np.abs(lam_m - lam_d)) < 1e-11 * np.max(np.abs(lam_d))
     assert np.max(np.abs(gx_m - gx_d[rows])) < 1e-10 * np.max(np.abs(gx_d))
     assert np.max(np.abs(gy_m - gy_d[rows])) < 1e-10 * np.max(np.abs(gy_d))
+
+
+def test_relres_and_relerr_closed_forms():
+    """The Sec. 5 error measures on cases with known values: for f = A c0, the relative residual
+    is 1 at c = 0 and at c = 2 c0 and vanishes at c = c0; the relative error of (1 + t) c_ref is
+    |t| per column, and each column is measured on its own."""
+    rng = np.random.default_rng(31)
+    nx, ny, M = 6, 5, 45
+    x, y = rng.random(M), rng.random(M)
+    c0 = rng.standard_normal((nx * ny, 2)) + 1j * rng.standard_normal((nx * ny, 2))
+    f = orc.forward(x, y, c0, nx, ny)
+    assert np.allclose(orc.relres(x, y, np.zeros_like(c0), f, nx, ny), 1.0, rtol=0, atol=1e-14)
+    assert np.allclose(orc.relres(x, y, 2 * c0, f, nx, ny), 1.0, rtol=0, atol=1e-13)
+    assert np.max(orc.relres(x, y, c0, f, nx, ny)) < 1e-14
+    c = c0 * np.array([1.5, 1 - 0.25j])[None, :]
+    assert np.allclose(orc.relerr(c, c0), [0.5, 0.25], rtol=0, atol=1e-15)
+    assert np.allclose(orc.relerr(c0[:, 0], c0[:, 0]), [0.0])
