@@ -2,8 +2,9 @@
 
 * Householder QR (single-CTA panels and cluster-cooperative panels for tall matrices):
   Q R = A, Q^* Q = I, |R_ii| equal to LAPACK's.
-* Truncated SVD (pivoted QR + one-sided Jacobi: blocked Gram steps, scalar rotations in
-  global memory, and cluster-resident scalar rotations):
+* Truncated SVD (pivoted QR -- pivots chosen blockwise on random sketches, or one per step --
+  + one-sided Jacobi: blocked Gram steps, scalar rotations in global memory, and
+  cluster-resident scalar rotations):
   singular values equal LAPACK's, P^* P = I, and the discarded part of C is below the
   threshold -- the truncation rule of the recompression (Sec. 2.2).
 """
@@ -67,6 +68,23 @@ def test_tsvd_fp64(nh, monkeypatch, jacobi, r, w, kind):
     assert np.max(np.abs(P.conj().T @ P - np.eye(k))) < 1e-12
     resid = C - P @ (P.conj().T @ C)
     assert np.linalg.norm(resid, 2) <= 2 * eps * s_ref[0] + 1e-13 * s_ref[0]
+
+
+@pytest.mark.parametrize("r,w,kind", CASES)
+def test_tsvd_fp64_classical_pivoting(nh, monkeypatch, r, w, kind):
+    """The truncated SVD with the one-pivot-per-step pivoted QR (NH_QRCP=exact) in place of the
+    sketch-pivoted blocks: the same singular values, truncation rank and subspace bound."""
+    monkeypatch.setenv("NH_QRCP", "exact")
+    C = make_matrix(r, w, kind, r + w)
+    eps = 1e-10
+    P, sig = nh.la_tsvd(torch.from_numpy(C).cuda(), eps)
+    P = P.cpu().numpy()
+    s_ref = np.linalg.svd(C, compute_uv=False)
+    k = P.shape[1]
+    assert abs(k - int(np.sum(s_ref > eps * s_ref[0]))) <= 1
+    assert np.max(np.abs(np.array(sig[:k]) - s_ref[:k])) < 1e-12 * s_ref[0]
+    assert np.max(np.abs(P.conj().T @ P - np.eye(k))) < 1e-12
+    assert np.linalg.norm(C - P @ (P.conj().T @ C), 2) <= 2 * eps * s_ref[0] + 1e-13 * s_ref[0]
 
 
 @pytest.mark.parametrize("jacobi", ["block", "block_cuda_cores", "scalar"])
