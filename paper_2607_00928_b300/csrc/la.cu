@@ -1781,36 +1781,44 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
 //  1. Gram G = X_P^* X_P, X_P = the pair's 64 columns, as the real Gram of the stacked operand
 //     S = [Re X_P, Im X_P]^T (128 x rows): D = S S^T holds Re^T Re, Re^T Im, Im^T Re, Im^T Im, and
 //     G = (Re^T Re + Im^T Im) + i (Re^T Im - Im^T Re).  One M = N = 128 MMA per k = 8 step and split
-//     term: 3 MMAs, against 12 of M = N = 64 for the complex form, at the full-width tensor rate.
-//     Chunks of 64 rows are split into TF32 hi/lo planes in shared memory (two buffers; loads run
-//     two chunks ahead in registers).  Each chunk accumulates in one of two tensor-memory
-//     accumulators; the previous chunk's is added (FP32, round to nearest) into two partial Grams in
-//     shared memory -- every warp owns one quarter of D and one real component of one partial, so
-//     the adds need no ordering -- and no tensor-core accumulation runs longer than 64 rows.
+//     term: 3 MMAs, against 12 of M = N = 64 for the complex form.  Chunks of 64 rows are split into
+//     TF32 hi/lo planes in shared memory (two buffers; loads run two chunks ahead in registers).
+//     Groups of four chunks (256 rows) accumulate in one of two tensor-memory accumulators; a
+//     finished group is added (FP32, round to nearest) into four real quarter Grams in shared memory,
+//     one per warp pair, while the next group's MMAs run, so no tensor-core accumulation runs longer
+//     than 256 rows (its truncation stays near 1e-6 relative).
 //  2. The largest cosine and the two-sided Jacobi on G -> V, exactly as in k_jacobi_blk.
-//  3. X_P <- X_P V over chunks of 64 rows: A = the chunk (complex planes, double-buffered), B = the
-//     planes of V^T, 12 MMAs of M = N = 64 per k = 8 step into one of two accumulators; the
-//     previous chunk's product is written back in place while the next chunk's MMAs run.
+//  3. X_P <- X_P V over chunks of 128 rows: A = the chunk (complex planes), B = the planes of V^T,
+//     12 MMAs of M = 128, N = 64 per k = 8 step into one of two accumulators; the previous chunk's
+//     product is written back while the current chunk's MMAs run.
 // Every wait is bounded: one that runs out sets g_jac_error, and the CTA leaves X untouched.
 namespace {
-constexpr int JT_W = 64, JT_CH = 64;             // pair width, rows per chunk
-constexpr uint32_t JT_SBO = (JT_CH / 4) * 128;   // 8-row group stride of a 64-deep K-major plane
-constexpr int JT_PLANE = JT_W * JT_CH * 4;       // 16 KB: one real plane of a 64 x 64 operand
-constexpr int JT_REGION = 4 * JT_PLANE;          // 64 KB: re hi, re lo, im hi, im lo (or hi, lo of 128 rows)
+constexpr int JT_W = 64;                          // pair width
+constexpr int JT_CH = 64;                         // Gram: rows per chunk
+constexpr int JT_GRP = 4;                         // Gram: chunks per tensor-memory accumulation
+constexpr int JT_CU = 128;                        // update: rows per chunk
+constexpr uint32_t JT_SBO = 16 * 128;             // 8-row group stride of a 64-deep K-major plane
+constexpr int JT_P64 = 64 * 64 * 4;               // one real plane, 64 rows x 64 deep (16 KB)
+constexpr int JT_P128 = 128 * 64 * 4;             // one real plane, 128 rows x 64 deep (32 KB)
+constexpr int JT_REGION = 4 * JT_P64;             // 64 KB
 constexpr int JT_LDG = JT_W + 1;
-constexpr size_t JT_PART = (size_t)JT_W * JT_LDG * sizeof(float2);
-constexpr size_t JT_SMEM = 2 * (size_t)JT_REGION + 2 * JT_PART + 1024;
+constexpr int JT_LDQ = JT_W + 1;                  // quarter Grams: 64 x 65 floats
+constexpr size_t JT_QUART = 4 * (size_t)JT_W * JT_LDQ * sizeof(float);
+constexpr size_t JT_SMEM = 2 * (size_t)JT_REGION + JT_QUART + 1024;
+static_assert(JT_QUART >= (size_t)4 * JT_P64, "the B planes of the update live in the quarter region");
+static_assert((size_t)2 * JT_W * JT_LDG * sizeof(float2) <= (size_t)2 * JT_REGION, "G and V fit in regions 0-1");
 }  // namespace
 
 __device__ int g_jac_error;
 
-// the 12 MMAs of one k = 8 step of a complex product D = A B^T given as TF32 planes
-__device__ __forceinline__ void jt_mma12(uint32_t dr, uint32_t di, uint32_t a, uint32_t b, uint32_t ko, uint32_t f) {
-  const uint32_t idp = tc_idesc(64, 64, false), idn = tc_idesc(64, 64, true);
-  const uint64_t arh = tc_desc(a + ko, JT_SBO), arl = tc_desc(a + JT_PLANE + ko, JT_SBO),
-                 aih = tc_desc(a + 2 * JT_PLANE + ko, JT_SBO), ail = tc_desc(a + 3 * JT_PLANE + ko, JT_SBO);
-  const uint64_t brh = tc_desc(b + ko, JT_SBO), brl = tc_desc(b + JT_PLANE + ko, JT_SBO),
-                 bih = tc_desc(b + 2 * JT_PLANE + ko, JT_SBO), bil = tc_desc(b + 3 * JT_PLANE + ko, JT_SBO);
+// the 12 MMAs of one k = 8 step of a complex product D = A B^T given as TF32 planes (A: m rows,
+// planes pa bytes apart; B: 64 rows, planes JT_P64 apart)
+__device__ __forceinline__ void jt_mma12(uint32_t dr, uint32_t di, uint32_t a, uint32_t pa, uint32_t b, uint32_t ko,
+                                         uint32_t f, uint32_t idp, uint32_t idn) {
+  const uint64_t arh = tc_desc(a + ko, JT_SBO), arl = tc_desc(a + pa + ko, JT_SBO),
+                 aih = tc_desc(a + 2 * pa + ko, JT_SBO), ail = tc_desc(a + 3 * pa + ko, JT_SBO);
+  const uint64_t brh = tc_desc(b + ko, JT_SBO), brl = tc_desc(b + JT_P64 + ko, JT_SBO),
+                 bih = tc_desc(b + 2 * JT_P64 + ko, JT_SBO), bil = tc_desc(b + 3 * JT_P64 + ko, JT_SBO);
   // D = A B: Dr = Ar Br - Ai Bi, Di = Ar Bi + Ai Br
   tc_mma(dr, arh, brh, idp, f); tc_mma(dr, arh, brl, idp, 1u); tc_mma(dr, arl, brh, idp, 1u);
   tc_mma(dr, aih, bih, idn, 1u); tc_mma(dr, aih, bil, idn, 1u); tc_mma(dr, ail, bih, idn, 1u);
@@ -1818,9 +1826,9 @@ __device__ __forceinline__ void jt_mma12(uint32_t dr, uint32_t di, uint32_t a, u
   tc_mma(di, aih, brh, idp, 1u); tc_mma(di, aih, brl, idp, 1u); tc_mma(di, ail, brh, idp, 1u);
 }
 
-// four consecutive values along k of one complex operand row, split into the four planes at byte
-// offset off
-__device__ __forceinline__ void jt_store4(unsigned char* buf, uint32_t off, const float2 (&v)[4]) {
+// four consecutive values along k of one complex operand row, split into the four planes (pl
+// bytes apart) at byte offset off
+__device__ __forceinline__ void jt_store4(unsigned char* buf, uint32_t pl, uint32_t off, const float2 (&v)[4]) {
   uint32_t p[4][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -1829,7 +1837,7 @@ __device__ __forceinline__ void jt_store4(unsigned char* buf, uint32_t off, cons
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    *reinterpret_cast<uint4*>(buf + q * JT_PLANE + off) = make_uint4(p[q][0], p[q][1], p[q][2], p[q][3]);
+    *reinterpret_cast<uint4*>(buf + q * pl + off) = make_uint4(p[q][0], p[q][1], p[q][2], p[q][3]);
 }
 
 __global__ void __launch_bounds__(256, 1)
@@ -1842,12 +1850,13 @@ __global__ void __launch_bounds__(256, 1)
   extern __shared__ unsigned char jt_raw[];
   const uint32_t raw_s = tc_smem_u32(jt_raw);
   unsigned char* sm = jt_raw + (((raw_s + 1023u) & ~1023u) - raw_s);
-  // shared memory: regions 0 and 1 (64 KB each), then two 64 x 65 complex arrays.  Gram: the two
-  // chunk buffers and the two partial Grams (G, P2).  Jacobi: G and V.  Update: B = V^T planes in
-  // region 0, A chunk buffers in region 1 and over G/V.
+  // shared memory: regions 0 and 1 (64 KB each), then the quarter region.  Gram: chunk plane
+  // buffers in regions 0/1, quarter Grams after them.  Jacobi: G and V in regions 0-1.  Update: B =
+  // V^T planes in the quarter region, the 128-row A chunk over regions 0-1.
   unsigned char* reg0 = sm;
   unsigned char* reg1 = sm + JT_REGION;
-  float2* G = reinterpret_cast<float2*>(sm + 2 * JT_REGION);   // G[i * LDG + j] = x_i^* x_j
+  float* Qg = reinterpret_cast<float*>(sm + 2 * JT_REGION);   // quarters q: Qg[q * 64 * LDQ + i * LDQ + j]
+  float2* G = reinterpret_cast<float2*>(sm);                   // G[i * LDG + j] = x_i^* x_j
   float2* V = G + W * LDG;
   __shared__ int cidx[W];
   __shared__ float rc[W / 2];
@@ -1871,13 +1880,14 @@ __global__ void __launch_bounds__(256, 1)
     fail = 0;
     skip = 0;
   }
-  for (int e = tid; e < 2 * W * LDG; e += 256) G[e] = make_float2(0.f, 0.f);   // G and P2 (= V)
+  for (int e = tid; e < 4 * W * JT_LDQ; e += 256) Qg[e] = 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
   const float floor2 = negl2 * (*d.amax);
   const int nch = (d.r + JT_CH - 1) / JT_CH;
+  const int ngr = (nch + JT_GRP - 1) / JT_GRP;
 
   // ---- 1. Gram.  Unit e = tid + 256 q: column c = 8 (e >> 7) + (e & 7), chunk rows 4 kq .. 4 kq + 3
   //      with kq = (e >> 3) & 15 -- eight lanes fill one 8-row x 16-byte core matrix, so a warp's
@@ -1906,78 +1916,87 @@ __global__ void __launch_bounds__(256, 1)
         }
         const uint32_t ore = tc_kmajor(c, 4 * kq, JT_SBO), oim = tc_kmajor(64 + c, 4 * kq, JT_SBO);
         *reinterpret_cast<uint4*>(b + ore) = make_uint4(h[0][0], h[0][1], h[0][2], h[0][3]);
-        *reinterpret_cast<uint4*>(b + 2 * JT_PLANE + ore) = make_uint4(l[0][0], l[0][1], l[0][2], l[0][3]);
+        *reinterpret_cast<uint4*>(b + JT_P128 + ore) = make_uint4(l[0][0], l[0][1], l[0][2], l[0][3]);
         *reinterpret_cast<uint4*>(b + oim) = make_uint4(h[1][0], h[1][1], h[1][2], h[1][3]);
-        *reinterpret_cast<uint4*>(b + 2 * JT_PLANE + oim) = make_uint4(l[1][0], l[1][1], l[1][2], l[1][3]);
+        *reinterpret_cast<uint4*>(b + JT_P128 + oim) = make_uint4(l[1][0], l[1][1], l[1][2], l[1][3]);
       }
     };
-    // hi plane of the 128 stacked rows at +0, lo plane at +2 JT_PLANE (32 KB each)
+    // chunk t accumulates into group (t / JT_GRP)'s accumulator; the group's last chunk commits
     auto mma_g = [&](unsigned char* b, int t) {
       if (tid == 0 && !fail) {
         tc_fence_after();
-        const uint32_t hi = tc_smem_u32(b), lo = hi + 2 * JT_PLANE, dd = tmem + (uint32_t)(t & 1) * 128;
+        const int g = t / JT_GRP;
+        const bool first = t % JT_GRP == 0;
+        const uint32_t hi = tc_smem_u32(b), lo = hi + JT_P128, dd = tmem + (uint32_t)(g & 1) * 128;
         const uint32_t id = tc_idesc(128, 128, false);
 #pragma unroll
         for (int ks = 0; ks < JT_CH / 8; ++ks) {
           const uint64_t h = tc_desc(hi + (uint32_t)ks * 256, JT_SBO), l = tc_desc(lo + (uint32_t)ks * 256, JT_SBO);
-          tc_mma(dd, h, h, id, ks == 0 ? 0u : 1u);
+          tc_mma(dd, h, h, id, (first && ks == 0) ? 0u : 1u);
           tc_mma(dd, h, l, id, 1u);
           tc_mma(dd, l, h, id, 1u);
         }
+        // the buffer is free again once these MMAs are done; the group is done after its last chunk
         tc_commit(&mbar[t & 1]);
       }
     };
-    // warp (quad, h = warp >> 2) adds rows 32 quad .. + 31, columns 64 h .. + 63 of chunk u's D:
-    // quad < 2: Re^T Re -> G.x (h = 0), Re^T Im -> G.y (h = 1); quad >= 2: Im^T Re -> P2.y (h = 0),
-    // Im^T Im -> P2.x (h = 1).  Afterwards G += conj-combined P2.
-    auto drain_g = [&](int u) {
-      if (!fail && !tc_wait(&mbar[u & 1], (uint32_t)((u >> 1) & 1))) atomicExch(&fail, 1);
+    // warp (quad, h = warp >> 2) adds rows 32 quad .. + 31, columns 64 h .. + 63 of group g's D
+    // into quarter 2 (quad >= 2) + h: Re^T Re, Re^T Im, Im^T Re, Im^T Im (rows i = s mod 64)
+    auto drain_g = [&](int g) {
       tc_fence_after();
       const int h = warp >> 2, i = (32 * quad + lane) & 63;
-      const bool re = (quad < 2) == (h == 0);
-      // this warp's real component of row i (4-byte accesses: the other component belongs to
-      // another warp)
-      float* dst = reinterpret_cast<float*>((quad < 2 ? G : V) + i * LDG) + (re ? 0 : 1);
-      const uint32_t base = tmem + (uint32_t)(u & 1) * 128 + (uint32_t)(64 * h) + ((uint32_t)(32 * quad) << 16);
+      float* dst = Qg + ((quad >= 2 ? 2 : 0) + h) * W * JT_LDQ + i * JT_LDQ;
+      const uint32_t base = tmem + (uint32_t)(g & 1) * 128 + (uint32_t)(64 * h) + ((uint32_t)(32 * quad) << 16);
       for (int c0 = 0; c0 < W; c0 += 16) {
         uint32_t v[16];
         tc_ld16(base + (uint32_t)c0, v);
         tc_wait_ld();
         if (!fail) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) dst[2 * (c0 + j)] += __uint_as_float(v[j]);
+          for (int j = 0; j < 16; ++j) dst[c0 + j] += __uint_as_float(v[j]);
         }
       }
       tc_fence_before();
     };
+    // Before storing chunk t into buffer t & 1, the MMAs of chunk t - 2 (its last reader) must be
+    // done: wait for the (t - 2)-th completion of that buffer's barrier.  When chunk t - 1 closed
+    // a group, that group is drained here, while chunk t's MMAs run.
     auto step_g = [&](int t, float2 (&pf)[4][4]) {
+      if (t >= 2 && !fail && !tc_wait(&mbar[t & 1], (uint32_t)(((t - 2) >> 1) & 1))) atomicExch(&fail, 1);
       if (t < nch) {
-        unsigned char* b = (t & 1) ? reg1 : reg0;   // last read by chunk t - 2, drained before
+        unsigned char* b = (t & 1) ? reg1 : reg0;
         store_g(b, pf);
         if (t + 2 < nch) load_g(t + 2, pf);
         tc_fence_async_smem();
-        __syncthreads();
-        mma_g(b, t);
       }
-      if (t >= 1) drain_g(t - 1);
+      __syncthreads();
+      if (t < nch) mma_g((t & 1) ? reg1 : reg0, t);
+      if (t >= 1 && ((t - 1) % JT_GRP == JT_GRP - 1 || t - 1 == nch - 1)) {
+        // group (t - 1) / JT_GRP is complete once chunk t - 1's MMAs are
+        const int u = t - 1;
+        if (!fail && !tc_wait(&mbar[u & 1], (uint32_t)((u >> 1) & 1))) atomicExch(&fail, 1);
+        drain_g(u / JT_GRP);
+      }
       __syncthreads();
     };
     load_g(0, pa);
     if (nch > 1) load_g(1, pb);
+    // chunk t's barrier parity: completion number t >> 1 of barrier t & 1.  A wait at step t for
+    // chunk t - 2 and at step t + 1 for chunk t are both satisfied by the same completion count,
+    // so barrier phases only ever advance.
     for (int t = 0; t <= nch; t += 2) {
       step_g(t, pa);
       if (t + 1 <= nch) step_g(t + 1, pb);
     }
-    // G = (Re^T Re + Im^T Im) + i (Re^T Im - Im^T Re)
-    for (int e = tid; e < W * W; e += 256) {
-      const int i = e / W, j = e - i * W;
-      const float2 p = V[i * LDG + j];
-      G[i * LDG + j].x += p.x;
-      G[i * LDG + j].y -= p.y;
-    }
-    __syncthreads();
+    (void)ngr;
   }
   if (fail) goto cleanup;
+  // G = (Re^T Re + Im^T Im) + i (Re^T Im - Im^T Re), in regions 0-1 (the plane buffers are done)
+  for (int e = tid; e < W * W; e += 256) {
+    const int i = e / W, j = e - i * W, o = i * JT_LDQ + j;
+    G[i * LDG + j] = make_float2(Qg[o] + Qg[3 * W * JT_LDQ + o], Qg[W * JT_LDQ + o] - Qg[2 * W * JT_LDQ + o]);
+  }
+  __syncthreads();
   // ---- 2. largest cosine of the fresh Gram (columns above the noise floor only)
   {
     const int ti = tid >> 4, tj = tid & 15;
@@ -2008,23 +2027,24 @@ __global__ void __launch_bounds__(256, 1)
   }
   // ---- 3. two-sided Jacobi on G, V <- V J for every rotation J
   jac_inner<float, W>(G, V, LDG, floor2, tol, max_inner, rc, rse, ract, rpa, rpb, &any_s);
-  // ---- 4. X_P <- X_P V.  B = V^T planes in region 0: B(n, k) = V(k, n)
-  for (int e = tid; e < W * (W / 4); e += 256) {
-    const int n = e >> 4, kq = e & 15;
-    float2 v4[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v4[i] = V[(4 * kq + i) * LDG + n];
-    jt_store4(reg0, tc_kmajor(n, 4 * kq, JT_SBO), v4);
-  }
-  __syncthreads();   // V is read: its region now takes the second A buffer
+  // ---- 4. X_P <- X_P V.  B = V^T planes in the quarter region: B(n, k) = V(k, n)
   {
-    unsigned char* abuf[2] = {reg1, sm + 2 * JT_REGION};
-    float2 pa[4][4], pb[4][4];
-    // A: unit e = tid + 256 q stages row m = e % 64 of the chunk, columns 4 (e / 64) .. + 3
-    auto load_u = [&](int t, float2 (&pf)[4][4]) {
+    unsigned char* bpl = sm + 2 * JT_REGION;
+    for (int e = tid; e < W * (W / 4); e += 256) {
+      const int n = e >> 4, kq = e & 15;
+      float2 v4[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = tid + 256 * q, m = e & 63, cq = e >> 6, row = t * JT_CH + m;
+      for (int i = 0; i < 4; ++i) v4[i] = V[(4 * kq + i) * LDG + n];
+      jt_store4(bpl, JT_P64, tc_kmajor(n, 4 * kq, JT_SBO), v4);
+    }
+    __syncthreads();   // V is read: regions 0-1 now take the A chunk
+    const int ncu = (d.r + JT_CU - 1) / JT_CU;
+    float2 pf[8][4];
+    // A: unit e = tid + 256 q stages row m = e % 128 of the chunk, columns 4 (e / 128) .. + 3
+    auto load_u = [&](int t) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = tid + 256 * q, m = e & 127, cq = e >> 7, row = t * JT_CU + m;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int col = cidx[4 * cq + i];
@@ -2032,36 +2052,29 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
     };
-    auto store_u = [&](unsigned char* b, const float2 (&pf)[4][4]) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = tid + 256 * q;
-        jt_store4(b, tc_kmajor(e & 63, 4 * (e >> 6), JT_SBO), pf[q]);
-      }
-    };
-    auto mma_u = [&](unsigned char* b, int t) {
+    auto mma_u = [&](int t) {
       if (tid == 0 && !fail) {
         tc_fence_after();
-        const uint32_t a = tc_smem_u32(b), bb = tc_smem_u32(reg0), dd = tmem + (uint32_t)(t & 1) * 128;
+        const uint32_t a = tc_smem_u32(sm), bb = tc_smem_u32(bpl), dd = tmem + (uint32_t)(t & 1) * 128;
+        const uint32_t idp = tc_idesc(128, 64, false), idn = tc_idesc(128, 64, true);
 #pragma unroll
-        for (int ks = 0; ks < W / 8; ++ks) jt_mma12(dd, dd + 64, a, bb, (uint32_t)ks * 256, ks == 0 ? 0u : 1u);
+        for (int ks = 0; ks < W / 8; ++ks)
+          jt_mma12(dd, dd + 64, a, JT_P128, bb, (uint32_t)ks * 256, ks == 0 ? 0u : 1u, idp, idn);
         tc_commit(&mbar[2 + (t & 1)]);
       }
     };
-    // warps 0-3 write output columns 0-31, warps 4-7 columns 32-63; lanes 0-15 of quadrant q own
-    // rows 16 q + lane of the chunk (M = 64 accumulator layout)
+    // warp (quad, h = warp >> 2): rows 32 quad + lane of chunk u, output columns 32 h .. + 31
     auto drain_u = [&](int u) {
       if (!fail && !tc_wait(&mbar[2 + (u & 1)], (uint32_t)((u >> 1) & 1))) atomicExch(&fail, 1);
       tc_fence_after();
-      const int n0 = warp < 4 ? 0 : 32;
+      const int n0 = 32 * (warp >> 2), row = u * JT_CU + 32 * quad + lane;
       for (int c0 = 0; c0 < 32; c0 += 16) {
         uint32_t vr[16], vi[16];
         const uint32_t la = tmem + (uint32_t)(u & 1) * 128 + ((uint32_t)(32 * quad) << 16) + (uint32_t)(n0 + c0);
         tc_ld16(la, vr);
         tc_ld16(la + 64, vi);
         tc_wait_ld();
-        const int row = u * JT_CH + 16 * quad + lane;
-        if (lane < 16 && row < d.r && !fail) {
+        if (row < d.r && !fail) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int col = cidx[n0 + c0 + j];
@@ -2071,24 +2084,23 @@ __global__ void __launch_bounds__(256, 1)
       }
       tc_fence_before();
     };
-    // chunk t + 2 is loaded while chunk t - 1 is written back: disjoint rows
-    auto step_u = [&](int t, float2 (&pf)[4][4]) {
-      if (t < nch) {
-        unsigned char* b = abuf[t & 1];   // last read by chunk t - 2's MMAs, drained before
-        store_u(b, pf);
-        if (t + 2 < nch) load_u(t + 2, pf);
+    load_u(0);
+    for (int t = 0; t <= ncu; ++t) {
+      if (t < ncu) {
+        // the single A buffer: chunk t - 1's MMAs must be done before it is overwritten
+        if (t >= 1 && !fail && !tc_wait(&mbar[2 + ((t - 1) & 1)], (uint32_t)(((t - 1) >> 1) & 1))) atomicExch(&fail, 1);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = tid + 256 * q;
+          jt_store4(sm, JT_P128, tc_kmajor(e & 127, 4 * (e >> 7), JT_SBO), pf[q]);
+        }
+        if (t + 1 < ncu) load_u(t + 1);   // rows of the next chunk: disjoint from the ones written below
         tc_fence_async_smem();
-        __syncthreads();
-        mma_u(b, t);
       }
-      if (t >= 1) drain_u(t - 1);
       __syncthreads();
-    };
-    load_u(0, pa);
-    if (nch > 1) load_u(1, pb);
-    for (int t = 0; t <= nch; t += 2) {
-      step_u(t, pa);
-      if (t + 1 <= nch) step_u(t + 1, pb);
+      if (t < ncu) mma_u(t);
+      if (t >= 1) drain_u(t - 1);   // overlaps chunk t's MMAs (the other accumulator)
+      __syncthreads();
     }
   }
   if (tid == 0 && !fail) atomicAdd(rows_updated, (unsigned long long)d.r);
