@@ -699,157 +699,63 @@ template <typename R> __device__ R block_sum(R v, R* sh) {
   return r;
 }
 
-// Factor panel columns [j0, j0+b) of every matrix; one CTA (256 threads) per matrix.
-// Reflector H = I - tau v v^*, v[0] = 1, tau = 2 / ||v||^2 real (Hermitian, unitary);
-// v = x + phase(x0) ||x|| e1 so H x = -phase(x0) ||x|| e1.  A zero column gets v = e1,
-// tau = 2.  The panel's compact-WY T (Q_p = I - V_p T V_p^*) is written to Tp.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qr_panel(const QRD<R>* __restrict__ ds, int j0, int nb) {
-  const QRD<R> q = ds[blockIdx.x];
-  const int k = min(q.m, q.n);
-  if (j0 >= k) return;
-  const int b = min(nb, k - j0);
-  __shared__ R red[32];
-  __shared__ cplx<R> sv0;
-  __shared__ R stau;
-  __shared__ cplx<R> Ts[32][33];
-  __shared__ cplx<R> Ys[32][33];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int jj = 0; jj < b; ++jj) {
-    const int col = j0 + jj;
-    cplx<R>* x = q.A + (size_t)col * q.lda;
-    R s = 0;
-    for (int i = col + tid; i < q.m; i += 256) s += abs2(x[i]);
-    const R nrm2 = block_sum<R>(s, red);
-    if (tid == 0) {
-      const cplx<R> a0 = x[col];
-      const R nrm = sqrt(nrm2);
-      const R aa = sqrt(abs2(a0));
-      cplx<R> ph = aa > R(0) ? mkc(a0.x / aa, a0.y / aa) : mkc(R(1), R(0));
-      if (nrm == R(0)) {
-        sv0 = mkc(R(0), R(0));
-        stau = R(2);
-        x[col] = mkc(R(0), R(0));
-      } else {
-        const cplx<R> v0 = a0 + nrm * ph;           // = ph * (aa + nrm)
-        sv0 = v0;
-        const R v0a2 = abs2(v0);
-        const R vn2 = R(1) + (nrm2 - aa * aa) / v0a2;
-        stau = R(2) / vn2;
-        x[col] = mkc(-nrm * ph.x, -nrm * ph.y);
-      }
-      q.tau[col] = stau;
-      q.V[(size_t)col + (size_t)col * q.ldv] = mkc(R(1), R(0));
-    }
-    __syncthreads();
-    const cplx<R> v0 = sv0;
-    const R v0a2 = abs2(v0);
-    cplx<R>* vcol = q.V + (size_t)col * q.ldv;
-    for (int i = col + 1 + tid; i < q.m; i += 256) {
-      cplx<R> xv = x[i];
-      cplx<R> v = (v0a2 > R(0)) ? mkc((xv.x * v0.x + xv.y * v0.y) / v0a2, (xv.y * v0.x - xv.x * v0.y) / v0a2)
-                                : mkc(R(0), R(0));
-      vcol[i] = v;
-      x[i] = mkc(R(0), R(0));
-    }
-    __syncthreads();
-    const R tau = stau;
-    // apply H to the remaining panel columns: one warp per column
-    for (int c = col + 1 + warp; c < j0 + b; c += 8) {
-      cplx<R>* y = q.A + (size_t)c * q.lda;
-      cplx<R> w = czero<R>();
-      for (int i = col + lane; i < q.m; i += 32) cfmac(w, vcol[i], y[i]);
-      w.x = warp_sum(w.x);
-      w.y = warp_sum(w.y);
-      w = tau * w;
-      for (int i = col + lane; i < q.m; i += 32) {
-        cplx<R> v = vcol[i];
-        y[i] = y[i] - v * w;
-      }
-    }
-    __syncthreads();
-  }
-  // Y = V_p^* V_p (strict upper part) over rows [j0, m)
-  for (int p = warp; p < b * b; p += 8) {
-    const int i = p / b, j = p % b;
-    if (i >= j) continue;
-    const cplx<R>* vi = q.V + (size_t)(j0 + i) * q.ldv;
-    const cplx<R>* vj = q.V + (size_t)(j0 + j) * q.ldv;
-    cplx<R> w = czero<R>();
-    for (int r = j0 + j + lane; r < q.m; r += 32) cfmac(w, vi[r], vj[r]);   // v_j zero above j0+j
-    w.x = warp_sum(w.x);
-    w.y = warp_sum(w.y);
-    if (lane == 0) Ys[i][j] = w;
-  }
-  for (int e = tid; e < 32 * 33; e += 256) Ts[e / 33][e % 33] = czero<R>();
-  __syncthreads();
-  // T(j,j) = tau_j ; T(0:j, j) = -tau_j T(0:j,0:j) Y(0:j, j)
-  for (int j = 0; j < b; ++j) {
-    const R tj = q.tau[j0 + j];
-    if (tid < j) {
-      cplx<R> acc = czero<R>();
-      for (int l = tid; l < j; ++l) cfma(acc, Ts[tid][l], Ys[l][j]);
-      Ts[tid][j] = (-tj) * acc;
-    }
-    if (tid == 0) Ts[j][j] = mkc(tj, R(0));
-    __syncthreads();
-  }
-  cplx<R>* Tp = q.Tp + (size_t)(j0 / nb) * nb * nb;
-  for (int e = tid; e < nb * nb; e += 256) {
-    const int i = e % nb, j = e / nb;
-    Tp[e] = (i < b && j < b) ? Ts[i][j] : czero<R>();
-  }
-}
-
-// Cluster-cooperative panel factorization: rows [j0, m) of the panel are split into QCS
-// slabs, one per CTA of the cluster.  Per column: partial norms -> cluster barrier -> every CTA
-// forms the same reflector from the gathered partials (fixed order, so identical) -> partial
-// dots of the remaining panel columns -> cluster barrier -> update own rows.  The compact-WY T
-// of the panel comes from the cluster-reduced Gram V_p^* V_p.
-template <typename R>
-__global__ void __launch_bounds__(256) k_qr_panel_cl(const QRD<R>* __restrict__ ds, int j0, int nb, int qcs) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int crank = (int)cluster.block_rank();
+// Householder panel of 32 columns.  Reflector H = I - tau v v^*, v[0] = 1, tau = 2 / ||v||^2 real
+// (Hermitian, unitary); v = x + phase(x0) ||x|| e1 so H x = -phase(x0) ||x|| e1.  A zero column
+// gets v = e1, tau = 2.  The panel's compact-WY T (Q_p = I - V_p T V_p^*) is written to Tp.
+// Panel factorization, rows [j0, m) split into qcs slabs (one per CTA of a cluster; qcs = 1: one
+// CTA, no cluster).  Per column: partial norms -> barrier -> every CTA forms the same reflector
+// from the gathered partials (fixed order, so identical) -> one pass over its own rows writes the
+// reflector entries and accumulates the partial dots of ALL remaining panel columns at once (each
+// thread owns rows, so the loads of a pass are independent and coalesced along the rows) ->
+// barrier -> a second pass updates the remaining columns and accumulates the next column's norm.
+// The compact-WY T of the panel comes from the reduced Gram V_p^* V_p (staged 32 rows at a time).
+template <typename R, bool CL>
+__global__ void __launch_bounds__(256) k_qr_panel2(const QRD<R>* __restrict__ ds, int j0, int nb, int qcs) {
+  int crank = 0;
+  if constexpr (CL) crank = (int)cg::this_cluster().block_rank();
   const QRD<R> q = ds[blockIdx.x / qcs];
   const int k = min(q.m, q.n);
   if (j0 >= k) return;                       // uniform over the cluster
   const int b = min(nb, k - j0);
-  const int rows = q.m - j0;
-  const int per = (rows + qcs - 1) / qcs;
+  const int rows = q.m - j0, per = (rows + qcs - 1) / qcs;
   const int lo = j0 + crank * per, hi = min(q.m, lo + per);
   __shared__ R pn[2][8];                     // partial norm^2 per warp
-  __shared__ R pd[2][32][2];                 // partial dots per panel column
+  __shared__ cplx<R> pd[2][8][32];           // partial dots per warp and remaining column
+  __shared__ cplx<R> wt[32];
   __shared__ cplx<R> Ts[32][33];
   __shared__ cplx<R> Ys[32][33];
+  cplx<R>(*Vs)[33] = Ts;                     // the Gram's row chunks, before Ts is needed
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // partial norm of the first column
-  auto part_norm = [&](int col, int buf) {
-    R s = 0;
-    for (int i = max(lo, col) + tid; i < hi; i += 256) s += abs2(q.A[(size_t)i + (size_t)col * q.lda]);
-    s = warp_sum(s);
-    if (lane == 0) pn[buf][warp] = s;
+  auto csync = [&]() {
+    if constexpr (CL) cg::this_cluster().sync();
+    else __syncthreads();
   };
-  part_norm(j0, 0);
+  auto rmt = [&](auto* ptr, int r) {
+    if constexpr (CL) return cg::this_cluster().map_shared_rank(ptr, r);
+    else { (void)r; return ptr; }
+  };
+  {
+    const cplx<R>* x = q.A + (size_t)j0 * q.lda;
+    R sn = 0;
+    for (int i = lo + tid; i < hi; i += 256) sn += abs2(x[i]);
+    sn = warp_sum(sn);
+    if (lane == 0) pn[0][warp] = sn;
+  }
   for (int jj = 0; jj < b; ++jj) {
-    const int col = j0 + jj;
-    const int buf = jj & 1;
-    cluster.sync();
-    // gather ||x||^2
+    const int col = j0 + jj, buf = jj & 1, nc = b - jj - 1;
+    csync();
     R nrm2 = 0;
     {
       R v = 0;
-      for (int e = lane; e < qcs * 8; e += 32) {
-        const R* p = cluster.map_shared_rank(&pn[buf][0], e / 8);
-        v += p[e % 8];
-      }
-      nrm2 = warp_sum(v);                    // same value in every warp and CTA
+      for (int e = lane; e < qcs * 8; e += 32) v += rmt(&pn[buf][0], e >> 3)[e & 7];
+      nrm2 = warp_sum(v);                    // the same value in every warp and CTA
     }
     cplx<R>* x = q.A + (size_t)col * q.lda;
-    const cplx<R> a0 = x[col];
+    const cplx<R> a0 = x[col];               // the owner overwrites it only after the next barrier
     const R nrm = sqrt(nrm2);
     const R aa = sqrt(abs2(a0));
     const cplx<R> ph = aa > R(0) ? mkc(a0.x / aa, a0.y / aa) : mkc(R(1), R(0));
-    cplx<R> v0 = mkc(R(0), R(0));
+    cplx<R> v0 = czero<R>();
     R tau = R(2);
     if (nrm > R(0)) {
       v0 = a0 + nrm * ph;
@@ -857,73 +763,103 @@ __global__ void __launch_bounds__(256) k_qr_panel_cl(const QRD<R>* __restrict__ 
     }
     const R v0a2 = abs2(v0);
     cplx<R>* vcol = q.V + (size_t)col * q.ldv;
-    // write own rows of v (row col belongs to the slab containing it)
-    for (int i = max(lo, col) + tid; i < hi; i += 256) {
+    const int r0 = max(lo, col);
+    // pass 1: reflector entries of own rows, partial dots v^* y_c of the nc remaining columns
+    cplx<R> acc[31];
+#pragma unroll
+    for (int c = 0; c < 31; ++c) acc[c] = czero<R>();
+    for (int i = r0 + tid; i < hi; i += 256) {
+      cplx<R> v;
       if (i == col) {
-        vcol[i] = mkc(R(1), R(0));     // x[col] <- R_kk only after the next barrier (others read a0)
-        q.tau[col] = tau;
+        v = mkc(R(1), R(0));
+        vcol[i] = v;
       } else {
         const cplx<R> xv = x[i];
-        vcol[i] = (v0a2 > R(0)) ? mkc((xv.x * v0.x + xv.y * v0.y) / v0a2, (xv.y * v0.x - xv.x * v0.y) / v0a2)
-                                : mkc(R(0), R(0));
-        x[i] = mkc(R(0), R(0));
+        v = (v0a2 > R(0)) ? mkc((xv.x * v0.x + xv.y * v0.y) / v0a2, (xv.y * v0.x - xv.x * v0.y) / v0a2) : czero<R>();
+        vcol[i] = v;
+        x[i] = czero<R>();
       }
+      const cplx<R>* y = x + q.lda + i;
+#pragma unroll
+      for (int c = 0; c < 31; ++c)
+        if (c < nc) cfmac(acc[c], v, y[(size_t)c * q.lda]);
+    }
+#pragma unroll
+    for (int c = 0; c < 31; ++c)
+      if (c < nc) {
+        const R wx = warp_sum(acc[c].x), wy = warp_sum(acc[c].y);
+        if (lane == 0) pd[buf][warp][c] = mkc(wx, wy);
+      }
+    csync();
+    if (tid < nc) {
+      cplx<R> sw = czero<R>();
+      for (int r = 0; r < qcs; ++r) {
+        const cplx<R>* pr = rmt(&pd[buf][0][0], r);
+        for (int w = 0; w < 8; ++w) sw = sw + pr[w * 32 + tid];
+      }
+      wt[tid] = tau * sw;
+    }
+    if (tid == 0 && col >= lo && col < hi) {
+      x[col] = (nrm > R(0)) ? mkc(-nrm * ph.x, -nrm * ph.y) : czero<R>();
+      q.tau[col] = tau;
     }
     __syncthreads();
-    // partial dots w_c = v^* A(:, c) over own rows, one warp per column
-    for (int c = col + 1 + warp; c < j0 + b; c += 8) {
-      const cplx<R>* y = q.A + (size_t)c * q.lda;
-      cplx<R> w = czero<R>();
-      for (int i = max(lo, col) + lane; i < hi; i += 32) cfmac(w, vcol[i], y[i]);
-      w.x = warp_sum(w.x);
-      w.y = warp_sum(w.y);
-      if (lane == 0) { pd[buf][c - j0][0] = w.x; pd[buf][c - j0][1] = w.y; }
+    // pass 2: y_c -= v w_c on own rows; the next column's partial norm (rows > col)
+    R sn = 0;
+    for (int i = r0 + tid; i < hi; i += 256) {
+      const cplx<R> v = (i == col) ? mkc(R(1), R(0)) : vcol[i];
+      cplx<R>* y = x + q.lda + i;
+#pragma unroll
+      for (int c = 0; c < 31; ++c)
+        if (c < nc) {
+          const cplx<R> yn = y[(size_t)c * q.lda] - v * wt[c];
+          y[(size_t)c * q.lda] = yn;
+          if (c == 0 && i > col) sn += abs2(yn);
+        }
     }
-    cluster.sync();
-    if (tid == 0 && col >= lo && col < hi) x[col] = (nrm > R(0)) ? mkc(-nrm * ph.x, -nrm * ph.y) : mkc(R(0), R(0));
-    // gather dots and update own rows; then the partial norm of the next column
-    for (int c = col + 1 + warp; c < j0 + b; c += 8) {
-      R wx = 0, wy = 0;
-      if (lane < qcs) {
-        const R* p = cluster.map_shared_rank(&pd[buf][c - j0][0], lane);
-        wx = p[0];
-        wy = p[1];
-      }
-      wx = warp_sum(wx);
-      wy = warp_sum(wy);
-      const cplx<R> w = mkc(tau * wx, tau * wy);
-      cplx<R>* y = q.A + (size_t)c * q.lda;
-      for (int i = max(lo, col) + lane; i < hi; i += 32) y[i] = y[i] - vcol[i] * w;
+    sn = warp_sum(sn);
+    if (lane == 0) pn[buf ^ 1][warp] = sn;
+  }
+  // Gram Y = V_p^* V_p (strict upper part) over own rows: 32-row chunks staged in shared memory,
+  // each thread accumulating up to two (i, j) pairs
+  const int npair = b * (b - 1) / 2;
+  int pi[2], pj[2];
+  cplx<R> ya[2] = {czero<R>(), czero<R>()};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int p = tid + 256 * h;
+    int j = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+    while (j * (j - 1) / 2 > p) --j;
+    while ((j + 1) * j / 2 <= p) ++j;
+    pj[h] = j;
+    pi[h] = p - j * (j - 1) / 2;
+  }
+  for (int rb = lo; rb < hi; rb += 32) {
+    __syncthreads();
+    for (int e = tid; e < 32 * b; e += 256) {
+      const int r = e & 31, c = e >> 5;
+      Vs[r][c] = (rb + r < hi) ? q.V[(size_t)(rb + r) + (size_t)(j0 + c) * q.ldv] : czero<R>();
     }
     __syncthreads();
-    if (jj + 1 < b) part_norm(col + 1, buf ^ 1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (tid + 256 * h < npair)
+        for (int r = 0; r < 32; ++r) cfmac(ya[h], Vs[r][pi[h]], Vs[r][pj[h]]);
   }
-  // Gram Y = V_p^* V_p over own rows (strict upper part), cluster-reduced
-  for (int p = warp; p < b * b; p += 8) {
-    const int i = p / b, j = p % b;
-    if (i >= j) continue;
-    const cplx<R>* vi = q.V + (size_t)(j0 + i) * q.ldv;
-    const cplx<R>* vj = q.V + (size_t)(j0 + j) * q.ldv;
-    cplx<R> w = czero<R>();
-    for (int r = max(lo, j0 + j) + lane; r < hi; r += 32) cfmac(w, vi[r], vj[r]);
-    w.x = warp_sum(w.x);
-    w.y = warp_sum(w.y);
-    if (lane == 0) Ys[i][j] = w;
-  }
-  cluster.sync();
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (tid + 256 * h < npair) Ys[pi[h]][pj[h]] = ya[h];
+  csync();
   if (crank == 0) {
     for (int e = tid; e < b * b; e += 256) {
       const int i = e / b, j = e % b;
       if (i >= j) continue;
-      cplx<R> acc = czero<R>();
-      for (int rk = 0; rk < qcs; ++rk) {
-        const cplx<R>* p = cluster.map_shared_rank(&Ys[i][j], rk);
-        acc = acc + *p;
-      }
-      Ts[i][j] = acc;       // staged: Gram in the strict upper part of Ts
+      cplx<R> s2 = czero<R>();
+      for (int rk = 0; rk < qcs; ++rk) s2 = s2 + *rmt(&Ys[i][j], rk);
+      Ts[i][j] = s2;       // staged: Gram in the strict upper part of Ts
     }
   }
-  cluster.sync();            // peers may exit only after rank 0 has read their Gram partials
+  csync();                 // peers may exit only after rank 0 has read their Gram partials
   if (crank != 0) return;
   for (int e = tid; e < 32 * 32; e += 256) {
     const int i = e / 32, j = e % 32;
@@ -935,9 +871,9 @@ __global__ void __launch_bounds__(256) k_qr_panel_cl(const QRD<R>* __restrict__ 
   for (int j = 0; j < b; ++j) {
     const R tj = q.tau[j0 + j];
     if (tid < j) {
-      cplx<R> acc = czero<R>();
-      for (int l = tid; l < j; ++l) cfma(acc, Ts[tid][l], Ys[l][j]);
-      Ts[tid][j] = (-tj) * acc;
+      cplx<R> a2 = czero<R>();
+      for (int l = tid; l < j; ++l) cfma(a2, Ts[tid][l], Ys[l][j]);
+      Ts[tid][j] = (-tj) * a2;
     }
     if (tid == 0) Ts[j][j] = mkc(tj, R(0));
     __syncthreads();
@@ -994,11 +930,11 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
   }
   if (kmax == 0) { ar_->release(mk); return out; }
   QRD<R>* dd = upload(d);
-  // rows per CTA ~ 1024: tall panels are shared by a cluster of up to 8 CTAs
+  // rows per CTA ~ 512: tall panels are shared by a cluster of up to 8 CTAs
   int mmax = 0;
   for (auto& q : d) mmax = std::max(mmax, q.m);
   int qcs = 1;
-  while (qcs < 8 && (long long)qcs * 1024 < mmax) qcs *= 2;
+  while (qcs < 8 && (long long)qcs * 512 < mmax) qcs *= 2;
   // Two-level blocking for k > GW: the 32-column panels of one group of GW columns update only
   // the group's own columns; then the group's merged compact-WY factor (T_g from the UT identity,
   // as in group_wy) updates the rest of the matrix with GEMMs of depth GW.  Matrices with k <= GW
@@ -1027,9 +963,9 @@ std::vector<QFac<R>> Ops<R>::qr(const std::vector<Mat<R>>& A, Arena& keep) {
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      NH_CK(cudaLaunchKernelEx(&cfg, k_qr_panel_cl<R>, (const QRD<R>*)dd, j0, (int)NB, qcs));
+      NH_CK(cudaLaunchKernelEx(&cfg, k_qr_panel2<R, true>, (const QRD<R>*)dd, j0, (int)NB, qcs));
     } else {
-      k_qr_panel<R><<<(int)d.size(), 256, 0, st_>>>(dd, j0, NB);
+      k_qr_panel2<R, false><<<(int)d.size(), 256, 0, st_>>>(dd, j0, NB, 1);
       NH_LAUNCH_CK();
     }
     prof.end(st_, K_QR_PANEL, fl, 0);
