@@ -1288,6 +1288,12 @@ __device__ void jac_inner(cplx<R>* G, cplx<R>* V, int ldg, R floor2, R tol, int 
     const int i = e / W, j = e - i * W;
     V[i * ldg + j] = mkc(R(i == j ? 1 : 0), R(0));
   }
+  // exact Hermitian symmetry (the rounds below update one half and mirror it)
+  for (int e = tid; e < W * W; e += 256) {
+    const int i = e / W, j = e - i * W;
+    if (i < j) G[j * ldg + i] = conj(G[i * ldg + j]);
+    else if (i == j) G[i * ldg + i].y = R(0);
+  }
   if (tid == 0) *any_s = 0;
   __syncthreads();
   for (int sw = 0; sw < max_inner; ++sw) {
@@ -1317,9 +1323,13 @@ __device__ void jac_inner(cplx<R>* G, cplx<R>* V, int ldg, R floor2, R tol, int 
         ract[tid] = act;
       }
       __syncthreads();
-      // J of pair P: columns (a, b) -> (c x_a - conj(se) x_b, se x_a + c x_b); identity when inactive
-      for (int e = tid; e < NP * NP; e += 256) {
-        const int P = e / NP, Q = e - P * NP;
+      // J of pair P: columns (a, b) -> (c x_a - conj(se) x_b, se x_a + c x_b); identity when inactive.
+      // Blocks (P, Q) with P <= Q only; block (Q, P) is the conjugate transpose.
+      for (int e = tid; e < NP * (NP + 1) / 2; e += 256) {
+        int Q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (Q * (Q + 1) / 2 > e) --Q;
+        while ((Q + 1) * (Q + 2) / 2 <= e) ++Q;
+        const int P = e - Q * (Q + 1) / 2;
         const int aP = ract[P], aQ = ract[Q];
         if (!aP && !aQ) continue;
         const int ra = pa[P], rb = pb[P], ca = pa[Q], cb = pb[Q];
@@ -1342,6 +1352,12 @@ __device__ void jac_inner(cplx<R>* G, cplx<R>* V, int ldg, R floor2, R tol, int 
         G[ra * ldg + cb] = n01;
         G[rb * ldg + ca] = n10;
         G[rb * ldg + cb] = n11;
+        if (P != Q) {
+          G[ca * ldg + ra] = conj(n00);
+          G[cb * ldg + ra] = conj(n01);
+          G[ca * ldg + rb] = conj(n10);
+          G[cb * ldg + rb] = conj(n11);
+        }
       }
       for (int e = tid; e < W * NP; e += 256) {
         const int i = e / NP, Q = e - i * NP;
