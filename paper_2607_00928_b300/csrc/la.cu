@@ -1236,12 +1236,53 @@ void Ops<R>::trinv(const std::vector<Mat<R>>& A, const std::vector<Mat<R>>& X) {
 // columns are split into blocks of 16; each launch is one round of a round-robin
 // tournament over blocks; a CTA takes one block pair and sweeps all 32-choose-2 column
 // pairs of it (16 warps, one column pair per warp per inner round).
+// A pair found orthogonal is recorded with the versions of its two blocks and the noise floor of
+// that visit; while neither block has been rotated since and the floor has not come down, the pair
+// is still orthogonal and later visits skip it without forming its Gram.
+struct JacSeen { unsigned va, vb; double floor2; };
+
 template <typename R> struct JacD {
   cplx<R>* X; int ld, r, k, nblk;   // nblk even
   unsigned* off;                    // max |gamma|/sqrt(alpha beta) of this sweep (float bits)
   const int* done;                  // converged flag from the previous sweep
   R* amax;                          // max squared column norm at the start of the sweep
+  unsigned* ver;                    // per 32-column block: how many blocked steps rotated it (blocked kernels)
+  JacSeen* seen;                    // per block pair (I < J): the record of its last orthogonal visit
 };
+
+// the pair's record, or nullptr when the kernel keeps none
+template <typename R> __device__ __forceinline__ JacSeen* jac_seen(const JacD<R>& d, int I, int J) {
+  if (!d.seen) return nullptr;
+  const int a = min(I, J), b = max(I, J);
+  return d.seen + (size_t)a * d.nblk + b;
+}
+// true when the pair is known to be orthogonal (uniform: thread 0 decides, one barrier)
+template <typename R>
+__device__ __forceinline__ bool jac_known_orthogonal(const JacD<R>& d, int I, int J, double floor2, int* flag) {
+  if (threadIdx.x == 0) {
+    int k = 0;
+    if (const JacSeen* sp = jac_seen(d, I, J)) {
+      const JacSeen sn = *sp;
+      const int a = min(I, J), b = max(I, J);
+      k = sn.va == d.ver[a] && sn.vb == d.ver[b] && floor2 >= sn.floor2;
+    }
+    *flag = k;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+template <typename R> __device__ __forceinline__ void jac_mark_orthogonal(const JacD<R>& d, int I, int J, double floor2) {
+  if (JacSeen* sp = jac_seen(d, I, J)) {
+    const int a = min(I, J), b = max(I, J);
+    *sp = JacSeen{d.ver[a], d.ver[b], floor2};
+  }
+}
+template <typename R> __device__ __forceinline__ void jac_mark_rotated(const JacD<R>& d, int I, int J) {
+  if (d.ver) {   // each block is in one pair per round: no other CTA of this launch touches these
+    d.ver[I] += 1u;
+    d.ver[J] += 1u;
+  }
+}
 
 // Largest squared column norm of each matrix (one CTA per matrix): the scale below which a
 // column counts as numerically zero in the Jacobi sweeps.
@@ -1612,7 +1653,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   __shared__ R rc[W / 2];
   __shared__ cplx<R> rse[W / 2];
   __shared__ int ract[W / 2], rpa[W / 2], rpb[W / 2];
-  __shared__ int any_s;
+  __shared__ int any_s, known;
   __shared__ float offw[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int I, J;
@@ -1623,6 +1664,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   }
   __syncthreads();
   const R floor2 = negl2 * (*d.amax);
+  if (jac_known_orthogonal(d, I, J, (double)floor2, &known)) return;
   // ---- 1. Gram: thread (ti, tj) owns G[ti + 16p][tj + 16q], p, q < 4
   const int ti = tid >> 4, tj = tid & 15;
   {
@@ -1682,7 +1724,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
       if (t > 0.f) atomicMax(d.off, __float_as_uint(t));
     }
     __syncthreads();
-    if ((R)offw[0] <= tol_out) return;   // uniform: the pair is already orthogonal
+    if ((R)offw[0] <= tol_out) {         // uniform: the pair is already orthogonal
+      if (tid == 0) jac_mark_orthogonal(d, I, J, (double)floor2);
+      return;
+    }
   }
   // ---- 3. two-sided Jacobi on G, V <- V J for every rotation J
   jac_inner<R, W>(G, V, LDG, floor2, tol, max_inner, rc, rse, ract, rpa, rpb, &any_s);
@@ -1724,7 +1769,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     }
     __syncthreads();
   }
-  if (tid == 0) atomicAdd(rows_updated, (unsigned long long)d.r);
+  if (tid == 0) {
+    atomicAdd(rows_updated, (unsigned long long)d.r);
+    jac_mark_rotated(d, I, J);
+  }
 }
 
 // =============================================================================== blocked Jacobi on tensor cores
@@ -1814,13 +1862,15 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ float rc[W / 2];
   __shared__ float2 rse[W / 2];
   __shared__ int ract[W / 2], rpa[W / 2], rpb[W / 2];
-  __shared__ int any_s, fail, skip;
+  __shared__ int any_s, fail, skip, known;
   __shared__ float offw[8];
   __shared__ uint64_t mbar[5];
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, quad = warp & 3;
   int I, J;
   rr_pair(blockIdx.x, round, d.nblk, I, J);
+  const float floor2 = negl2 * (*d.amax);
+  if (jac_known_orthogonal(d, I, J, (double)floor2, &known)) return;
   if (tid < W) {
     const int c = (tid < 32 ? I : J) * 32 + (tid & 31);
     cidx[tid] = c < d.k ? c : -1;
@@ -1837,7 +1887,6 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  const float floor2 = negl2 * (*d.amax);
   const int nch = (d.r + JT_CH - 1) / JT_CH;
   const int ngr = (nch + JT_GRP - 1) / JT_GRP;
 
@@ -1973,6 +2022,7 @@ __global__ void __launch_bounds__(256, 1)
       for (int w = 0; w < 8; ++w) tt = fmaxf(tt, offw[w]);
       if (tt > 0.f) atomicMax(d.off, __float_as_uint(tt));
       skip = tt <= tol_out;            // the pair is already orthogonal
+      if (skip) jac_mark_orthogonal(d, I, J, (double)floor2);
     }
     __syncthreads();
     if (skip) goto cleanup;
@@ -2055,7 +2105,10 @@ __global__ void __launch_bounds__(256, 1)
       __syncthreads();
     }
   }
-  if (tid == 0 && !fail) atomicAdd(rows_updated, (unsigned long long)d.r);
+  if (tid == 0 && !fail) {
+    atomicAdd(rows_updated, (unsigned long long)d.r);
+    jac_mark_rotated(d, I, J);
+  }
 cleanup:
   if (tid == 0) {
     if (fail) atomicExch(&g_jac_error, 1);
@@ -2307,7 +2360,12 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
     int nb = (p + bw - 1) / bw;
     if (nb < 2) nb = 2;
     if (nb & 1) nb++;
-    jd.push_back({X[i].p, X[i].ld, X[i].m, p, nb, offs + i, done + i, amaxv + i});
+    jd.push_back({X[i].p, X[i].ld, X[i].m, p, nb, offs + i, done + i, amaxv + i, nullptr, nullptr});
+    if (jmode == J_BLOCK) {
+      jd.back().ver = ar_->template arr<unsigned>(nb, true);
+      jd.back().seen = ar_->template arr<JacSeen>((size_t)nb * nb);
+      NH_CK(cudaMemsetAsync(jd.back().seen, 0xFF, (size_t)nb * nb * sizeof(JacSeen), st_));
+    }
     jmap.push_back((int)i);
     maxblk = std::max(maxblk, nb);
   }
