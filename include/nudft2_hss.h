@@ -249,6 +249,12 @@ nudft2_status nudft2_exact_apply(const double* d_x, const double* d_y, int64_t M
  * d_x: M points (device), d_out: M x n complex128 column major (ld M).  Errors: EINVAL. */
 nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, void* stream);
 
+/* nudft2_test_fail_alloc: host-side fault injection for tests (not in the paper).  With k > 0 the
+ * k-th device-memory request of the library's arenas from now on fails with ENOMEM, once, on
+ * whichever thread makes it; k <= 0 disarms.  Exercises the failure paths (status codes, freeing a
+ * handle whose build failed) without touching the GPU. */
+void nudft2_test_fail_alloc(long long k);
+
 /* Building blocks, exposed for unit tests of the batched dense kernels.
  * prec: NUDFT2_FP64 (complex128 buffers) or NUDFT2_MIXED (complex64 buffers).
  *

@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, ci, vp]
     L.nudft2_la_qr_apply.argtypes = [ci, vp, i64, i64, i64, vp, i64, i64, ci, ci, vp]
+    L.nudft2_test_fail_alloc.argtypes = [ctypes.c_longlong]
+    L.nudft2_test_fail_alloc.restype = None
     L.nudft2_la_gemm.argtypes = [ci, ci, ci, i64, i64, i64, ctypes.c_double, vp, i64, i64, vp, i64, i64,
                                  ctypes.c_double, vp, i64, i64, ci, vp]
     L.nudft2_exact_apply.argtypes = [vp, vp, i64, ci, ci, ci, vp, i64, ci, vp, i64, vp]
@@ -97,7 +99,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
               "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_run_batched", "nudft2_hss_plsqr",
-              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_la_gemm", "nudft2_exact_apply",
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_test_fail_alloc", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L

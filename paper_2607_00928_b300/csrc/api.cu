@@ -1150,6 +1150,8 @@ nudft2_status nudft2_la_qr(int prec, void* d_a, int64_t m, int64_t n, int64_t ld
   });
 }
 
+void nudft2_test_fail_alloc(long long k) { fault_alloc_countdown().store(k > 0 ? k : 0); }
+
 nudft2_status nudft2_la_qr_apply(int prec, void* d_a, int64_t m, int64_t n, int64_t lda, void* d_c, int64_t s,
                                  int64_t ldc, int conj, int grouped, void* stream) {
   return guard([&] {

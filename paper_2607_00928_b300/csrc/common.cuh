@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -101,6 +102,19 @@ template <typename R> struct Mat {
   size_t bytes() const { return (size_t)ld * n * sizeof(cplx<R>); }
 };
 
+// ------------------------------------------------------------------ injected allocation failures
+// Host-side fault injection for tests: when armed with k > 0, the k-th device-memory request of the
+// arenas from then on fails with ENOMEM (once), exactly as an exhausted device would report it.
+inline std::atomic<long long>& fault_alloc_countdown() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+inline void fault_alloc_check() {
+  auto& c = fault_alloc_countdown();
+  if (c.load(std::memory_order_relaxed) > 0 && c.fetch_sub(1) == 1)
+    throw Error(ST_ENOMEM, "device allocation failed (injected by nudft2_test_fail_alloc)");
+}
+
 // ------------------------------------------------------------------ stream-ordered arena
 // Large chunks come from cudaMallocAsync on the owning stream; sub-allocations are bump
 // pointers with 256-byte alignment.  mark()/release() give stack-like scratch lifetimes.
@@ -120,6 +134,7 @@ class Arena {
     if (bytes == 0) bytes = 256;
     if (dedicated_ && bytes >= chunk_ / 4) {
       if (frozen_) throw Error(ST_ENOMEM, "arena is frozen during graph capture and has no room left");
+      fault_alloc_check();
       void* p = nullptr;
       NH_CK(cudaMallocAsync(&p, bytes, st_));
       big_.push_back({p, bytes});
@@ -149,6 +164,7 @@ class Arena {
       chunks_.pop_back();
     }
     size_t sz = bytes > chunk_ ? bytes : chunk_;
+    fault_alloc_check();
     void* p = nullptr;
     NH_CK(cudaMallocAsync(&p, sz, st_));
     chunks_.push_back({p, sz, bytes});
