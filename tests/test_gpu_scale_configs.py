@@ -50,6 +50,10 @@ def test_config2_fp64_n128_full_size(nh):
     assert _relcols(c, ct) < 1e-8
     idx = np.random.default_rng(2).choice(w.M, 48, replace=False)
     assert _sampled_residual(x, y, c, f, w.nx, w.ny, idx) < 1e-8
+    # the oracle's own least-squares solution of the noisy data (CGLS with the direct applies, first
+    # column, ~20 s on the host), not only c_true
+    c_ls, _ = orc.cgls(x, y, f[:, 0], w.nx, w.ny, tol=1e-13)
+    assert _relcols(c[:, :1], c_ls[:, None]) < 1e-8
 
 
 def test_config3_mixed_n256_full_size(nh):
