@@ -78,11 +78,11 @@ void Prof::begin(cudaStream_t st) {
   cur_ = get();
   NH_CK(cudaEventRecord(cur_, st));
 }
-void Prof::end(cudaStream_t st, int cls, double flops, double bytes) {
+void Prof::end(cudaStream_t st, int cls, double flops, double bytes, int nlaunch) {
   if (!on || !cur_) return;
   cudaEvent_t b = get();
   NH_CK(cudaEventRecord(b, st));
-  pend_.push_back({cls, cur_, b, flops, bytes});
+  pend_.push_back({cls, cur_, b, flops, bytes, nlaunch});
   cur_ = nullptr;
   if (pend_.size() > 4096) collect();
 }
@@ -94,7 +94,7 @@ void Prof::collect() {
     stats[p.cls].ms += ms;
     stats[p.cls].flops += p.flops;
     stats[p.cls].bytes += p.bytes;
-    stats[p.cls].launches += 1;
+    stats[p.cls].launches += p.n;
     pool_.push_back(p.a);
     pool_.push_back(p.b);
   }
@@ -412,8 +412,9 @@ template <typename R> void Ops<R>::gemm_run(const std::vector<GemmD<R>>& d, int 
       // ordered after it, so the space is handed back at once
       auto mk = ar_->mark();
       prof.begin(st_);
-      count(gemm_tc_run(d, cls, *ar_, st_, &Ops<R>::stage_cb, this));
-      prof.end(st_, K_GEMM_TC, fl, by);
+      const int nl = gemm_tc_run(d, cls, *ar_, st_, &Ops<R>::stage_cb, this);
+      count(nl);
+      prof.end(st_, K_GEMM_TC, fl, by, nl);
       ar_->release(mk);
       return;
     }
@@ -2282,7 +2283,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         }
         count(2);
       }
-      prof.end(st_, K_QRCP, fl, 0);
+      prof.end(st_, K_QRCP, fl, 0, 2 * pmax);
     }
     // 1b. pre-truncation: the pivoted QR reveals the rank, so rows of R with |R_kk| two decades
     //     below the truncation threshold (and the trailing block under them) are dropped before
@@ -2449,7 +2450,7 @@ void Ops<R>::tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep, std
         }
         count();
       }
-      prof.end(st_, jtc ? K_JACOBI_TC : K_JACOBI, fl, 0);
+      prof.end(st_, jtc ? K_JACOBI_TC : K_JACOBI, fl, 0, maxblk - 1);
       NH_CK(cudaMemcpyAsync(hoff.data(), offs, nm * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
       NH_CK(cudaStreamSynchronize(st_));
       bool all = true;

@@ -84,13 +84,14 @@ class Prof {
   ~Prof();
   bool on = false;
   void begin(cudaStream_t st);
-  void end(cudaStream_t st, int cls, double flops, double bytes);
+  // nlaunch: kernel launches inside the region (per-launch averages use it)
+  void end(cudaStream_t st, int cls, double flops, double bytes, int nlaunch = 1);
   void collect();   // synchronises the recorded events and accumulates
   void add_flops(int cls, double f) { if (on) stats[cls].flops += f; }
   KStat stats[K_NCLASS];
 
  private:
-  struct Pend { int cls; cudaEvent_t a, b; double flops, bytes; };
+  struct Pend { int cls; cudaEvent_t a, b; double flops, bytes; int n; };
   cudaEvent_t get();
   std::vector<cudaEvent_t> pool_;
   std::vector<Pend> pend_;

@@ -240,7 +240,7 @@ void Ops<R>::qrcp_sketch(const std::vector<Mat<R>>& A, const std::vector<int*>& 
     k_qs_vmax<R><<<(int)qp.size(), 256, 0, st_>>>(dq, vmax);
     NH_LAUNCH_CK();
     count(2);
-    prof.end(st_, K_QRCP, 0, 0);
+    prof.end(st_, K_QRCP, 0, 0, 2);
     // ---- stopping rule: estimate from the sketch, exact norms when the estimate is close
     NH_CK(cudaMemcpyAsync(hv.data(), vmax, act.size() * sizeof(double), cudaMemcpyDeviceToHost, st_));
     NH_CK(cudaStreamSynchronize(st_));
@@ -301,7 +301,7 @@ void Ops<R>::qrcp_sketch(const std::vector<Mat<R>>& A, const std::vector<int*>& 
     k_qs_scatter<R><<<dim3(QS_LIST, (unsigned)sd.size()), 256, 0, st_>>>(ds);
     NH_LAUNCH_CK();
     count(3);
-    prof.end(st_, K_QRCP, 0, 0);
+    prof.end(st_, K_QRCP, 0, 0, 2 * QS_B + 3);
     // ---- unpivoted panel of the block, then the trailing matrix
     std::vector<Mat<R>> pan, trail;
     std::vector<int> tr_of;
