@@ -15,6 +15,7 @@
 
 #include "../../include/nudft2_hss.h"
 #include "hss.cuh"
+#include "retry.h"
 
 using namespace nh;
 
@@ -1254,42 +1255,26 @@ nudft2_status nudft2_hss_run_batched(int count, const double* const* d_x, const 
   });
   std::vector<nudft2_status> st((size_t)count, NUDFT2_OK);
   std::vector<std::string> msg((size_t)count);
-  std::mutex mu;
-  std::condition_variable cv;
-  int active = 0;
-  long finished = 0;
+  MemoryRetry retry;
   auto r = guard([&] {
     run_pool(count, threads, [&](int k) {
       const int i = order[(size_t)k];
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        active++;
-      }
-      nudft2_status s = NUDFT2_OK;
-      for (;;) {
-        nudft2_hss_t h = nullptr;
-        s = nudft2_hss_build(d_x[i], d_y[i], M[i], nx[i], ny[i], opts ? &opts[i] : nullptr, stream, &h);
-        if (s == NUDFT2_OK) s = nudft2_hss_factor(h, stream);
-        if (s == NUDFT2_OK) s = nudft2_hss_solve(h, d_f[i], ldf[i], nrhs[i], d_c[i], ldc[i], stream);
-        if (s != NUDFT2_OK) msg[(size_t)i] = nudft2_last_error();
-        if (h) nudft2_hss_free(h);
-        if (s != NUDFT2_ENOMEM) break;
-        // out of device memory while other problems hold theirs: wait for one of them to finish,
-        // then start this one again; alone on the device, the failure stands
-        std::unique_lock<std::mutex> lk(mu);
-        if (active <= 1) break;
-        const long seen = finished;
-        active--;
-        cv.wait(lk, [&] { return finished > seen || active == 0; });
-        active++;
-      }
-      st[(size_t)i] = s;
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        active--;
-        finished++;
-      }
-      cv.notify_all();
+      retry.begin();
+      // out of device memory while other problems hold theirs: wait for one of them to finish, then
+      // start this one again (MemoryRetry); every handle of a failed attempt is freed first
+      const int s = retry.run(
+          [&]() -> int {
+            nudft2_hss_t h = nullptr;
+            nudft2_status a = nudft2_hss_build(d_x[i], d_y[i], M[i], nx[i], ny[i], opts ? &opts[i] : nullptr, stream, &h);
+            if (a == NUDFT2_OK) a = nudft2_hss_factor(h, stream);
+            if (a == NUDFT2_OK) a = nudft2_hss_solve(h, d_f[i], ldf[i], nrhs[i], d_c[i], ldc[i], stream);
+            if (a != NUDFT2_OK) msg[(size_t)i] = nudft2_last_error();
+            if (h) nudft2_hss_free(h);
+            return (int)a;
+          },
+          (int)NUDFT2_ENOMEM);
+      st[(size_t)i] = (nudft2_status)s;
+      retry.end();
     });
   });
   if (r != NUDFT2_OK) return r;
