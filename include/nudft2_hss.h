@@ -211,6 +211,20 @@ nudft2_status nudft2_hss_run_batched(int count, const double* const* d_x, const 
 nudft2_status nudft2_hss_plsqr(nudft2_hss_t h, const void* d_f, int64_t ldf, int nrhs, void* d_c, int64_t ldc,
                                double tol, int maxit, int* iters, double* relres, void* stream);
 
+/* Factor store (not in the paper; the reuse of the offline stage across runs, Sec. 4.1).
+ * nudft2_hss_save writes a factored handle to the file `path`: a versioned header (the options, M,
+ * nx, ny, the tree depths), the points, then every HSS generator and URV factor, entries in the
+ * handle's precision (complex128 for FP64, complex64 for MIXED) -- about the handle's device
+ * memory (nudft2_hss_info().device_bytes).  Checkpointed levels are recomputed first.  Errors:
+ * ESTATE (not factored), EINVAL (file cannot be written), ECUDA.
+ * nudft2_hss_load reads such a file into a new factored handle (*out) on which solve, apply, grad
+ * and plsqr give the same results as on the saved one; no construction or factorization runs.
+ * The header and the points are validated on the host before any device work.  Errors: EINVAL (no
+ * such file, not a factor store, another version, truncated or corrupt contents), ENOMEM, ECUDA;
+ * *out is NULL on error. */
+nudft2_status nudft2_hss_save(nudft2_hss_t h, const char* path);
+nudft2_status nudft2_hss_load(const char* path, void* stream, nudft2_hss_t* out);
+
 /* Per-level checkpointing of the URV factors (Sec. 2.3 storage; not in the paper): hand back the
  * device memory of the factors of the top `levels` tree levels and of the root (levels >= L: all
  * of them), keeping the HSS generators and the factors of the levels below.  The next call that

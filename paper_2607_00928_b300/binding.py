@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_la_qr.argtypes = [ci, vp, i64, i64, i64, vp, i64, ci, vp]
     L.nudft2_la_qr_apply.argtypes = [ci, vp, i64, i64, i64, vp, i64, i64, ci, ci, vp]
+    L.nudft2_hss_save.argtypes = [vp, ctypes.c_char_p]
+    L.nudft2_hss_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
     L.nudft2_test_fail_alloc.argtypes = [ctypes.c_longlong]
     L.nudft2_test_fail_alloc.restype = None
     L.nudft2_la_gemm.argtypes = [ci, ci, ci, i64, i64, i64, ctypes.c_double, vp, i64, i64, vp, i64, i64,
@@ -99,7 +101,7 @@ def lib() -> ctypes.CDLL:
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
               "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_run_batched", "nudft2_hss_plsqr",
-              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_test_fail_alloc", "nudft2_la_gemm", "nudft2_exact_apply",
+              "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_test_fail_alloc", "nudft2_hss_save", "nudft2_hss_load", "nudft2_la_gemm", "nudft2_exact_apply",
               "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
@@ -246,6 +248,24 @@ class NudftHSS:
     def factor(self):
         _check(lib().nudft2_hss_factor(self._h, _stream(self.stream)))
         return self
+
+    def save(self, path: str):
+        """Write the factored handle (points, generators, URV factors) to `path` (nudft2_hss_save)."""
+        _check(lib().nudft2_hss_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "NudftHSS":
+        """A factored handle read back from a file written by save() (nudft2_hss_load)."""
+        h = cls.__new__(cls)
+        h._h = ctypes.c_void_p()
+        h.stream = stream
+        _check(lib().nudft2_hss_load(str(path).encode(), _stream(stream), ctypes.byref(h._h)))
+        i = Info()
+        _check(lib().nudft2_hss_info(h._h, ctypes.byref(i)))
+        h.M, h.nx, h.ny = int(i.M), int(i.nx), int(i.ny)
+        h.N = h.nx * h.ny
+        h.x = h.y = None
+        return h
 
     def solve(self, f: torch.Tensor) -> torch.Tensor:
         """c (N, s) = F^{-1} G~_hss^+ f for f (M,) or (M, s); lexicographic ky + kx*ny order."""

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -19,6 +20,8 @@
 
 using namespace nh;
 
+// factor store file: "NUDF" "T2HS" (ASCII, little-endian words), then the version
+constexpr uint32_t STORE_MAGIC0 = 0x4644554Eu, STORE_MAGIC1 = 0x53483254u, STORE_VERSION = 1u;
 thread_local std::string nudft2_err_tls;
 #define g_err nudft2_err_tls
 
@@ -649,6 +652,34 @@ static nudft2_status batch_result(const std::vector<nudft2_status>& st, const st
   return NUDFT2_OK;
 }
 
+// Handle state shared by build and load: stream, arenas, the plan (binning and sorting of the
+// points) and the exact-apply and DFT tables.
+static void init_handle(nudft2_hss_s* h, const double* d_x, const double* d_y, int64_t M, int nx, int ny,
+                        const nudft2_opts& opt, int Lx, int Ly, void* stream) {
+  h->opt = opt;
+  h->M = (int)M; h->nx = nx; h->ny = ny; h->L = std::max(Lx, Ly); h->N = nx * ny;
+  NH_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+  NH_CK(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+  enter(h, stream);
+  h->keep.set_stream(h->st);
+  h->scr.set_stream(h->st);
+  h->ops.reset(new Ops<double>(h->st, &h->scr));
+  make_plan(h->st, h->keep, h->scr, d_x, d_y, (int)M, nx, ny, Lx, Ly, h->pl);
+  h->Ax = h->keep.arr<double2>((size_t)M * nx);
+  h->Ay = h->keep.arr<double2>((size_t)M * ny);
+  twiddle_table(h->st, h->pl.x, (int)M, nx, h->Ax);
+  twiddle_table(h->st, h->pl.y, (int)M, ny, h->Ay);
+  h->Fxi = h->keep.arr<double2>((size_t)nx * nx);
+  h->Fyi = h->keep.arr<double2>((size_t)ny * ny);
+  h->Fxf = h->keep.arr<double2>((size_t)nx * nx);
+  h->Fyf = h->keep.arr<double2>((size_t)ny * ny);
+  dft_matrix<double>(h->st, nx, +1, 1.0 / nx, h->Fxi);
+  dft_matrix<double>(h->st, ny, +1, 1.0 / ny, h->Fyi);
+  dft_matrix<double>(h->st, nx, -1, 1.0, h->Fxf);
+  dft_matrix<double>(h->st, ny, -1, 1.0, h->Fyf);
+  h->ops->count(8);
+}
+
 // ----------------------------------------------------------------------------- C-ABI
 extern "C" {
 
@@ -728,29 +759,8 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
                    ST_EINVAL, "points must be finite and lie in [0,1)^2");
     }
     h = new nudft2_hss_s();
-    h->opt = opt;
-    h->M = (int)M; h->nx = nx; h->ny = ny; h->L = std::max(Lx, Ly); h->N = nx * ny;
-    NH_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
-    NH_CK(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
-    enter(h, stream);
-    h->keep.set_stream(h->st);
-    h->scr.set_stream(h->st);
-    h->ops.reset(new Ops<double>(h->st, &h->scr));
     const double t0 = now_ms();
-    make_plan(h->st, h->keep, h->scr, d_x, d_y, (int)M, nx, ny, Lx, Ly, h->pl);
-    h->Ax = h->keep.arr<double2>((size_t)M * nx);
-    h->Ay = h->keep.arr<double2>((size_t)M * ny);
-    twiddle_table(h->st, h->pl.x, (int)M, nx, h->Ax);
-    twiddle_table(h->st, h->pl.y, (int)M, ny, h->Ay);
-    h->Fxi = h->keep.arr<double2>((size_t)nx * nx);
-    h->Fyi = h->keep.arr<double2>((size_t)ny * ny);
-    h->Fxf = h->keep.arr<double2>((size_t)nx * nx);
-    h->Fyf = h->keep.arr<double2>((size_t)ny * ny);
-    dft_matrix<double>(h->st, nx, +1, 1.0 / nx, h->Fxi);
-    dft_matrix<double>(h->st, ny, +1, 1.0 / ny, h->Fyi);
-    dft_matrix<double>(h->st, nx, -1, 1.0, h->Fxf);
-    dft_matrix<double>(h->st, ny, -1, 1.0, h->Fyf);
-    h->ops->count(8);
+    init_handle(h, d_x, d_y, M, nx, ny, opt, Lx, Ly, stream);
     const bool prof = (opt.flags & NUDFT2_FLAG_PROFILE) != 0;
     h->ops->prof.on = prof;
     if (opt.prec == NUDFT2_FP64) {
@@ -1281,6 +1291,100 @@ nudft2_status nudft2_hss_run_batched(int count, const double* const* d_x, const 
   if (status)
     for (int i = 0; i < count; ++i) status[i] = st[(size_t)i];
   return batch_result(st, msg);
+}
+
+nudft2_status nudft2_hss_save(nudft2_hss_t h, const char* path) {
+  return guard([&] {
+    NH_REQUIRE(h != nullptr && path != nullptr, ST_EINVAL, "save: bad arguments");
+    NH_REQUIRE(h->factored, ST_ESTATE, "save before factor");
+    ensure_factors(h);
+    NH_CK(cudaStreamSynchronize(h->st));
+    std::unique_ptr<FILE, int (*)(FILE*)> f(std::fopen(path, "wb"), &std::fclose);
+    NH_REQUIRE(f != nullptr, ST_EINVAL, "save: cannot open the file");
+    auto wr = [&](const void* p, size_t n) {
+      NH_REQUIRE(n == 0 || std::fwrite(p, 1, n, f.get()) == n, ST_EINVAL, "save: write failed");
+    };
+    const uint32_t head[4] = {STORE_MAGIC0, STORE_MAGIC1, STORE_VERSION, (uint32_t)sizeof(nudft2_opts)};
+    wr(head, sizeof(head));
+    wr(&h->opt, sizeof(nudft2_opts));
+    const int64_t M = h->M;
+    const int32_t dims[4] = {h->nx, h->ny, h->pl.Lx, h->pl.Ly};
+    wr(&M, sizeof(M));
+    wr(dims, sizeof(dims));
+    std::vector<double> hx((size_t)M), hy((size_t)M);
+    NH_CK(cudaMemcpy(hx.data(), h->pl.x, M * sizeof(double), cudaMemcpyDeviceToHost));
+    NH_CK(cudaMemcpy(hy.data(), h->pl.y, M * sizeof(double), cudaMemcpyDeviceToHost));
+    wr(hx.data(), hx.size() * sizeof(double));
+    wr(hy.data(), hy.size() * sizeof(double));
+    if (h->h64) h->h64->save(f.get());
+    else h->h32->save(f.get());
+  });
+}
+
+nudft2_status nudft2_hss_load(const char* path, void* stream, nudft2_hss_t* out) {
+  nudft2_hss_s* h = nullptr;
+  double* dxy = nullptr;
+  auto st = guard([&] {
+    NH_REQUIRE(path != nullptr && out != nullptr, ST_EINVAL, "load: bad arguments");
+    *out = nullptr;
+    std::unique_ptr<FILE, int (*)(FILE*)> f(std::fopen(path, "rb"), &std::fclose);
+    NH_REQUIRE(f != nullptr, ST_EINVAL, "load: cannot open the file");
+    auto rd = [&](void* p, size_t n) {
+      NH_REQUIRE(n == 0 || std::fread(p, 1, n, f.get()) == n, ST_EINVAL, "load: file truncated or corrupt");
+    };
+    // header and points: checked on the host before any device work
+    uint32_t head[4];
+    rd(head, sizeof(head));
+    NH_REQUIRE(head[0] == STORE_MAGIC0 && head[1] == STORE_MAGIC1, ST_EINVAL, "load: not a factor store");
+    NH_REQUIRE(head[2] == STORE_VERSION && head[3] == (uint32_t)sizeof(nudft2_opts), ST_EINVAL,
+               "load: factor store of another version");
+    nudft2_opts opt;
+    rd(&opt, sizeof(opt));
+    int64_t M = 0;
+    int32_t dims[4];
+    rd(&M, sizeof(M));
+    rd(dims, sizeof(dims));
+    const int nx = dims[0], ny = dims[1], Lx = dims[2], Ly = dims[3];
+    NH_REQUIRE(nx >= 1 && ny >= 1 && (int64_t)nx * ny <= (1LL << 26) && M >= (int64_t)nx * ny && M < (1LL << 31),
+               ST_EINVAL, "load: bad problem sizes");
+    NH_REQUIRE(Lx >= 1 && Lx <= 12 && Ly >= 1 && Ly <= 12 && (nx >> Lx) >= 1 && (ny >> Ly) >= 1, ST_EINVAL,
+               "load: bad tree depths");
+    NH_REQUIRE(opt.prec == NUDFT2_FP64 || opt.prec == NUDFT2_MIXED, ST_EINVAL, "load: unknown precision");
+    std::vector<double> hxy((size_t)2 * M);
+    rd(hxy.data(), hxy.size() * sizeof(double));
+    for (double v : hxy)
+      NH_REQUIRE(std::isfinite(v) && v >= 0 && v < 1, ST_EINVAL, "load: points must be finite and lie in [0,1)^2");
+    NH_CK(cudaMalloc(&dxy, hxy.size() * sizeof(double)));
+    NH_CK(cudaMemcpy(dxy, hxy.data(), hxy.size() * sizeof(double), cudaMemcpyHostToDevice));
+    h = new nudft2_hss_s();
+    init_handle(h, dxy, dxy + M, M, nx, ny, opt, Lx, Ly, stream);
+    NH_CK(cudaStreamSynchronize(h->st));
+    if (opt.prec == NUDFT2_FP64) {
+      h->h64.reset(new Hss<double>(h->st, &h->pl));
+      h->h64->load(f.get());
+    } else {
+      h->h32.reset(new Hss<float>(h->st, &h->pl));
+      h->Ax32 = h->keep.arr<float2>((size_t)M * nx);
+      h->Ay32 = h->keep.arr<float2>((size_t)M * ny);
+      convert_gather<double, float>(h->st, h->Ax, (int)M, nullptr, (int)M, nx, h->Ax32, (int)M, 1.0);
+      convert_gather<double, float>(h->st, h->Ay, (int)M, nullptr, (int)M, ny, h->Ay32, (int)M, 1.0);
+      h->h32->load(f.get());
+    }
+    const bool prof = (opt.flags & NUDFT2_FLAG_PROFILE) != 0;
+    h->ops->prof.on = prof;
+    if (h->h64) h->h64->ops().prof.on = prof;
+    else h->h32->ops().prof.on = prof;
+    NH_CK(cudaStreamSynchronize(h->st));
+    h->factored = true;
+    *out = h;
+  });
+  if (dxy) cudaFree(dxy);
+  if (st != NUDFT2_OK && h) {
+    const std::string msg = g_err;
+    nudft2_hss_free(h);
+    g_err = msg;
+  }
+  return st;
 }
 
 void nudft2_hss_free(nudft2_hss_t h) {

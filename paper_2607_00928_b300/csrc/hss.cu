@@ -11,6 +11,7 @@
 //   solve        -- Sec. 2.3: bottom-up application of Omega^*, P^*; root least squares;
 //                   top-down back substitution.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
 #include "hss.cuh"
@@ -1428,6 +1429,155 @@ template <typename R> void Hss<R>::matvec_adj(const cplx<R>* y, int ldy, int s, 
   }
   NH_CK(cudaStreamSynchronize(st_));
   scr_.release(mk);
+}
+
+// ------------------------------------------------------------------------------- factor store
+// Section layout (all little-endian, as written by this host): per tree level l = 1..L and node p
+// the ten integers (ku, kv, pu, pv, m, n, mc, n1, rows2, omega), the matrices D, U, V, R, W, B[0..3],
+// Wk, D11inv, V2 and the Householder factors Om, Qv, P; then the root's two sizes, its Householder
+// factor and R^{-1}.  A matrix is (int32 rows, int32 cols, rows x cols complex entries column by
+// column); a Householder factor is (int32 m, int32 k, int32 merged) then V (m x k), the k / 32
+// panel T blocks and, when merged, the k / 256 group T blocks.
+namespace {
+void fwr(FILE* f, const void* p, size_t n) {
+  NH_REQUIRE(n == 0 || std::fwrite(p, 1, n, f) == n, ST_EINVAL, "save: write failed");
+}
+void frd(FILE* f, void* p, size_t n) {
+  NH_REQUIRE(n == 0 || std::fread(p, 1, n, f) == n, ST_EINVAL, "load: file truncated or corrupt");
+}
+template <typename R> void save_mat(FILE* f, const Mat<R>& a) {
+  const int32_t mn[2] = {a.p ? a.m : 0, a.p ? a.n : 0};
+  fwr(f, mn, sizeof(mn));
+  if ((size_t)mn[0] * mn[1] == 0) return;
+  std::vector<cplx<R>> h((size_t)mn[0] * mn[1]);
+  NH_CK(cudaMemcpy2D(h.data(), (size_t)mn[0] * sizeof(cplx<R>), a.p, (size_t)a.ld * sizeof(cplx<R>),
+                     (size_t)mn[0] * sizeof(cplx<R>), mn[1], cudaMemcpyDeviceToHost));
+  fwr(f, h.data(), h.size() * sizeof(cplx<R>));
+}
+template <typename R> Mat<R> load_mat(FILE* f, Arena& ar) {
+  int32_t mn[2];
+  frd(f, mn, sizeof(mn));
+  NH_REQUIRE(mn[0] >= 0 && mn[1] >= 0 && (int64_t)mn[0] * mn[1] < (1LL << 40), ST_EINVAL, "load: bad matrix size");
+  if ((size_t)mn[0] * mn[1] == 0) {
+    Mat<R> e;
+    e.m = mn[0]; e.n = mn[1]; e.ld = std::max(mn[0], 1);
+    return e;
+  }
+  Mat<R> a = ar.template mat<R>(mn[0], mn[1]);
+  std::vector<cplx<R>> h((size_t)mn[0] * mn[1]);
+  frd(f, h.data(), h.size() * sizeof(cplx<R>));
+  NH_CK(cudaMemcpy(a.p, h.data(), h.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+  return a;
+}
+template <typename R> void save_raw(FILE* f, const cplx<R>* d, size_t n) {
+  std::vector<cplx<R>> h(n);
+  if (n) NH_CK(cudaMemcpy(h.data(), d, n * sizeof(cplx<R>), cudaMemcpyDeviceToHost));
+  fwr(f, h.data(), n * sizeof(cplx<R>));
+}
+template <typename R> cplx<R>* load_raw(FILE* f, Arena& ar, size_t n) {
+  std::vector<cplx<R>> h(n);
+  frd(f, h.data(), n * sizeof(cplx<R>));
+  cplx<R>* d = (cplx<R>*)ar.alloc(std::max<size_t>(n, 1) * sizeof(cplx<R>));
+  if (n) NH_CK(cudaMemcpy(d, h.data(), n * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+  return d;
+}
+template <typename R> void save_qf(FILE* f, const QFac<R>& q) {
+  const int32_t h[3] = {q.V ? q.m : 0, q.V ? q.k : 0, q.Tg ? 1 : 0};
+  fwr(f, h, sizeof(h));
+  if (h[1] == 0) return;
+  Mat<R> v;
+  v.p = q.V; v.m = q.m; v.n = q.k; v.ld = q.ldv;
+  save_mat(f, v);
+  constexpr int NB = Ops<R>::NB, GW = Ops<R>::GW;
+  save_raw<R>(f, q.Tp, (size_t)((q.k + NB - 1) / NB) * NB * NB);
+  if (h[2]) save_raw<R>(f, q.Tg, (size_t)((q.k + GW - 1) / GW) * GW * GW);
+}
+template <typename R> QFac<R> load_qf(FILE* f, Arena& ar) {
+  int32_t h[3];
+  frd(f, h, sizeof(h));
+  NH_REQUIRE(h[0] >= 0 && h[1] >= 0 && h[1] <= h[0] && (h[2] == 0 || h[2] == 1), ST_EINVAL, "load: bad factor header");
+  QFac<R> q;
+  q.m = h[0]; q.k = h[1];
+  if (h[1] == 0) return q;
+  Mat<R> v = load_mat<R>(f, ar);
+  NH_REQUIRE(v.m == h[0] && v.n == h[1], ST_EINVAL, "load: factor size mismatch");
+  q.V = v.p; q.ldv = v.ld;
+  constexpr int NB = Ops<R>::NB, GW = Ops<R>::GW;
+  q.Tp = load_raw<R>(f, ar, (size_t)((q.k + NB - 1) / NB) * NB * NB);
+  if (h[2]) q.Tg = load_raw<R>(f, ar, (size_t)((q.k + GW - 1) / GW) * GW * GW);
+  return q;
+}
+}  // namespace
+
+template <typename R> void Hss<R>::save(FILE* f) {
+  NH_REQUIRE(factored && dropped_ == 0, ST_ESTATE, "save: factor (and recompute checkpointed levels) first");
+  NH_CK(cudaStreamSynchronize(st_));
+  const int L = pl_->L;
+  for (int l = 1; l <= L; ++l)
+    for (Node2<R>& nd : t_[l]) {
+      const int32_t iv[10] = {nd.ku, nd.kv, nd.pu, nd.pv, nd.m, nd.n, nd.mc, nd.n1, nd.rows2, nd.omega ? 1 : 0};
+      fwr(f, iv, sizeof(iv));
+      save_mat(f, nd.D);
+      save_mat(f, nd.U);
+      save_mat(f, nd.V);
+      save_mat(f, nd.R_);
+      save_mat(f, nd.W);
+      for (int c = 0; c < 4; ++c) save_mat(f, nd.B[c]);
+      save_mat(f, nd.Wk);
+      save_mat(f, nd.D11inv);
+      save_mat(f, nd.V2);
+      save_qf(f, nd.omega ? nd.Om : QFac<R>());
+      save_qf(f, nd.Qv);
+      save_qf(f, nd.P);
+    }
+  const int32_t rs[2] = {root_rows_, root_cols_};
+  fwr(f, rs, sizeof(rs));
+  save_qf(f, Proot_);
+  save_mat(f, Rinv_);
+}
+
+template <typename R> void Hss<R>::load(FILE* f) {
+  const int L = pl_->L;
+  t_.assign(L + 1, {});
+  for (int l = 0; l <= L; ++l) t_[l].resize((size_t)pl_->nn[l]);
+  gen_.reset(new Arena((size_t)256 << 20, true));
+  gen_->set_stream(st_);
+  fac_.clear();
+  for (int l = 0; l <= L; ++l) {
+    fac_.emplace_back(new Arena((size_t)64 << 20, true));
+    fac_.back()->set_stream(st_);
+  }
+  for (int l = 1; l <= L; ++l)
+    for (Node2<R>& nd : t_[l]) {
+      int32_t iv[10];
+      frd(f, iv, sizeof(iv));
+      for (int q = 0; q < 9; ++q) NH_REQUIRE(iv[q] >= 0, ST_EINVAL, "load: bad node header");
+      nd.ku = iv[0]; nd.kv = iv[1]; nd.pu = iv[2]; nd.pv = iv[3];
+      nd.m = iv[4]; nd.n = iv[5]; nd.mc = iv[6]; nd.n1 = iv[7]; nd.rows2 = iv[8]; nd.omega = iv[9] != 0;
+      nd.D = load_mat<R>(f, *gen_);
+      nd.U = load_mat<R>(f, *gen_);
+      nd.V = load_mat<R>(f, *gen_);
+      nd.R_ = load_mat<R>(f, *gen_);
+      nd.W = load_mat<R>(f, *gen_);
+      for (int c = 0; c < 4; ++c) nd.B[c] = load_mat<R>(f, *gen_);
+      Arena& fa = *fac_[l];
+      nd.Wk = load_mat<R>(f, fa);
+      nd.D11inv = load_mat<R>(f, fa);
+      nd.V2 = load_mat<R>(f, fa);
+      nd.Om = load_qf<R>(f, fa);
+      nd.Qv = load_qf<R>(f, fa);
+      nd.P = load_qf<R>(f, fa);
+    }
+  int32_t rs[2];
+  frd(f, rs, sizeof(rs));
+  NH_REQUIRE(rs[0] >= rs[1] && rs[1] >= 0, ST_EINVAL, "load: bad root sizes");
+  root_rows_ = rs[0];
+  root_cols_ = rs[1];
+  Proot_ = load_qf<R>(f, *fac_[0]);
+  Rinv_ = load_mat<R>(f, *fac_[0]);
+  NH_REQUIRE(Rinv_.m == root_cols_ && Rinv_.n == root_cols_, ST_EINVAL, "load: root size mismatch");
+  factored = true;
+  dropped_ = 0;
 }
 
 template <typename R> double Hss<R>::solve_entries() const {

@@ -1,6 +1,7 @@
 // HSS construction (1D compression, face-splitting assembly, recompression), URV
 // factorization and URV solve for the transformed 2D NUDFT matrix G~ = A F^{-1}.
 #pragma once
+#include <cstdio>
 #include <memory>
 #include <vector>
 
@@ -87,6 +88,11 @@ template <typename R> class Hss {
   // ensure_factored() recomputes them from the generators and the kept factors of the levels below
   // (returns true when it did, i.e. device addresses of factors changed).
   void checkpoint(int levels);
+  // Factor store: write every generator and URV factor (device -> file), or read them back into a
+  // fresh object built on the same plan (file -> device) and mark it factored.  The file position
+  // advances past this object's section.
+  void save(FILE* f);
+  void load(FILE* f);
   bool ensure_factored();
   int dropped_levels() const { return dropped_; }
   // y (N x s, tree column order) = G~_hss^+ f (f: M x s in 2D row order); both device

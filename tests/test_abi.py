@@ -78,3 +78,26 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_factor_store_header_is_checked_on_the_host(cdll, tmp_path):
+    """nudft2_hss_load validates the file header before any device work: a missing file, a file
+    that is not a factor store, one of another version and a truncated header are all EINVAL, and
+    *out stays NULL."""
+    import struct
+    from paper_2607_00928_b300.binding import EINVAL
+    cdll.nudft2_hss_load.restype = ctypes.c_int
+    cdll.nudft2_hss_load.argtypes = [ctypes.c_char_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    out = ctypes.c_void_p()
+    assert cdll.nudft2_hss_load(str(tmp_path / "missing.bin").encode(), None, ctypes.byref(out)) == EINVAL
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a factor store at all" * 4)
+    assert cdll.nudft2_hss_load(str(junk).encode(), None, ctypes.byref(out)) == EINVAL
+    magic = struct.pack("<II", 0x4644554E, 0x53483254)
+    other = tmp_path / "other.bin"
+    other.write_bytes(magic + struct.pack("<II", 999, 48) + bytes(64))
+    assert cdll.nudft2_hss_load(str(other).encode(), None, ctypes.byref(out)) == EINVAL
+    short = tmp_path / "short.bin"
+    short.write_bytes(magic + struct.pack("<I", 1))
+    assert cdll.nudft2_hss_load(str(short).encode(), None, ctypes.byref(out)) == EINVAL
+    assert out.value is None
