@@ -1454,7 +1454,8 @@ template <typename R> void save_mat(FILE* f, const Mat<R>& a) {
                      (size_t)mn[0] * sizeof(cplx<R>), mn[1], cudaMemcpyDeviceToHost));
   fwr(f, h.data(), h.size() * sizeof(cplx<R>));
 }
-template <typename R> Mat<R> load_mat(FILE* f, Arena& ar) {
+// (copies into arena memory run on the arena's stream: its allocations are stream-ordered)
+template <typename R> Mat<R> load_mat(FILE* f, Arena& ar, cudaStream_t st) {
   int32_t mn[2];
   frd(f, mn, sizeof(mn));
   NH_REQUIRE(mn[0] >= 0 && mn[1] >= 0 && (int64_t)mn[0] * mn[1] < (1LL << 40), ST_EINVAL, "load: bad matrix size");
@@ -1466,7 +1467,8 @@ template <typename R> Mat<R> load_mat(FILE* f, Arena& ar) {
   Mat<R> a = ar.template mat<R>(mn[0], mn[1]);
   std::vector<cplx<R>> h((size_t)mn[0] * mn[1]);
   frd(f, h.data(), h.size() * sizeof(cplx<R>));
-  NH_CK(cudaMemcpy(a.p, h.data(), h.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+  NH_CK(cudaMemcpyAsync(a.p, h.data(), h.size() * sizeof(cplx<R>), cudaMemcpyHostToDevice, st));
+  NH_CK(cudaStreamSynchronize(st));
   return a;
 }
 template <typename R> void save_raw(FILE* f, const cplx<R>* d, size_t n) {
@@ -1474,11 +1476,14 @@ template <typename R> void save_raw(FILE* f, const cplx<R>* d, size_t n) {
   if (n) NH_CK(cudaMemcpy(h.data(), d, n * sizeof(cplx<R>), cudaMemcpyDeviceToHost));
   fwr(f, h.data(), n * sizeof(cplx<R>));
 }
-template <typename R> cplx<R>* load_raw(FILE* f, Arena& ar, size_t n) {
+template <typename R> cplx<R>* load_raw(FILE* f, Arena& ar, size_t n, cudaStream_t st) {
   std::vector<cplx<R>> h(n);
   frd(f, h.data(), n * sizeof(cplx<R>));
   cplx<R>* d = (cplx<R>*)ar.alloc(std::max<size_t>(n, 1) * sizeof(cplx<R>));
-  if (n) NH_CK(cudaMemcpy(d, h.data(), n * sizeof(cplx<R>), cudaMemcpyHostToDevice));
+  if (n) {
+    NH_CK(cudaMemcpyAsync(d, h.data(), n * sizeof(cplx<R>), cudaMemcpyHostToDevice, st));
+    NH_CK(cudaStreamSynchronize(st));
+  }
   return d;
 }
 template <typename R> void save_qf(FILE* f, const QFac<R>& q) {
@@ -1492,19 +1497,19 @@ template <typename R> void save_qf(FILE* f, const QFac<R>& q) {
   save_raw<R>(f, q.Tp, (size_t)((q.k + NB - 1) / NB) * NB * NB);
   if (h[2]) save_raw<R>(f, q.Tg, (size_t)((q.k + GW - 1) / GW) * GW * GW);
 }
-template <typename R> QFac<R> load_qf(FILE* f, Arena& ar) {
+template <typename R> QFac<R> load_qf(FILE* f, Arena& ar, cudaStream_t st) {
   int32_t h[3];
   frd(f, h, sizeof(h));
   NH_REQUIRE(h[0] >= 0 && h[1] >= 0 && h[1] <= h[0] && (h[2] == 0 || h[2] == 1), ST_EINVAL, "load: bad factor header");
   QFac<R> q;
   q.m = h[0]; q.k = h[1];
   if (h[1] == 0) return q;
-  Mat<R> v = load_mat<R>(f, ar);
+  Mat<R> v = load_mat<R>(f, ar, st);
   NH_REQUIRE(v.m == h[0] && v.n == h[1], ST_EINVAL, "load: factor size mismatch");
   q.V = v.p; q.ldv = v.ld;
   constexpr int NB = Ops<R>::NB, GW = Ops<R>::GW;
-  q.Tp = load_raw<R>(f, ar, (size_t)((q.k + NB - 1) / NB) * NB * NB);
-  if (h[2]) q.Tg = load_raw<R>(f, ar, (size_t)((q.k + GW - 1) / GW) * GW * GW);
+  q.Tp = load_raw<R>(f, ar, (size_t)((q.k + NB - 1) / NB) * NB * NB, st);
+  if (h[2]) q.Tg = load_raw<R>(f, ar, (size_t)((q.k + GW - 1) / GW) * GW * GW, st);
   return q;
 }
 }  // namespace
@@ -1554,27 +1559,27 @@ template <typename R> void Hss<R>::load(FILE* f) {
       for (int q = 0; q < 9; ++q) NH_REQUIRE(iv[q] >= 0, ST_EINVAL, "load: bad node header");
       nd.ku = iv[0]; nd.kv = iv[1]; nd.pu = iv[2]; nd.pv = iv[3];
       nd.m = iv[4]; nd.n = iv[5]; nd.mc = iv[6]; nd.n1 = iv[7]; nd.rows2 = iv[8]; nd.omega = iv[9] != 0;
-      nd.D = load_mat<R>(f, *gen_);
-      nd.U = load_mat<R>(f, *gen_);
-      nd.V = load_mat<R>(f, *gen_);
-      nd.R_ = load_mat<R>(f, *gen_);
-      nd.W = load_mat<R>(f, *gen_);
-      for (int c = 0; c < 4; ++c) nd.B[c] = load_mat<R>(f, *gen_);
+      nd.D = load_mat<R>(f, *gen_, st_);
+      nd.U = load_mat<R>(f, *gen_, st_);
+      nd.V = load_mat<R>(f, *gen_, st_);
+      nd.R_ = load_mat<R>(f, *gen_, st_);
+      nd.W = load_mat<R>(f, *gen_, st_);
+      for (int c = 0; c < 4; ++c) nd.B[c] = load_mat<R>(f, *gen_, st_);
       Arena& fa = *fac_[l];
-      nd.Wk = load_mat<R>(f, fa);
-      nd.D11inv = load_mat<R>(f, fa);
-      nd.V2 = load_mat<R>(f, fa);
-      nd.Om = load_qf<R>(f, fa);
-      nd.Qv = load_qf<R>(f, fa);
-      nd.P = load_qf<R>(f, fa);
+      nd.Wk = load_mat<R>(f, fa, st_);
+      nd.D11inv = load_mat<R>(f, fa, st_);
+      nd.V2 = load_mat<R>(f, fa, st_);
+      nd.Om = load_qf<R>(f, fa, st_);
+      nd.Qv = load_qf<R>(f, fa, st_);
+      nd.P = load_qf<R>(f, fa, st_);
     }
   int32_t rs[2];
   frd(f, rs, sizeof(rs));
   NH_REQUIRE(rs[0] >= rs[1] && rs[1] >= 0, ST_EINVAL, "load: bad root sizes");
   root_rows_ = rs[0];
   root_cols_ = rs[1];
-  Proot_ = load_qf<R>(f, *fac_[0]);
-  Rinv_ = load_mat<R>(f, *fac_[0]);
+  Proot_ = load_qf<R>(f, *fac_[0], st_);
+  Rinv_ = load_mat<R>(f, *fac_[0], st_);
   NH_REQUIRE(Rinv_.m == root_cols_ && Rinv_.n == root_cols_, ST_EINVAL, "load: root size mismatch");
   factored = true;
   dropped_ = 0;
