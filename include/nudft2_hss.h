@@ -78,6 +78,12 @@ typedef struct {
 #define NUDFT2_FLAG_FP64_RESIDUALS 2u   /* MIXED: every refinement residual from the exact FP64 apply
                                            (default: the first; later steps subtract A d of the
                                            O(eps)-small correction d in FP32)               */
+#define NUDFT2_FLAG_FADI 4u   /* Alg. 1 step 1 by the route Sec. 3.1 cites: the 1D HSS approximations
+                                 by factored ADI on the Sylvester equation of the transformed 1D
+                                 matrix (Zolotarev shifts for the two arcs of a block) and the
+                                 interpolative decomposition, with nested skeletons; default: the
+                                 truncated SVD of each node's kernel-entry block.  EINVAL when eps is
+                                 too small for n (more than 64 shifts needed).                    */
 
 /* Accumulated device time of one kernel class (NUDFT2_FLAG_PROFILE), with its algorithmic
  * flop and byte counts summed over launches. */
@@ -262,6 +268,18 @@ nudft2_status nudft2_exact_apply(const double* d_x, const double* d_y, int64_t M
  * Psi(gamma_j, xi_k) = (1/n)((gamma_j/xi_k)^n - 1)/((gamma_j/xi_k) - 1), Psi = 1 at gamma = xi).
  * d_x: M points (device), d_out: M x n complex128 column major (ld M).  Errors: EINVAL. */
 nudft2_status nudft2_psi_eval(const double* d_x, int64_t M, int n, void* d_out, void* stream);
+
+/* nudft2_fadi_plan: host only (no device work), for tests of the shift computation of
+ * NUDFT2_FLAG_FADI.  The plan of a node of d columns (first column 0) of a 1D matrix with n
+ * columns at tolerance eps1: side 0 for its row block G~(J, K^c), side 1 for its column block
+ * G~(J^c, K) (Sec. 3.1, the Sylvester equation of the transformed 1D matrix).  Writes the exact
+ * columns (*ne entries of ex, <= 65), the J (<= 64) shift positions xa (zeros) and xb (poles) in
+ * units of the circle (shift = exp(-2 pi i x)), the (ne + J)^2 mixing matrix C (column major,
+ * interleaved re/im doubles) of the candidate basis a^T C, and the bound max|r|/min|r| of the
+ * shifts.  All arrays are caller-owned host memory.  Returns 0, or EINVAL for a bad node (d < 1,
+ * d >= n) or an eps1 needing more than 64 shifts. */
+int nudft2_fadi_plan(int side, int d, int n, double eps1, int* ne, int* J, int* ex, double* xa, double* xb,
+                     double* C, double* ratio);
 
 /* nudft2_test_fail_alloc: host-side fault injection for tests (not in the paper).  With k > 0 the
  * k-th device-memory request of the library's arenas from now on fails with ENOMEM, once, on

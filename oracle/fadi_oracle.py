@@ -44,9 +44,9 @@ Readings (the same ones the CUDA path takes):
 """
 from __future__ import annotations
 
+import mpmath
 import numpy as np
 import scipy.linalg as sla
-from scipy.special import ellipj, ellipkm1
 
 from .nudft_oracle import tilde_1d
 
@@ -105,11 +105,15 @@ def moebius_inverse(w, t2, t3, t4, gamma):
 
 
 def wachspress_p(gamma, J):
-    """p_j = gamma dn((2j - 1) K(k') / (2J), k'), k'^2 = 1 - 1/gamma^2, j = 1..J."""
-    m1 = 1.0 / gamma**2                       # 1 - k'^2
-    K = ellipkm1(m1)
-    u = (2.0 * np.arange(1, J + 1) - 1.0) / (2.0 * J) * K
-    return gamma * ellipj(u, 1.0 - m1)[2]
+    """p_j = gamma dn((2j - 1) K(k') / (2J), k'), k'^2 = 1 - 1/gamma^2, j = 1..J.
+
+    K and dn by mpmath at 30 digits: for gamma above ~3e4 the parameter k'^2 is within 1e-9 of
+    1, where scipy's ellipj switches to an approximation good to only about 1 - k'^2."""
+    with mpmath.workdps(30):
+        m1 = mpmath.mpf(1) / mpmath.mpf(gamma) ** 2         # 1 - k'^2
+        K = mpmath.ellipk(1 - m1)
+        return np.array([float(mpmath.mpf(gamma) * mpmath.ellipfun("dn", (2 * j - 1) * K / (2 * J), m=1 - m1))
+                         for j in range(1, J + 1)])
 
 
 def zolotarev_ratio(gamma, p, samples=4001):

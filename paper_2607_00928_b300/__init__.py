@@ -6,5 +6,5 @@ constants of include/nudft2_hss.h.  All arithmetic runs in the CUDA library libn
 """
 from .binding import (  # noqa: F401
     EXACT_ADJ, EXACT_FWD, FAST_ADJ, FAST_FWD, FP64, MIXED, PINV, PINV_ADJ, LIB_PATH, NudftError, NudftHSS, lib,
-    build_batched, exact_apply, la_gemm, la_qr, la_qr_apply, la_tsvd, lstsq, peak_fma, psi_eval, run_batched, solve_batched,
+    build_batched, exact_apply, fadi_plan, la_gemm, la_qr, la_qr_apply, la_tsvd, lstsq, peak_fma, psi_eval, run_batched, solve_batched,
 )

@@ -44,6 +44,7 @@ class KStat(ctypes.Structure):
 
 FLAG_PROFILE = 1
 FLAG_FP64_RESIDUALS = 2
+FLAG_FADI = 4
 
 
 class NudftError(RuntimeError):
@@ -98,11 +99,13 @@ def lib() -> ctypes.CDLL:
     L.nudft2_exact_fwd_noalloc.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp]
     L.nudft2_peak_fma.argtypes = [ci, ctypes.POINTER(ctypes.c_double), vp]
     L.nudft2_hss_checkpoint.argtypes = [vp, ci, vp]
+    pint, pdbl = ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_double)
+    L.nudft2_fadi_plan.argtypes = [ci, ci, ci, ctypes.c_double, pint, pint, pint, pdbl, pdbl, pdbl, pdbl]
     L.nudft2_last_error.restype = ctypes.c_char_p
     for f in ("nudft2_hss_build", "nudft2_hss_factor", "nudft2_hss_solve", "nudft2_hss_apply", "nudft2_hss_info",
               "nudft2_hss_grad", "nudft2_hss_build_batched", "nudft2_hss_solve_batched", "nudft2_hss_run_batched", "nudft2_hss_plsqr",
               "nudft2_psi_eval", "nudft2_hss_kstats", "nudft2_la_tsvd", "nudft2_la_qr", "nudft2_la_qr_apply", "nudft2_test_fail_alloc", "nudft2_hss_save", "nudft2_hss_load", "nudft2_la_gemm", "nudft2_exact_apply",
-              "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint"):
+              "nudft2_exact_fwd_noalloc", "nudft2_peak_fma", "nudft2_hss_checkpoint", "nudft2_fadi_plan"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -131,6 +134,22 @@ def peak_fma(prec: int) -> float:
     v = ctypes.c_double()
     _check(lib().nudft2_peak_fma(prec, ctypes.byref(v), _stream()))
     return v.value
+
+
+def fadi_plan(side: int, d: int, n: int, eps1: float) -> dict:
+    """The host-side fADI plan of a node of d columns out of n (nudft2_fadi_plan; no device work)."""
+    ne, J, ratio = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    ex = (ctypes.c_int * 65)()
+    xa, xb = (ctypes.c_double * 64)(), (ctypes.c_double * 64)()
+    C = (ctypes.c_double * (2 * 65 * 65))()
+    code = lib().nudft2_fadi_plan(side, d, n, eps1, ctypes.byref(ne), ctypes.byref(J), ex, xa, xb, C,
+                                  ctypes.byref(ratio))
+    if code != OK:
+        raise NudftError(code, "fadi_plan: bad node or eps1 too small for n")
+    q = ne.value + J.value
+    Cc = [complex(C[2 * e], C[2 * e + 1]) for e in range(q * q)]
+    return dict(ex=list(ex[:ne.value]), J=J.value, xa=list(xa[:J.value]), xb=list(xb[:J.value]),
+                C=[Cc[j * q:(j + 1) * q] for j in range(q)], ratio=ratio.value)   # C as columns
 
 
 def psi_eval(x: torch.Tensor, n: int) -> torch.Tensor:
@@ -233,7 +252,7 @@ class NudftHSS:
 
     def __init__(self, x, y, nx: int, ny: int, eps: float = 1e-10, levels: int = 0, leaf: int = 64,
                  prec: str = "fp64", refine_tol: float = 1e-8, refine_max: int = 8, stream=None,
-                 profile: bool = False, fp64_residuals: bool = False, levels_y: int = 0):
+                 profile: bool = False, fp64_residuals: bool = False, levels_y: int = 0, fadi: bool = False):
         self._h = ctypes.c_void_p()
         self.x = torch.as_tensor(x).to(device="cuda", dtype=torch.float64).contiguous()
         self.y = torch.as_tensor(y).to(device="cuda", dtype=torch.float64).contiguous()
@@ -241,7 +260,8 @@ class NudftHSS:
         self.nx, self.ny, self.N = nx, ny, nx * ny
         self.stream = stream
         o = Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
-                 (FLAG_PROFILE if profile else 0) | (FLAG_FP64_RESIDUALS if fp64_residuals else 0), levels_y)
+                 (FLAG_PROFILE if profile else 0) | (FLAG_FP64_RESIDUALS if fp64_residuals else 0)
+                 | (FLAG_FADI if fadi else 0), levels_y)
         _check(lib().nudft2_hss_build(ctypes.c_void_p(self.x.data_ptr()), ctypes.c_void_p(self.y.data_ptr()),
                                       self.M, nx, ny, ctypes.byref(o), _stream(stream), ctypes.byref(self._h)))
 
@@ -356,9 +376,9 @@ class NudftHSS:
 
 
 def _opts(eps=1e-10, levels=0, leaf=64, prec="fp64", refine_tol=1e-8, refine_max=8, profile=False,
-          levels_y=0) -> Opts:
+          levels_y=0, fadi=False) -> Opts:
     return Opts(eps, levels, leaf, MIXED if prec == "mixed" else FP64, refine_tol, refine_max,
-                FLAG_PROFILE if profile else 0, levels_y)
+                (FLAG_PROFILE if profile else 0) | (FLAG_FADI if fadi else 0), levels_y)
 
 
 def build_batched(problems, factor: bool = True, threads: int = 8, stream=None):
@@ -368,7 +388,7 @@ def build_batched(problems, factor: bool = True, threads: int = 8, stream=None):
     n = len(problems)
     xs = [torch.as_tensor(p["x"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
     ys = [torch.as_tensor(p["y"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
-    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max", "levels_y")
+    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max", "levels_y", "fadi")
     opts = (Opts * n)(*[_opts(**{k: p[k] for k in keys if k in p}) for p in problems])
     px = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
     py = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ys])
@@ -419,7 +439,7 @@ def run_batched(problems, fs, threads: int = 8, stream=None):
     n = len(problems)
     xs = [torch.as_tensor(p["x"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
     ys = [torch.as_tensor(p["y"]).to(device="cuda", dtype=torch.float64).contiguous() for p in problems]
-    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max", "levels_y")
+    keys = ("eps", "levels", "leaf", "prec", "refine_tol", "refine_max", "levels_y", "fadi")
     opts = (Opts * n)(*[_opts(**{k: p[k] for k in keys if k in p}) for p in problems])
     Ns = [int(p["nx"]) * int(p["ny"]) for p in problems]
     fcs = [_colmajor(f, x.numel()) for f, x in zip(fs, xs)]

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnudft2_hss.so")
-SOURCES = ["la.cu", "gemm_tc.cu", "nudft.cu", "hss.cu", "api.cu", "noalloc.cu", "peaks.cu", "sweep.cu", "qrcp.cu"]
+SOURCES = ["la.cu", "gemm_tc.cu", "nudft.cu", "hss.cu", "api.cu", "noalloc.cu", "peaks.cu", "sweep.cu", "qrcp.cu", "fadi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

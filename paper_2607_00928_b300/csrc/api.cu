@@ -766,7 +766,7 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
     if (opt.prec == NUDFT2_FP64) {
       h->h64.reset(new Hss<double>(h->st, &h->pl));
       h->h64->ops().prof.on = prof;
-      h->h64->build(opt.eps);
+      h->h64->build(opt.eps, (opt.flags & NUDFT2_FLAG_FADI) != 0);
     } else {
       h->h32.reset(new Hss<float>(h->st, &h->pl));
       h->h32->ops().prof.on = prof;
@@ -774,7 +774,7 @@ nudft2_status nudft2_hss_build(const double* d_x, const double* d_y, int64_t M, 
       h->Ay32 = h->keep.arr<float2>((size_t)M * ny);
       convert_gather<double, float>(h->st, h->Ax, (int)M, nullptr, (int)M, nx, h->Ax32, (int)M, 1.0);
       convert_gather<double, float>(h->st, h->Ay, (int)M, nullptr, (int)M, ny, h->Ay32, (int)M, 1.0);
-      h->h32->build(opt.eps);
+      h->h32->build(opt.eps, (opt.flags & NUDFT2_FLAG_FADI) != 0);
     }
     NH_CK(cudaStreamSynchronize(h->st));
     if (h->h32 && gemm_tc_error(true))

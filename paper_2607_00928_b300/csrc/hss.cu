@@ -2,7 +2,8 @@
 //
 // Stage map (Li & Liu):
 //   build_1d     -- HSS approximations of the transformed 1D matrices at eps/10 (Alg. 1, step 1),
-//                   by kernel-entry evaluation and per-node truncated SVD compression.
+//                   by kernel-entry evaluation and per-node truncated SVD compression
+//                   (fadi.cu: build_1d_fadi, the fADI + interpolative decomposition route).
 //   assemble_2d  -- generators of the face-splitting product on T^x . T^y from the constructive
 //                   proof of Thm. 3.5 (leaf D, U, V; B, R, W from Kronecker products).
 //   recompress   -- Sec. 2.2: bottom-up orthogonalization then top-down truncated-SVD compression.
@@ -708,9 +709,14 @@ template <typename R> void Hss<R>::recompress(double eps) {
   }
 }
 
-template <typename R> void Hss<R>::build(double eps) {
-  build_1d(pl_->tx, pl_->xo, eps / 10.0, gx_, Gx_);
-  build_1d(pl_->ty, pl_->yo, eps / 10.0, gy_, Gy_);
+template <typename R> void Hss<R>::build(double eps, bool fadi) {
+  if (fadi) {
+    build_1d_fadi(pl_->tx, pl_->xo, eps / 10.0, gx_);
+    build_1d_fadi(pl_->ty, pl_->yo, eps / 10.0, gy_);
+  } else {
+    build_1d(pl_->tx, pl_->xo, eps / 10.0, gx_, Gx_);
+    build_1d(pl_->ty, pl_->yo, eps / 10.0, gy_, Gy_);
+  }
   assemble_2d();
   recompress(eps);
   compact_generators();

@@ -1,7 +1,9 @@
 // HSS construction (1D compression, face-splitting assembly, recompression), URV
 // factorization and URV solve for the transformed 2D NUDFT matrix G~ = A F^{-1}.
 #pragma once
+#include <complex>
 #include <cstdio>
+#include <map>
 #include <memory>
 #include <vector>
 
@@ -79,10 +81,28 @@ template <typename R> struct Node2 {
   Mat<R> D11inv, V2;
 };
 
+// Plan of one node of the fADI + ID construction of a 1D HSS (fadi.cu), for a node of d columns
+// out of n in its own frame (first column 0).  side 0: the row block G~(J, K^c); side 1: the
+// column block G~(J^c, K).  The candidate basis row of a point (side 0) or a column (side 1) is
+// a^T C with a = [exact part (ex.size() entries), z_1 .. z_J] (the fADI factor with the shifts
+// alpha_i = exp(-2 pi i xa_i), beta_i = exp(-2 pi i xb_i)).
+struct FadiPlan {
+  int J = 0;
+  std::vector<int> ex;                    // side 0: exact columns; side 1: exact unit columns
+  std::vector<double> xa, xb;             // shift positions in units of the circle
+  std::vector<std::complex<double>> C;    // (ex.size() + J)^2, column major
+  double ratio = 0;                       // bound on max_E |r| / min_F |r| of the shifts
+  int q() const { return (int)ex.size() + J; }
+};
+constexpr int FADI_JMAX = 64;             // at most 64 shifts, so a basis has at most 65 columns
+FadiPlan fadi_plan(int side, int d, int n, double eps1, int jmax);
+
 template <typename R> class Hss {
  public:
   Hss(cudaStream_t st, const Plan* pl);
-  void build(double eps);
+  // fadi: the 1D HSS approximations by fADI + interpolative decomposition (the construction the
+  // paper cites for Alg. 1 step 1) instead of truncated SVDs of the kernel-entry blocks
+  void build(double eps, bool fadi = false);
   void factor();
   // Per-level checkpointing: hand back the URV factors of the top `levels` levels (and the root);
   // ensure_factored() recomputes them from the generators and the kept factors of the levels below
@@ -122,6 +142,8 @@ template <typename R> class Hss {
  private:
   void build_1d(const Tree1D& t, const double* xo, double eps, std::vector<std::vector<Gen1D<R>>>& g,
                 Mat<R>& G);
+  void build_1d_fadi(const Tree1D& t, const double* xo, double eps, std::vector<std::vector<Gen1D<R>>>& g);
+  const FadiPlan& fadi_plan_of(int side, int d, int n, double eps1);
   void assemble_2d();
   void recompress(double eps);
   void factor_level(int l);
@@ -137,6 +159,7 @@ template <typename R> class Hss {
   std::unique_ptr<Arena> gen_;                 // the final generators (after build)
   std::vector<std::unique_ptr<Arena>> fac_;   // factor storage per level (0 = root)
   int dropped_ = 0;                            // top levels whose factors were handed back
+  std::map<long long, FadiPlan> fplans_;       // fADI plans by (side, d, n)
   // root factor
   QFac<R> Proot_;
   Mat<R> Droot_, Rinv_;

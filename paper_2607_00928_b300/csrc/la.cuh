@@ -156,6 +156,14 @@ template <typename R> class Ops {
   void tsvd_ct(const std::vector<Mat<R>>& Ct, double eps, Arena& keep,
                std::vector<Mat<R>>& P, std::vector<std::vector<double>>& S);
 
+  // Row interpolative decomposition of every basis B_i (mc_i x q_i, q_i <= 1024), passed as
+  // W_i = B_i^* (q_i x mc_i, overwritten by its column-pivoted QR): rank r_i = the leading pivots
+  // with |R_kk| > tol |R_00| (at least 1 when mc_i >= 1), skeleton sk_i = the first r_i pivots
+  // (host), interpolation matrix T_i (mc_i x r_i, from `keep`) with T_i(sk_i, :) = I and
+  // B_i ~= T_i B_i(sk_i, :).  fadi.cu.
+  void row_id(const std::vector<Mat<R>>& W, double tol, Arena& keep, std::vector<Mat<R>>& T,
+              std::vector<std::vector<int>>& sk);
+
   int launches() const { return launches_; }
   void count(int n = 1) { launches_ += n; }
   // Capture mode: host->device descriptor copies are staged in `pool` (kept alive with the graph).

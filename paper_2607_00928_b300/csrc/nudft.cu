@@ -21,18 +21,6 @@ __device__ __forceinline__ int find_prob2(const int* pre, int n, int t) {
 }
 
 // ---------------------------------------------------------------- kernel entries (Sec. 2.4)
-__device__ __forceinline__ double2 psi_entry(double x, int k, int n) {
-  double t = x - (double)k / (double)n;
-  t -= floor(t + 0.5);
-  if (t == 0.0) return make_double2(1.0, 0.0);
-  double sn, cn, s1, c1, sp, cp;
-  sincospi((double)n * t, &sn, &cn);
-  sincospi(t, &s1, &c1);
-  sincospi((double)(n - 1) * t, &sp, &cp);
-  const double r = sn / ((double)n * s1);
-  return make_double2(r * cp, -r * sp);
-}
-
 template <typename R>
 __global__ void k_psi(const PsiD<R>* __restrict__ ds, const int* __restrict__ pre, int np) {
   const int pi = find_prob2(pre, np, blockIdx.x);

@@ -5,9 +5,21 @@
 
 namespace nh {
 
-// out(i, k) = Psi(x[idx ? idx[i] : i], k0 + k; n), i < m, k < nk.
 // Psi(gamma, xi) = (1/n) sum_l (gamma/xi)^l = exp(-i pi (n-1) t) sin(pi n t) / (n sin(pi t)),
-// t = x - k/n reduced to [-1/2, 1/2); Psi = 1 at t = 0.
+// t = x - k/n reduced to [-1/2, 1/2); Psi = 1 at t = 0 (the entries of the transformed 1D matrix).
+__device__ __forceinline__ double2 psi_entry(double x, int k, int n) {
+  double t = x - (double)k / (double)n;
+  t -= floor(t + 0.5);
+  if (t == 0.0) return make_double2(1.0, 0.0);
+  double sn, cn, s1, c1, sp, cp;
+  sincospi((double)n * t, &sn, &cn);
+  sincospi(t, &s1, &c1);
+  sincospi((double)(n - 1) * t, &sp, &cp);
+  const double r = sn / ((double)n * s1);
+  return make_double2(r * cp, -r * sp);
+}
+
+// out(i, k) = Psi(x[i], k0 + k; n), i < m, k < nk.
 template <typename R> struct PsiD {
   const double* x; int m; int k0, nk, n; cplx<R>* out; int ld;
 };
