@@ -185,7 +185,8 @@ static void fadi_y(const std::vector<cd>& cn, const std::vector<cd>& cv, const s
 }
 
 FadiPlan fadi_plan(int side, int d, int n, double eps1, int jmax) {
-  NH_REQUIRE(d >= 1 && d < n && jmax >= 1 && jmax <= FADI_JMAX, ST_EINVAL, "fadi_plan: bad node");
+  NH_REQUIRE((side == 0 || side == 1) && d >= 1 && d < n && jmax >= 1 && jmax <= FADI_JMAX, ST_EINVAL,
+             "fadi_plan: bad node");
   FadiPlan P;
   const int nset = side == 0 ? n - d - 1 : d - 1;
   double e1, e2, f1, f2;
@@ -479,7 +480,7 @@ template <typename R> static GemmD<R> gemm_d(const Mat<R>& A, const Mat<R>& B, c
 }
 
 template <typename R> const FadiPlan& Hss<R>::fadi_plan_of(int side, int d, int n, double eps1) {
-  const long long key = ((long long)n * 8192 + d) * 2 + side;
+  const auto key = std::make_tuple(side, d, n);
   auto it = fplans_.find(key);
   if (it == fplans_.end()) it = fplans_.emplace(key, fadi_plan(side, d, n, eps1, FADI_JMAX)).first;
   return it->second;

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <map>
 #include <memory>
+#include <tuple>
 #include <vector>
 
 #include "la.cuh"
@@ -159,7 +160,7 @@ template <typename R> class Hss {
   std::unique_ptr<Arena> gen_;                 // the final generators (after build)
   std::vector<std::unique_ptr<Arena>> fac_;   // factor storage per level (0 = root)
   int dropped_ = 0;                            // top levels whose factors were handed back
-  std::map<long long, FadiPlan> fplans_;       // fADI plans by (side, d, n)
+  std::map<std::tuple<int, int, int>, FadiPlan> fplans_;   // fADI plans by (side, d, n)
   // root factor
   QFac<R> Proot_;
   Mat<R> Droot_, Rinv_;

@@ -39,3 +39,5 @@ def test_library_plan_rejects_bad_nodes(plan):
         plan(0, 0, 16, 1e-10)
     with pytest.raises(NudftError):
         plan(1, 16, 16, 1e-10)
+    with pytest.raises(NudftError):
+        plan(2, 4, 16, 1e-10)
