@@ -41,3 +41,20 @@ def test_library_plan_rejects_bad_nodes(plan):
         plan(1, 16, 16, 1e-10)
     with pytest.raises(NudftError):
         plan(2, 4, 16, 1e-10)
+
+
+def test_library_plan_weights_carry_the_blocks_singular_values(plan):
+    """With the library's shifts and mixing matrix, the oracle's basis of a row block has the
+    block's singular values (the property the ID's pivot cut relies on)."""
+    from oracle import tilde_1d
+    n, d, m, c0 = 128, 16, 500, 48
+    got = plan(0, d, n, 1e-12)
+    P = dict(ex=np.array(got["ex"]), J=got["J"], xa=np.array(got["xa"]), xb=np.array(got["xb"]),
+             C=np.array(got["C"]).T)
+    x = c0 / n + np.random.default_rng(9).random(m) * d / n
+    B = fo.node_basis(P, 0, np.arange(m), c0, n, x)
+    Kc = np.r_[0:c0, c0 + d:n]
+    sx = np.linalg.svd(tilde_1d(x, n)[:, Kc], compute_uv=False)
+    sb = np.linalg.svd(B, compute_uv=False)
+    k = min(len(sb), 20)
+    assert np.abs(sb[:k] - sx[:k]).max() <= 1e-12 * sx[0]
