@@ -251,7 +251,7 @@ def node_basis(plan, side, cand, c0, n, xs=None):
 # ------------------------------------------------------------------------- interpolative decomposition
 def row_id(B, tol):
     """Row ID of B (m x q) by the column-pivoted Householder QR of B^* (scipy / LAPACK geqp3):
-    B^* P = Q R, rank r = #{k : |R_kk| > tol |R_00|} (at least 1 when B has a nonzero row),
+    B^* P = Q R, rank r = the leading pivots with |R_kk| > tol |R_00| (1 for the zero block),
     skeleton S = P[:r], T = P [I; (R11^{-1} R12)^*] so that T(S, :) = I and B ~= T B(S, :)."""
     m = B.shape[0]
     if m == 0:
@@ -259,8 +259,13 @@ def row_id(B, tol):
     W = B.conj().T
     _, R, P = sla.qr(W, mode="economic", pivoting=True)
     dg = np.abs(np.diag(R))
-    r = int(np.sum(dg > tol * dg[0])) if dg.size and dg[0] > 0 else 0
-    r = max(r, 1)
+    T = np.zeros((m, 1), np.complex128)
+    if dg[0] == 0.0:               # the zero block: T = the unit vector of the first pivot
+        T[P[0], 0] = 1.0
+        return P[:1].copy(), T
+    r = 0                          # the leading pivots above the cut
+    while r < dg.size and dg[r] > tol * dg[0]:
+        r += 1
     X = sla.solve_triangular(R[:r, :r], R[:r, r:])
     T = np.zeros((m, r), np.complex128)
     T[P[:r], :] = np.eye(r)

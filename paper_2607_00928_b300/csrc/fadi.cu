@@ -427,23 +427,30 @@ void Ops<R>::row_id(const std::vector<Mat<R>>& W, double tol, Arena& keep, std::
   std::vector<GemmD<R>> gm;
   std::vector<CopyD<R>> cp;
   std::vector<Mat<R>> Xs(nm);
+  // a basis whose largest pivot is (numerically) zero is the zero block: on points exactly on the
+  // grid k/n the kernel entries are exact zeros.  It keeps rank 1 with T = the unit vector of its
+  // first pivot (an exact ID of the zero block) instead of inverting a zero R_11.
+  const double zero_pivot = sizeof(R) == 8 ? 1e-300 : 1e-30;
   for (int i : act) {
     const int mc = W[i].n, p = std::min(W[i].m, W[i].n);
     const R* g = hdg.data() + doff[i];
     const double cut = tol * (double)g[0];
+    const bool zero = !((double)g[0] > zero_pivot);
     int r = 0;
-    while (r < p && (double)g[r] > cut) ++r;
+    if (!zero)
+      while (r < p && (double)g[r] > cut) ++r;
     r = std::max(r, 1);
     rk[i] = r;
     const int* pm = hperm.data() + poff[i];
     sk[i].assign(pm, pm + r);
     for (int j = 0; j < mc; ++j) inv[poff[i] + pm[j]] = j;
+    Mat<R> tp = ar_->template mat<R>(mc, r);   // [I; X^*] in pivot order (set_identity below)
+    Tp.push_back(tp);
+    if (zero) continue;
     // X = R11^{-1} R12 (r x (mc - r))
     Mat<R> S = ar_->template mat<R>(r, r);
     tri.push_back(W[i].block(0, 0, r, r));
     triX.push_back(S);
-    Mat<R> tp = ar_->template mat<R>(mc, r);
-    Tp.push_back(tp);
     if (mc > r) {
       Xs[i] = ar_->template mat<R>(r, mc - r);
       gm.push_back({S.p, W[i].at(0, r), Xs[i].p, r, mc - r, r, S.ld, W[i].ld, Xs[i].ld, OP_N, OP_N, R(1), R(0)});

@@ -114,6 +114,12 @@ def test_row_id_of_an_exactly_low_rank_matrix():
     assert np.abs(A - T @ A[S]).max() < 1e-11 * np.abs(A).max()
 
 
+def test_row_id_of_the_zero_block():
+    S, T = fo.row_id(np.zeros((7, 4), np.complex128), 1e-10)
+    assert len(S) == 1 and T.shape == (7, 1)
+    assert T[S[0], 0] == 1.0 and np.count_nonzero(T) == 1
+
+
 def test_row_side_basis_carries_the_blocks_singular_values():
     """B = [near column, Z diag(g) R_Y^T] has the singular values of G~(J, K^c)."""
     rng = np.random.default_rng(6)
