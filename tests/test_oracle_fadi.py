@@ -184,3 +184,90 @@ def test_hss1d_on_the_uniform_grid_is_the_identity():
     h = fo.hss1d_fadi_id(x, n, 3, 1e-12)
     H = fo.hss1d_dense(h)
     assert np.abs(H - fo.tilde_1d_sorted(h)).max() < 1e-13
+
+
+# ---------------------------------------------------------------- planted mistakes
+# Each test plants a plausible slip in the oracle (on the CPU) and checks that one of the pins
+# above would fail on it.
+
+def _residual_identity_error(fadi_fn):
+    rng = np.random.default_rng(3)
+    n, d = 64, 8
+    x, kf, s, dk, u, v, X = _node_cauchy(rng, n, d, 120)
+    xa, xb, _, _ = fo.zolotarev_shifts((0.0, d / n), ((d + 1) / n, (n - 1) / n), 6)
+    al, be = fo._em(xa), fo._em(xb)
+    Z, Y, g = fadi_fn(s, u, dk, v, al, be)
+    ref = fo.rational(s, al, be)[:, None] * X / fo.rational(dk, al, be)[None, :]
+    return np.abs(X - (Z * g) @ Y.T - ref).max() / np.abs(X).max()
+
+
+def test_pin_catches_a_shifted_shift_index_in_fadi():
+    def bad_fadi(rn, ru, cn, cv, alpha, beta):
+        J = len(alpha)
+        Z = np.zeros((len(rn), J), np.complex128)
+        Y = np.zeros((len(cn), J), np.complex128)
+        z, y = ru / (rn - beta[0]), cv / (cn - alpha[0])
+        for i in range(J):
+            Z[:, i], Y[:, i] = z, y
+            if i + 1 < J:
+                z = z * (rn - alpha[i + 1]) / (rn - beta[i + 1])      # slip: alpha_{i+1} for alpha_i
+                y = y * (cn - beta[i]) / (cn - alpha[i + 1])
+        return Z, Y, beta - alpha
+    assert _residual_identity_error(fo.fadi) < 1e-12
+    assert _residual_identity_error(bad_fadi) > 1e-6
+
+
+def test_pin_catches_a_wrong_sign_of_g():
+    def bad_fadi(*a):
+        Z, Y, g = fo.fadi(*a)
+        return Z, Y, -g                                              # slip: alpha - beta
+    assert _residual_identity_error(bad_fadi) > 1e-3
+
+
+def test_pin_catches_the_complementary_modulus_swapped():
+    def bad_p(gam, J):
+        import mpmath
+        with mpmath.workdps(30):
+            m = 1 - mpmath.mpf(1) / mpmath.mpf(gam) ** 2
+            K = mpmath.ellipk(1 - m)                                 # slip: K(k) for K(k')
+            return np.array([float(gam * mpmath.ellipfun("dn", (2 * j - 1) * K / (2 * J), m=m))
+                             for j in range(1, J + 1)])
+    gam, J = 100.0, 8
+    bound = 4.0 * np.exp(-np.pi**2 * J / np.log(4.0 * gam))
+    assert fo.zolotarev_ratio(gam, fo.wachspress_p(gam, J)) <= bound * (1 + 1e-3)
+    assert fo.zolotarev_ratio(gam, bad_p(gam, J)) > 2 * bound
+
+
+def _hss_error():
+    rng = np.random.default_rng(1)
+    x = rng.random(300)
+    h = fo.hss1d_fadi_id(x, 64, 3, 1e-11)
+    G = fo.tilde_1d_sorted(h)
+    return np.linalg.norm(fo.hss1d_dense(h) - G, 2) / np.linalg.norm(G, 2)
+
+
+def test_pin_catches_a_dropped_near_column(monkeypatch):
+    good = fo.node_plan
+
+    def bad_plan(side, d, n, eps1, jmax=64):
+        P = good(side, d, n, eps1, jmax)
+        if side == 0 and P["J"]:
+            P = dict(P)
+            P["C"] = P["C"].copy()
+            P["C"][0, 0] = 0.0                                       # slip: the touching column left out
+        return P
+    assert _hss_error() < 5e-11                                      # the reconstruction pin's bound
+    monkeypatch.setattr(fo, "node_plan", bad_plan)
+    assert _hss_error() > 5e-11
+
+
+def test_pin_catches_a_column_basis_without_conjugation(monkeypatch):
+    good = fo.row_id
+    calls = {"n": 0}
+
+    def bad_row_id(B, tol):
+        S, T = good(B, tol)
+        calls["n"] += 1
+        return S, (T.conj() if calls["n"] % 2 == 0 else T)           # slip: V = T_c instead of conj(T_c)
+    monkeypatch.setattr(fo, "row_id", bad_row_id)
+    assert _hss_error() > 5e-11                                      # fails the reconstruction pin
